@@ -1,0 +1,92 @@
+"""Planted mistakes in the oracle must fail at least one pin.
+
+Each case patches one oracle function with a plausible slip (a dropped factor,
+a flipped sign, a wrong update order) and runs the pins that should catch it.
+This shows the pins in test_oracle_pins.py are strong enough to notice the
+mistakes they are meant to notice.  Everything here runs on the CPU.
+"""
+import math
+
+import pytest
+
+import oracle
+import oracle.cac_mfz as om
+import test_oracle_pins as pins
+
+
+def _fails(check, *args):
+    try:
+        check(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def _inj_eta_half(j, e, R, h, eta, tau):
+    return j * e * (R * h - (eta * eta / 2.0) * math.sqrt(tau))
+
+
+def _inj_no_R(j, e, R, h, eta, tau):
+    return j * e * (h - (eta * eta / 4.0) * math.sqrt(tau))
+
+
+def _cn_sign(Goff, R, c, hz, tau):
+    st = math.sqrt(tau)
+    return +Goff @ (R * (c + st) / 4.0) + (st / 2.0) * hz[:, None]
+
+
+def _cn_half(Goff, R, c, hz, tau):
+    st = math.sqrt(tau)
+    return -Goff @ (R * (c + st) / 2.0) + (st / 2.0) * hz[:, None]
+
+
+def _bn_geq(Goff, R, c, hz, tau):
+    st = math.sqrt(tau)
+    return -(st / 2.0) * (Goff @ (R * (c >= 0.0)) - hz[:, None])
+
+
+def _euler_sequential(c, e, p, inj, prm):
+    c1 = c + prm.dt * ((-1.0 + p - c * c) * c + prm.K * inj)
+    e1 = e + prm.dt * (-prm.beta * (c1 * c1 - prm.tau) * e)
+    return c1, e1
+
+
+def _brute_force_pin():
+    # the correct oracle hits 8 of the 12 seeds of brute_force_hits()
+    assert pins.brute_force_hits() >= 7
+
+
+@pytest.mark.parametrize("name,target,fake,checks", [
+    ("eta^2/2 threshold", "injection", _inj_eta_half, ["separable_cn"]),
+    ("R_r dropped from injection", "injection", _inj_no_R, ["separable_cn", "brute"]),
+    ("coupling sign flipped", "local_field_cn", _cn_sign, ["J", "brute"]),
+    ("coupling halved 1/4 -> 1/2", "local_field_cn", _cn_half, ["J", "three"]),
+    ("H(0) = 1 in the binarised field", "local_field_bn", _bn_geq, ["three"]),
+    ("e updated from the new c", "euler_step", _euler_sequential, ["three"]),
+])
+def test_planted_mistake_is_caught(monkeypatch, name, target, fake, checks):
+    monkeypatch.setattr(om, target, fake)
+    monkeypatch.setattr(oracle, target, fake)
+    table = {
+        "separable_cn": (pins.test_separable_case_is_hard_threshold, "cn"),
+        "brute": (_brute_force_pin,),
+        "J": (pins.test_coupling_J_symmetric_zero_diagonal,),
+        "three": (pins.test_three_spin_hand_worked_step,),
+    }
+    caught = [c for c in checks if _fails(*table[c])]
+    assert caught, f"planted mistake '{name}' passed every pin in {checks}"
+
+
+def test_planted_refit_mistake_is_caught(monkeypatch):
+    orig = om.refit_exact
+
+    def wrong(G, hz, g, sigma):
+        R, s = orig(G, hz, g, sigma)
+        off = sigma == 0
+        R = R.copy()
+        R[off] = hz[off] / g[off]  # forgets the coupling to the support
+        return R, s
+
+    monkeypatch.setattr(om, "refit_exact", wrong)
+    monkeypatch.setattr(oracle, "refit_exact", wrong)
+    assert _fails(pins.test_refit_matches_lstsq_and_is_jacobi_fixed_point)
