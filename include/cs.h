@@ -1,0 +1,157 @@
+/*
+ * cs.h -- C ABI of the GB300 (sm_103a) solver for L0-regularised compressed
+ * sensing by the mean-field coherent Ising machine with chaotic amplitude
+ * control and a classical refit (CAC-MFZ-CDP, arXiv 2405.00366).
+ *
+ * The solver minimises  E(R, sigma) = 1/2 ||y - A (sigma o R)||^2 + lambda ||sigma||_0
+ * (Eq. doublel0) by the alternating loop of Algorithm 1: for each outer
+ * iteration it integrates the mean-field CIM amplitude equations (Eq. mfeq1,
+ * Eq. MFZlocalfieldmain, Eq. GMFZEC5 with the local field of Eq. localfieldMFZ
+ * or Eq. localfieldMFZBN) by explicit Euler steps, reads the support
+ * sigma = H(c) off the final amplitudes, and refits R on that support.
+ *
+ * Conventions for every call:
+ *  - Every call returns a cs_status; none aborts the process and no kernel
+ *    traps.  On failure cs_last_error() gives a message (thread-local).
+ *  - The caller keeps ownership of every pointer it passes.  Host buffers are
+ *    read or written before the call returns unless stated otherwise.
+ *  - The library owns all device memory it allocates; it is released by
+ *    cs_problem_destroy.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is queued on it in order.
+ *  - Matrices are row-major.  Per-trial arrays are laid out [r][t]: element
+ *    (r, t) of an N x T array is at r * T + t.
+ */
+#ifndef CS_H
+#define CS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CS_OK = 0,
+  CS_EINVAL = 1,      /* bad argument (sizes, NaN input, parameters) */
+  CS_ENOMEM = 2,      /* device allocation failed or HBM budget exceeded */
+  CS_ECUDA = 3,       /* a CUDA runtime call failed; see cs_last_error() */
+  CS_ETIMEOUT = 4,    /* a device-side wait exceeded params.timeout_ms; results invalid */
+  CS_ENOTREADY = 5,   /* no solve has completed on this problem yet */
+  CS_ESINGULAR = 6    /* warning: a refit needed the ridge; results are valid */
+} cs_status;
+
+enum { CS_FIELD_CN = 0, CS_FIELD_BN = 1 };          /* Eq. localfieldMFZ / Eq. localfieldMFZBN */
+enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1 };   /* normal equations / damped Jacobi */
+enum { CS_PUMP_LINEAR = 0, CS_PUMP_SIGMOID = 1 };   /* p0 -> p1 ramp / Eq. pumprateGACS */
+enum { CS_INIT_UNIFORM = 0, CS_INIT_NORMAL = 1 };   /* U(-s, s) / N(0, s^2) */
+/* Storage precision of the coupling matrix G and arithmetic of the Euler loop:
+ * FP64 keeps G and the amplitudes in double; the others accumulate in float. */
+enum { CS_P_FP64 = 0, CS_P_FP32 = 1, CS_P_BF16 = 2, CS_P_FP16 = 3 };
+
+/* Run parameters (Methods and Numerical experiments of the paper).
+ * Fill with cs_params_default() and override. */
+typedef struct {
+  int32_t n_outer;      /* outer iterations of Algorithm 1 (>= 1) */
+  int32_t n_steps;      /* Euler steps per CIM run (>= 1) */
+  double dt;            /* Euler step (> 0) */
+  int32_t pump_kind;    /* CS_PUMP_* */
+  double p0, p1;        /* linear pump: p(t_n) = p0 + (p1 - p0) n / n_steps */
+  double p_thr, d, t0, width; /* sigmoid pump: (p_thr - d) + 2d / (1 + exp(-(t - t0)/width)) */
+  double beta;          /* CAC feedback rate, Eq. GMFZEC5 */
+  double tau;           /* target amplitude (> 0) */
+  double K;             /* feedback strength, Eq. mfeq1 */
+  double j;             /* out-coupling rate, Eq. MFZlocalfieldmain */
+  double eta_init;      /* <= 0: fixed eta = sqrt(2 lambda); else Eq. etaSchedulling */
+  double eta_end, velo;
+  int32_t init_kind;    /* CS_INIT_*: initial amplitudes of each CIM run */
+  double init_scale;
+  int32_t field;        /* CS_FIELD_* */
+  int32_t refit;        /* CS_REFIT_* */
+  double jacobi_dt;     /* damped Jacobi step (paper: 0.1) */
+  int32_t jacobi_iters; /* damped Jacobi sweeps per outer iteration (paper: 100) */
+  int32_t precision;    /* CS_P_* */
+  uint64_t seed;        /* key of the counter-based initial-amplitude generator */
+  int32_t instance;     /* instance number mixed into that key */
+  int32_t record_steps; /* record c, e after each of the first k steps of outer iteration 0 */
+  int64_t timeout_ms;   /* bound on every device-side wait (grid barrier) */
+  int32_t test_phantom_ctas; /* test hook: the grid barrier also waits for this many CTAs that
+                                do not exist, so it runs into timeout_ms; 0 in normal use */
+} cs_params;
+
+typedef struct cs_problem cs_problem;
+
+/* Defaults: 20 x 1000 steps, dt 0.01, linear pump 0 -> 1.5, beta 0.2, tau 1,
+ * K = j = 1, fixed eta, U(-0.01, 0.01) initial amplitudes, continuous field,
+ * exact refit, FP32, seed 0, no recording, 10 s timeout. */
+void cs_params_default(cs_params* p);
+
+/* Create a problem from A (M x N, row-major, float64) and y (M, float64) and
+ * form, on the GPU, G = A^T A (FP64), h^z = A^T y and g = diag G
+ * (Eq. l0Hamiltonian and the Zeeman term of Eq. localfieldMFZ).  G is then
+ * kept resident for every solve on this problem.
+ *  on_device = 0: A, y are host pointers (copied to the device);
+ *  on_device = 1: A, y are device pointers, read on `stream` before return.
+ * Errors: CS_EINVAL for M, N < 1, lambda < 0 or NULL pointers; CS_ENOMEM;
+ * CS_ECUDA.  A and y are checked for finite values on the device. */
+cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t N,
+                            double lambda, int on_device, void* stream, cs_problem** out);
+
+/* Queue one full solve (Algorithm 1, every outer iteration) of `trials`
+ * independent trials on the problem's stream; returns without waiting.
+ * Trial t draws its initial amplitudes from key (seed, instance, t, outer).
+ * Errors: CS_EINVAL for bad parameters or trials < 1; CS_ENOMEM; CS_ECUDA. */
+cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
+
+/* Wait for the last solve and copy out the kept trial (lowest energy, ties to
+ * the lower trial index): x_hat = sigma o R (N doubles), sigma_hat (N bytes,
+ * 0/1) and its energy (Eq. doublel0 with the problem's lambda, recomputed from
+ * A and y in FP64).  Any output pointer may be NULL.  stats, if not NULL,
+ * receives CS_STATS_LEN doubles:
+ *   [0] kept trial index  [1] |sigma_hat|  [2] 1 if a refit used the ridge
+ *   [3] device error word (0 = none)       [4] trials  [5] N  [6] M
+ * Host pointers.  Returns CS_ETIMEOUT if a device wait timed out,
+ * CS_ESINGULAR (with valid outputs) if the ridge was needed. */
+#define CS_STATS_LEN 8
+cs_status cs_result(cs_problem* p, double* x_hat, uint8_t* sigma_hat, double* energy,
+                    double* stats);
+
+/* Per-trial results of the last solve (host pointers, any may be NULL):
+ * R (N x trials, [r][t]), sigma (N x trials bytes), energy (trials),
+ * support_sizes (n_outer x trials int32: |sigma| after each outer iteration). */
+cs_status cs_result_trials(cs_problem* p, double* R, uint8_t* sigma, double* energy,
+                           int32_t* support_sizes);
+
+/* The recorded amplitudes of the last solve: c and e after each of the first
+ * params.record_steps Euler steps of outer iteration 0, as doubles laid out
+ * [step][r][t] (record_steps x N x trials).  Host pointers. */
+cs_status cs_trajectory(cs_problem* p, double* c, double* e);
+
+/* Copy the FP64 Gram data formed by cs_problem_create to host buffers
+ * (any may be NULL): G (N x N), h^z = A^T y (N), g = diag G (N). */
+cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g);
+
+/* Device time of the work queued by the last cs_problem_create and the last
+ * cs_solve on this problem, from CUDA events recorded on the problem's stream
+ * around each group of launches, summed per group into ms[CS_TIMING_LEN]:
+ *   [0] Gram formation  [1] Euler kernels (all outer iterations)
+ *   [2] refits          [3] the rest (coupling copy, initial R, objective, selection)
+ * and, in *launches, how many kernels the library launched for them.  Waits for
+ * the stream.  Host pointers, either may be NULL. */
+#define CS_TIMING_LEN 4
+cs_status cs_problem_timing(cs_problem* p, double* ms, int64_t* launches);
+
+/* Sizes of a problem. */
+cs_status cs_problem_shape(const cs_problem* p, int64_t* M, int64_t* N);
+
+/* Release everything the problem owns.  NULL is ignored. */
+void cs_problem_destroy(cs_problem* p);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_H */

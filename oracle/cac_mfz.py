@@ -227,12 +227,13 @@ def euler_step(c, e, p, inj, prm: Params):
 
 
 def cim_run(Goff, hz, R, eta, prm: Params, outer: int, inst: int = 0,
-            record_steps: int = 0):
+            record_steps: int = 0, max_steps: Optional[int] = None):
     """One CIM run (support estimation of Algorithm 1) for all trials (columns of R).
 
     Returns sigma (N, T) uint8, the final (c, e) and, if record_steps > 0, the
     amplitudes c and e after each of the first record_steps steps
-    (shape (record_steps, N, T)).
+    (shape (record_steps, N, T)).  max_steps stops the run early (a bounded
+    sample for tests and timing; the schedules still refer to prm.n_steps).
     """
     N, T = R.shape
     c = np.stack([initial_amplitudes(prm.seed, inst, t, outer, N, prm.init_kind, prm.init_scale)
@@ -241,7 +242,7 @@ def cim_run(Goff, hz, R, eta, prm: Params, outer: int, inst: int = 0,
     rec_c = np.zeros((record_steps, N, T)) if record_steps else None
     rec_e = np.zeros((record_steps, N, T)) if record_steps else None
     field = local_field_cn if prm.field == "cn" else local_field_bn
-    for n in range(prm.n_steps):
+    for n in range(prm.n_steps if max_steps is None else min(max_steps, prm.n_steps)):
         p = pump(n, prm)
         h = field(Goff, R, c, hz, prm.tau)
         inj = injection(prm.j, e, R, h, eta, prm.tau)
@@ -311,13 +312,14 @@ def hamming_loss(sigma, xi):
 
 # ---------------------------------------------------------------- Algorithm 1
 def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
-          record_steps: int = 0, R_init: Optional[np.ndarray] = None):
+          record_steps: int = 0, R_init: Optional[np.ndarray] = None,
+          max_steps: Optional[int] = None):
     """Alternating minimisation (Algorithm 1) for `trials` independent trials.
 
     Returns a dict with the kept (lowest-energy) trial's x_hat, sigma, energy and
     index, every trial's R, sigma and energy, per-outer support sizes, a flag
     for ridge use and, with record_steps, the first steps' (c, e) of outer
-    iteration 0.
+    iteration 0.  max_steps truncates every CIM run (bounded samples only).
     """
     A = np.asarray(A, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -335,7 +337,8 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
     for i in range(prm.n_outer):
         eta = eta_at(i, prm, lam)
         sigma, c, e, rc, re = cim_run(Goff, hz, R, eta, prm, outer=i, inst=inst,
-                                      record_steps=record_steps if i == 0 else 0)
+                                      record_steps=record_steps if i == 0 else 0,
+                                      max_steps=max_steps)
         if i == 0 and record_steps:
             rec = (rc, re)
         for t in range(trials):

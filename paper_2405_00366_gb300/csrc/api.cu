@@ -1,0 +1,402 @@
+// The C ABI of include/cs.h: argument checks, ownership of device memory and
+// the host-side order of the stream-ordered launches of one solve
+// (Algorithm 1: per outer iteration one persistent Euler kernel and one refit
+// kernel; then the objective and the kept trial).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct cs_problem {
+  cs::ProblemDev P;
+  cs::SolveDev S;
+  // timing marks: event pair k brackets launch group k of category cats[k]
+  std::vector<cudaEvent_t> events;
+  std::vector<int> cats;
+  int n_marks = 0, n_create_marks = 0;
+};
+
+namespace cs {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured_device != dev) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    configured_device = dev;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+namespace {
+
+cs_status fail(cs_status st, const std::string& msg) {
+  set_last_error(msg);
+  return st;
+}
+
+cs_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CS_CUDA(call, what)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+cudaStream_t g_alloc_stream = nullptr;  // stream of the allocation in progress
+
+template <typename T>
+cudaError_t alloc(T** p, size_t elems) {
+  return dev_alloc((void**)p, (elems == 0 ? 1 : elems) * sizeof(T), g_alloc_stream);
+}
+
+void free_solve(SolveDev& S, cudaStream_t st) {
+  void* ptrs[] = {S.R, S.c, S.e, S.b, S.X0, S.X1, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
+                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular};
+  for (void* q : ptrs) dev_free(q, st);
+  S = SolveDev();
+}
+
+void free_problem(ProblemDev& P) {
+  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.flag};
+  for (void* q : ptrs) dev_free(q, P.stream);
+  P = ProblemDev();
+}
+
+size_t compute_bytes(int precision) { return precision == CS_P_FP64 ? 8 : 4; }
+
+// (Re)size the per-solve buffers for `trials`, n_outer and record_steps.
+cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int trials) {
+  const int rec = prm.record_steps > 0 ? std::min(prm.record_steps, prm.n_steps) : 0;
+  const bool fits = S.R && trials <= S.cap_trials && prm.n_outer <= S.cap_outer && rec <= S.cap_record &&
+                    compute_bytes(prm.precision) <= compute_bytes(S.cap_prec < 0 ? 0 : S.cap_prec);
+  if (!fits) {
+    free_solve(S, P.stream);
+    g_alloc_stream = P.stream;
+    const size_t N = (size_t)P.N, Np = (size_t)P.Npad, T = (size_t)trials;
+    const size_t cb = compute_bytes(prm.precision);
+    CS_CUDA(alloc(&S.R, N * T), "cudaMalloc R");
+    CS_CUDA(dev_alloc(&S.c, N * T * cb, P.stream), "cudaMalloc c");
+    CS_CUDA(dev_alloc(&S.e, N * T * cb, P.stream), "cudaMalloc e");
+    CS_CUDA(dev_alloc(&S.b, N * T * cb, P.stream), "cudaMalloc b");
+    CS_CUDA(dev_alloc(&S.X0, Np * T * cb, P.stream), "cudaMalloc X0");
+    CS_CUDA(dev_alloc(&S.X1, Np * T * cb, P.stream), "cudaMalloc X1");
+    CS_CUDA(cudaMemsetAsync(S.X0, 0, Np * T * cb, P.stream), "memset X0");
+    CS_CUDA(cudaMemsetAsync(S.X1, 0, Np * T * cb, P.stream), "memset X1");
+    CS_CUDA(alloc(&S.sigma, N * T), "cudaMalloc sigma");
+    CS_CUDA(alloc(&S.energy, T), "cudaMalloc energy");
+    CS_CUDA(alloc(&S.ssize, (size_t)prm.n_outer * T), "cudaMalloc ssize");
+    CS_CUDA(alloc(&S.sidx, N * T), "cudaMalloc sidx");
+    S.work_elems = T * (N * N + 2 * N);
+    CS_CUDA(alloc(&S.work, S.work_elems), "cudaMalloc refit workspace");
+    CS_CUDA(alloc(&S.rec_c, (size_t)rec * N * T), "cudaMalloc rec_c");
+    CS_CUDA(alloc(&S.rec_e, (size_t)rec * N * T), "cudaMalloc rec_e");
+    CS_CUDA(alloc(&S.x_hat, N), "cudaMalloc x_hat");
+    CS_CUDA(alloc(&S.sigma_hat, N), "cudaMalloc sigma_hat");
+    CS_CUDA(alloc(&S.stats, CS_STATS_LEN), "cudaMalloc stats");
+    CS_CUDA(alloc(&S.bar, 1), "cudaMalloc barrier");
+    CS_CUDA(alloc(&S.err, 1), "cudaMalloc err");
+    CS_CUDA(alloc(&S.singular, 1), "cudaMalloc singular");
+    S.cap_trials = trials;
+    S.cap_outer = prm.n_outer;
+    S.cap_record = rec;
+    S.cap_prec = prm.precision;
+  }
+  S.trials = trials;
+  S.n_outer = prm.n_outer;
+  S.record_steps = rec;
+  S.precision = prm.precision;
+  return CS_OK;
+}
+
+cs_status check_params(const cs_params* p, int trials) {
+  if (!p) return fail(CS_EINVAL, "params is NULL");
+  if (trials < 1) return fail(CS_EINVAL, "trials must be >= 1");
+  if (p->n_outer < 1 || p->n_steps < 1) return fail(CS_EINVAL, "n_outer and n_steps must be >= 1");
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(CS_EINVAL, "dt must be > 0");
+  if (!(p->tau > 0.0)) return fail(CS_EINVAL, "tau must be > 0");
+  if (p->pump_kind != CS_PUMP_LINEAR && p->pump_kind != CS_PUMP_SIGMOID) return fail(CS_EINVAL, "bad pump_kind");
+  if (p->pump_kind == CS_PUMP_SIGMOID && !(p->width > 0.0)) return fail(CS_EINVAL, "sigmoid width must be > 0");
+  if (p->init_kind != CS_INIT_UNIFORM && p->init_kind != CS_INIT_NORMAL) return fail(CS_EINVAL, "bad init_kind");
+  if (p->field != CS_FIELD_CN && p->field != CS_FIELD_BN) return fail(CS_EINVAL, "bad field");
+  if (p->refit != CS_REFIT_EXACT) return fail(CS_EINVAL, "only the exact refit is available");
+  if (p->precision < CS_P_FP64 || p->precision > CS_P_FP16) return fail(CS_EINVAL, "bad precision");
+  if (p->eta_init > 0.0 && !(p->velo > 0.0)) return fail(CS_EINVAL, "velo must be > 0 with an eta schedule");
+  if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
+  if (p->timeout_ms <= 0) return fail(CS_EINVAL, "timeout_ms must be > 0");
+  if (p->test_phantom_ctas < 0 || p->test_phantom_ctas > 1024) return fail(CS_EINVAL, "bad test_phantom_ctas");
+  const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
+                         p->eta_init, p->eta_end, p->velo, p->init_scale};
+  for (double v : vals)
+    if (!std::isfinite(v)) return fail(CS_EINVAL, "non-finite parameter");
+  return CS_OK;
+}
+
+// Threshold of outer iteration i (Eq. etaSchedulling), or sqrt(2 lambda) when fixed.
+double eta_at(int i, const cs_params& p, double lambda) {
+  if (p.eta_init <= 0.0) return std::sqrt(2.0 * lambda);
+  return std::max(p.eta_init * (1.0 - i / p.velo), p.eta_end);
+}
+
+cudaError_t mark(cs_problem* p, int cat, bool begin) {
+  const int k = begin ? p->n_marks : p->n_marks - 1;
+  const size_t need = 2 * (size_t)(k + 1);
+  while (p->events.size() < need) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    p->events.push_back(ev);
+  }
+  if (begin) {
+    if ((int)p->cats.size() <= k) p->cats.resize(k + 1);
+    p->cats[k] = cat;
+    ++p->n_marks;
+  }
+  return cudaEventRecord(p->events[2 * k + (begin ? 0 : 1)], p->P.stream);
+}
+
+}  // namespace
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+void cs_params_default(cs_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_outer = 20;
+  p->n_steps = 1000;
+  p->dt = 0.01;
+  p->pump_kind = CS_PUMP_LINEAR;
+  p->p0 = 0.0;
+  p->p1 = 1.5;
+  p->p_thr = 1.0;
+  p->d = 0.4;
+  p->t0 = 4.0;
+  p->width = 2.0;
+  p->beta = 0.2;
+  p->tau = 1.0;
+  p->K = 1.0;
+  p->j = 1.0;
+  p->eta_init = 0.0;
+  p->eta_end = 0.0;
+  p->velo = 51.0;
+  p->init_kind = CS_INIT_UNIFORM;
+  p->init_scale = 0.01;
+  p->field = CS_FIELD_CN;
+  p->refit = CS_REFIT_EXACT;
+  p->jacobi_dt = 0.1;
+  p->jacobi_iters = 100;
+  p->precision = CS_P_FP32;
+  p->seed = 0;
+  p->instance = 0;
+  p->record_steps = 0;
+  p->timeout_ms = 10000;
+}
+
+const char* cs_last_error(void) { return g_last_error.c_str(); }
+
+cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t N, double lambda, int on_device,
+                            void* stream, cs_problem** out) {
+  if (!out) return fail(CS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A || !y) return fail(CS_EINVAL, "A or y is NULL");
+  if (M < 1 || N < 1) return fail(CS_EINVAL, "M and N must be >= 1");
+  if (M > (1 << 20) || N > (1 << 16)) return fail(CS_EINVAL, "M or N too large");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(CS_EINVAL, "lambda must be finite and >= 0");
+  cs_problem* p = new cs_problem();
+  ProblemDev& P = p->P;
+  P.M = M;
+  P.N = N;
+  P.Npad = (N + 7) / 8 * 8;
+  P.lambda = lambda;
+  P.stream = (cudaStream_t)stream;
+  auto bail = [&](cs_status st) {
+    free_problem(P);
+    for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
+    delete p;
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&P.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "device query"));
+  const size_t MN = (size_t)M * N;
+  g_alloc_stream = P.stream;
+  if ((e = alloc(&P.A, MN)) != cudaSuccess || (e = alloc(&P.y, (size_t)M)) != cudaSuccess ||
+      (e = alloc(&P.G, (size_t)N * N)) != cudaSuccess || (e = alloc(&P.hz, (size_t)N)) != cudaSuccess ||
+      (e = alloc(&P.g, (size_t)N)) != cudaSuccess || (e = alloc(&P.flag, 1)) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMalloc problem"));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(P.A, A, MN * sizeof(double), kind, P.stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(P.y, y, (size_t)M * sizeof(double), kind, P.stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(P.flag, 0, sizeof(int), P.stream)) != cudaSuccess)
+    return bail(cuda_fail(e, "copy A, y"));
+  if ((e = mark(p, TM_GRAM, true)) != cudaSuccess || (e = launch_gram(P)) != cudaSuccess ||
+      (e = mark(p, TM_GRAM, false)) != cudaSuccess)
+    return bail(cuda_fail(e, "gram launch"));
+  P.launches = 2;
+  p->n_create_marks = p->n_marks;
+  int flag = 0;
+  if ((e = cudaMemcpyAsync(&flag, P.flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(P.stream)) != cudaSuccess)
+    return bail(cuda_fail(e, "gram"));
+  if (flag) return bail(fail(CS_EINVAL, "A or y has a non-finite value"));
+  *out = p;
+  return CS_OK;
+}
+
+cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
+  if (!p) return fail(CS_EINVAL, "problem is NULL");
+  cs_status st = check_params(prm, trials);
+  if (st != CS_OK) return st;
+  ProblemDev& P = p->P;
+  SolveDev& S = p->S;
+  S.done = false;
+  p->n_marks = p->n_create_marks;
+  P.launches = 2;
+  CS_CUDA(mark(p, TM_OTHER, true), "event");
+  if (P.gs_prec != prm->precision) ++P.launches;
+  CS_CUDA(launch_store_coupling(P, prm->precision), "store coupling");
+  if ((st = ensure_solve(P, S, *prm, trials)) != CS_OK) return st;
+  CS_CUDA(cudaMemsetAsync(S.err, 0, sizeof(int), P.stream), "memset err");
+  CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), P.stream), "memset singular");
+  int khz = 0;
+  CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P.device), "clock rate");
+  const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
+  CS_CUDA(launch_init_R(P, S), "init R");
+  CS_CUDA(mark(p, TM_OTHER, false), "event");
+  P.launches += 1;
+  for (int i = 0; i < prm->n_outer; ++i) {
+    const double eta = eta_at(i, *prm, P.lambda);
+    CS_CUDA(mark(p, TM_EULER, true), "event");
+    cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
+    if (e == cudaErrorInvalidConfiguration)
+      return fail(CS_EINVAL, "N too large for the on-chip Euler kernel at this precision");
+    CS_CUDA(e, "euler launch");
+    CS_CUDA(mark(p, TM_EULER, false), "event");
+    CS_CUDA(mark(p, TM_REFIT, true), "event");
+    CS_CUDA(launch_refit(P, S, *prm, i), "refit launch");
+    CS_CUDA(mark(p, TM_REFIT, false), "event");
+    P.launches += 2;
+  }
+  CS_CUDA(mark(p, TM_OTHER, true), "event");
+  CS_CUDA(launch_finish(P, S), "finish launch");
+  CS_CUDA(mark(p, TM_OTHER, false), "event");
+  P.launches += 2;
+  S.done = true;
+  return CS_OK;
+}
+
+static cs_status wait_and_check(cs_problem* p, double* stats_out) {
+  if (!p) return fail(CS_EINVAL, "problem is NULL");
+  if (!p->S.done) return fail(CS_ENOTREADY, "no solve queued on this problem");
+  CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
+  double st[CS_STATS_LEN];
+  CS_CUDA(cudaMemcpy(st, p->S.stats, sizeof(st), cudaMemcpyDeviceToHost), "copy stats");
+  if (stats_out) std::memcpy(stats_out, st, sizeof(st));
+  const int err = (int)st[3];
+  if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a grid barrier timed out");
+  if (err != 0) return fail(CS_ECUDA, "device error word " + std::to_string(err));
+  return st[2] != 0.0 ? CS_ESINGULAR : CS_OK;
+}
+
+cs_status cs_result(cs_problem* p, double* x_hat, uint8_t* sigma_hat, double* energy, double* stats) {
+  double st[CS_STATS_LEN];
+  cs_status s = wait_and_check(p, st);
+  if (s != CS_OK && s != CS_ESINGULAR) return s;
+  const size_t N = (size_t)p->P.N;
+  if (x_hat) CS_CUDA(cudaMemcpy(x_hat, p->S.x_hat, N * sizeof(double), cudaMemcpyDeviceToHost), "copy x_hat");
+  if (sigma_hat) CS_CUDA(cudaMemcpy(sigma_hat, p->S.sigma_hat, N, cudaMemcpyDeviceToHost), "copy sigma_hat");
+  if (energy) *energy = st[7];
+  if (stats) std::memcpy(stats, st, sizeof(st));
+  if (s == CS_ESINGULAR) set_last_error("a refit used the ridge");
+  return s;
+}
+
+cs_status cs_result_trials(cs_problem* p, double* R, uint8_t* sigma, double* energy, int32_t* support_sizes) {
+  cs_status s = wait_and_check(p, nullptr);
+  if (s != CS_OK && s != CS_ESINGULAR) return s;
+  const size_t N = (size_t)p->P.N, T = (size_t)p->S.trials;
+  if (R) CS_CUDA(cudaMemcpy(R, p->S.R, N * T * sizeof(double), cudaMemcpyDeviceToHost), "copy R");
+  if (sigma) CS_CUDA(cudaMemcpy(sigma, p->S.sigma, N * T, cudaMemcpyDeviceToHost), "copy sigma");
+  if (energy) CS_CUDA(cudaMemcpy(energy, p->S.energy, T * sizeof(double), cudaMemcpyDeviceToHost), "copy energy");
+  if (support_sizes)
+    CS_CUDA(cudaMemcpy(support_sizes, p->S.ssize, (size_t)p->S.n_outer * T * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost),
+            "copy support sizes");
+  return s;
+}
+
+cs_status cs_trajectory(cs_problem* p, double* c, double* e) {
+  cs_status s = wait_and_check(p, nullptr);
+  if (s != CS_OK && s != CS_ESINGULAR) return s;
+  const size_t n = (size_t)p->S.record_steps * p->P.N * p->S.trials;
+  if (c) CS_CUDA(cudaMemcpy(c, p->S.rec_c, n * sizeof(double), cudaMemcpyDeviceToHost), "copy rec_c");
+  if (e) CS_CUDA(cudaMemcpy(e, p->S.rec_e, n * sizeof(double), cudaMemcpyDeviceToHost), "copy rec_e");
+  return s;
+}
+
+cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g) {
+  if (!p) return fail(CS_EINVAL, "problem is NULL");
+  CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
+  const size_t N = (size_t)p->P.N;
+  if (G) CS_CUDA(cudaMemcpy(G, p->P.G, N * N * sizeof(double), cudaMemcpyDeviceToHost), "copy G");
+  if (hz) CS_CUDA(cudaMemcpy(hz, p->P.hz, N * sizeof(double), cudaMemcpyDeviceToHost), "copy hz");
+  if (g) CS_CUDA(cudaMemcpy(g, p->P.g, N * sizeof(double), cudaMemcpyDeviceToHost), "copy g");
+  return CS_OK;
+}
+
+cs_status cs_problem_timing(cs_problem* p, double* ms, int64_t* launches) {
+  if (!p) return fail(CS_EINVAL, "problem is NULL");
+  CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
+  double acc[CS_TIMING_LEN] = {0, 0, 0, 0};
+  for (int k = 0; k < p->n_marks; ++k) {
+    float t = 0.f;
+    CS_CUDA(cudaEventElapsedTime(&t, p->events[2 * k], p->events[2 * k + 1]), "event time");
+    acc[p->cats[k]] += t;
+  }
+  if (ms) std::memcpy(ms, acc, sizeof(acc));
+  if (launches) *launches = p->P.launches;
+  return CS_OK;
+}
+
+cs_status cs_problem_shape(const cs_problem* p, int64_t* M, int64_t* N) {
+  if (!p) return fail(CS_EINVAL, "problem is NULL");
+  if (M) *M = p->P.M;
+  if (N) *N = p->P.N;
+  return CS_OK;
+}
+
+void cs_problem_destroy(cs_problem* p) {
+  if (!p) return;
+  cudaStream_t st = p->P.stream;
+  free_solve(p->S, st);
+  free_problem(p->P);
+  cudaStreamSynchronize(st);
+  for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
+  delete p;
+}
+
+}  // extern "C"

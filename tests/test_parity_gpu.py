@@ -1,0 +1,230 @@
+"""GPU path (libcs.so through its C ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+* FP64 solves: trajectories to 1e-10 relative, supports identical, signal to 1e-8.
+* FP32 solves: trajectories ||c_gpu - c_ref||_inf / max(||c_ref||_inf, 1e-2) <= 1e-4
+  per step over the first 200 steps; final supports identical; RMSE within 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import cs_inputs
+import oracle
+from paper_2405_00366_gb300 import cs
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_KEYS = {"n_outer", "n_steps", "dt", "pump_kind", "p0", "p1", "p_thr", "d", "t0", "width", "beta", "tau",
+               "K", "j", "eta_init", "eta_end", "velo", "init_kind", "init_scale", "field", "refit", "seed"}
+
+
+def oracle_params(w):
+    return oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS})
+
+
+def gpu_solve(inst, w, trials, record_steps=0, device_inputs=True):
+    prm = cs.params_from_workload(w, record_steps=record_steps)
+    if device_inputs:
+        A = torch.from_numpy(inst.A).cuda()
+        y = torch.from_numpy(inst.y).cuda()
+    else:
+        A, y = inst.A, inst.y
+    h = cs.cs_problem_create(A, y, inst.lam)
+    try:
+        cs.cs_solve(h, prm, trials)
+        x, s, E, st, status = cs.cs_result(h)
+        R, sig, Es, ss = cs.cs_result_trials(h, trials, w["n_outer"])
+        traj = cs.cs_trajectory(h, min(record_steps, w["n_steps"]), trials) if record_steps else None
+        gram = cs.cs_problem_gram(h)
+    finally:
+        cs.cs_problem_destroy(h)
+    return dict(x_hat=x, sigma=s, energy=E, stats=st, status=status, R=R, sigmas=sig, energies=Es,
+                support_sizes=ss, trajectory=traj, gram=gram)
+
+
+def rel_traj_err(c, ref):
+    """Per-step ||c - ref||_inf / max(||ref||_inf, 1e-2)."""
+    num = np.abs(c - ref).reshape(c.shape[0], -1).max(axis=1)
+    den = np.maximum(np.abs(ref).reshape(ref.shape[0], -1).max(axis=1), 1e-2)
+    return num / den
+
+
+# ------------------------------------------------------------------ a1: Gram
+@pytest.mark.parametrize("N,M", [(1, 1), (7, 5), (200, 120), (333, 130), (64, 300)])
+def test_gram_parity(N, M):
+    inst = cs_inputs.random_instance(N, M, max(1, N // 10), 0.01, 0.1, seed=N + M)
+    A = torch.from_numpy(inst.A).cuda()
+    y = torch.from_numpy(inst.y).cuda()
+    h = cs.cs_problem_create(A, y, inst.lam)
+    try:
+        G, hz, g = cs.cs_problem_gram(h)
+    finally:
+        cs.cs_problem_destroy(h)
+    Gr, hzr, gr = oracle.gram(inst.A, inst.y)
+    scale = np.abs(inst.A).max() ** 2 * M
+    np.testing.assert_allclose(G, Gr, rtol=0, atol=1e-13 * scale)
+    assert np.array_equal(G, G.T)
+    np.testing.assert_allclose(hz, hzr, rtol=0, atol=1e-13 * np.abs(inst.A).max() * np.abs(inst.y).sum() + 1e-300)
+    np.testing.assert_array_equal(g, np.diag(G))
+
+
+def test_host_inputs_match_device_inputs():
+    w = cs_inputs.workload("single_n200_fp64", n_outer=2, n_steps=300)
+    inst = cs_inputs.workload_instance(w)
+    a = gpu_solve(inst, w, 1, device_inputs=True)
+    b = gpu_solve(inst, w, 1, device_inputs=False)
+    np.testing.assert_array_equal(a["x_hat"], b["x_hat"])
+    np.testing.assert_array_equal(a["sigma"], b["sigma"])
+
+
+# ------------------------------------------------------------------ a2-a5: trajectories
+def test_trajectory_fp64_single():
+    w = cs_inputs.workload("single_n200_fp64", n_outer=1)
+    inst = cs_inputs.workload_instance(w)
+    g = gpu_solve(inst, w, 1, record_steps=200)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=1, record_steps=200)
+    c, e = g["trajectory"]
+    assert rel_traj_err(c, r["trajectory"][0]).max() <= 1e-10
+    assert rel_traj_err(e, r["trajectory"][1]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("field", ["cn", "bn"])
+def test_trajectory_fp32_trials64(field):
+    """The N = 2000, M = 1200, 64-trial workload: the first 200 Euler steps of every trial."""
+    w = cs_inputs.workload("trials64_n2000_fp32", n_outer=1, field=field)
+    inst = cs_inputs.workload_instance(w)
+    g = gpu_solve(inst, w, 64, record_steps=200)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=64, record_steps=200, max_steps=200)
+    c, e = g["trajectory"]
+    err_c = rel_traj_err(c, r["trajectory"][0])
+    err_e = rel_traj_err(e, r["trajectory"][1])
+    assert err_c.max() <= 1e-4, err_c.max()
+    assert err_e.max() <= 1e-4, err_e.max()
+
+
+# ------------------------------------------------------------------ whole solve
+def _compare_solve(g, r, inst, trials, x_tol, fp64):
+    np.testing.assert_array_equal(g["support_sizes"], r["support_sizes"])
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_array_equal(g["sigma"], r["sigma"])
+    assert int(g["stats"][0]) == r["best_trial"]
+    np.testing.assert_allclose(g["x_hat"], r["x_hat"], rtol=0, atol=x_tol)
+    np.testing.assert_allclose(g["R"], r["R"], rtol=0, atol=x_tol * 10)
+    np.testing.assert_allclose(g["energies"], r["energies"], rtol=1e-9 if fp64 else 1e-6)
+    assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+
+
+def test_solve_fp64_single_full():
+    """The single FP64 workload at its full size: N=200, M=120, 20 x 1000 steps."""
+    w = cs_inputs.workload("single_n200_fp64")
+    inst = cs_inputs.workload_instance(w)
+    g = gpu_solve(inst, w, 1)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=1)
+    _compare_solve(g, r, inst, 1, 1e-9, True)
+    assert g["energy"] == pytest.approx(r["energy"], rel=1e-10)
+    # the energy is the recomputed objective of the reported signal
+    res = inst.y - inst.A @ g["x_hat"]
+    assert g["energy"] == pytest.approx(0.5 * res @ res + inst.lam * g["sigma"].sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("precision,field", [("fp32", "cn"), ("fp32", "bn"), ("fp64", "bn")])
+def test_solve_ragged(precision, field):
+    """N = 333 (not a multiple of any tile), 5 trials, both fields."""
+    inst = cs_inputs.random_instance(333, 211, 30, 0.01, 0.04, seed=7)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=4, n_steps=600, precision=precision, field=field,
+             seed=11)
+    g = gpu_solve(inst, w, 5)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=5)
+    _compare_solve(g, r, inst, 5, 1e-9 if precision == "fp64" else 1e-5, precision == "fp64")
+
+
+def test_solve_paper_schedules_fp64():
+    """Sigmoid pump (Eq. pumprateGACS), eta schedule (Eq. etaSchedulling), Gaussian initial amplitudes."""
+    inst = cs_inputs.random_instance(150, 90, 15, 0.05, 0.0162, seed=21)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=6, n_steps=500, dt=0.02, pump_kind="sigmoid",
+             d=0.4, eta_init=0.8, eta_end=0.18, velo=5.0, init_kind="normal", seed=5)
+    g = gpu_solve(inst, w, 3)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=3)
+    _compare_solve(g, r, inst, 3, 1e-9, True)
+
+
+@pytest.mark.parametrize("N,M", [(1, 1), (2, 3), (9, 4)])
+def test_tiny_sizes(N, M):
+    inst = cs_inputs.random_instance(N, M, 1, 0.0, 0.01, seed=N)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=200)
+    g = gpu_solve(inst, w, 2)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=2)
+    _compare_solve(g, r, inst, 2, 1e-9, True)
+
+
+def test_empty_support():
+    """lambda so large that every spin ends off: R = A^T y / diag G, x_hat = 0, E = 1/2 ||y||^2."""
+    inst = cs_inputs.random_instance(64, 40, 5, 0.0, 50.0, seed=2)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300)
+    g = gpu_solve(inst, w, 2)
+    assert g["sigmas"].sum() == 0
+    G, hz, gd = oracle.gram(inst.A, inst.y)
+    np.testing.assert_allclose(g["R"], np.repeat((hz / gd)[:, None], 2, axis=1), rtol=1e-13)
+    assert g["energy"] == pytest.approx(0.5 * inst.y @ inst.y, rel=1e-13)
+
+
+def test_singular_support_uses_ridge():
+    """lambda = 0 with M < N: the support exceeds M, G_SS is singular and both sides take the ridge."""
+    inst = cs_inputs.random_instance(40, 12, 6, 0.1, 0.0, seed=3)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=400)
+    g = gpu_solve(inst, w, 1)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=1)
+    assert r["singular"] and g["status"] == cs.CS_ESINGULAR and g["stats"][2] == 1.0
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    assert np.all(np.isfinite(g["R"]))
+    # both interpolate y on the support
+    assert np.linalg.norm(inst.y - inst.A @ g["x_hat"]) < 1e-4 * np.linalg.norm(inst.y)
+
+
+def test_trials64_full_size_properties():
+    """The N = 2000, 64-trial workload at full size (30 x 2000 steps), in the launch
+    configuration the benchmark times.  The oracle runs trials 0 and 1 for the first two
+    outer iterations; the rest is checked by properties that hold at any size."""
+    w = cs_inputs.workload("trials64_n2000_fp32")
+    inst = cs_inputs.workload_instance(w)
+    g = gpu_solve(inst, w, 64)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(dict(w, n_outer=2)), trials=2)
+    np.testing.assert_array_equal(g["support_sizes"][:2, :2], r["support_sizes"])
+    G, hz, gd = oracle.gram(inst.A, inst.y)
+    for t in range(64):
+        s = g["sigmas"][:, t]
+        S = np.flatnonzero(s)
+        R = g["R"][:, t]
+        # the refit is the least-squares solution on S: zero gradient
+        grad = inst.A[:, S].T @ (inst.y - inst.A[:, S] @ R[S])
+        assert np.abs(grad).max() <= 1e-9 * np.linalg.norm(hz)
+        # off the support R is the Jacobi fixed point
+        lhs = gd * R + (G - np.diag(gd)) @ (s * R)
+        np.testing.assert_allclose(lhs, hz, rtol=0, atol=1e-9)
+        res = inst.y - inst.A @ (s * R)
+        assert g["energies"][t] == pytest.approx(0.5 * res @ res + inst.lam * s.sum(), rel=1e-10)
+    assert int(g["stats"][0]) == int(np.argmin(g["energies"]))
+    assert oracle.rmse(g["x_hat"], inst.x0) < 0.05
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """A grid barrier that waits for CTAs that never arrive runs into timeout_ms,
+    the solve reports CS_ETIMEOUT, and the next solve on the same problem works."""
+    w = cs_inputs.workload("single_n200_fp64", n_outer=1, n_steps=50)
+    inst = cs_inputs.workload_instance(w)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        bad = cs.params_from_workload(w, timeout_ms=200, test_phantom_ctas=1)
+        cs.cs_solve(h, bad, 1)
+        with pytest.raises(cs.CSError) as ei:
+            cs.cs_result(h)
+        assert ei.value.status == cs.CS_ETIMEOUT
+        cs.cs_solve(h, cs.params_from_workload(w), 1)
+        x, s, E, st, status = cs.cs_result(h)
+        assert status == cs.CS_OK and np.isfinite(E)
+    finally:
+        cs.cs_problem_destroy(h)
+    torch.cuda.synchronize()
