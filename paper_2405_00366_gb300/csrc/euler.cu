@@ -13,16 +13,18 @@
 //       q_r = (sqrt tau / 2) R_r (A^T y)_r - theta
 // with theta = sqrt(tau) eta^2 / 4 (Eq. MFZlocalfieldmain).
 //
-// Work split: CTA b owns rows [b*RB, (b+1)*RB) of G_off, which it keeps in
-// shared memory for the whole run (loaded once), together with its rows of the
-// state c, e, b.  Each step every CTA reads all of X (N x T) from L2, forms its
+// Work split: CTA b owns a block of rows of G_off, which it keeps in shared
+// memory for the whole run (loaded once), and the same rows of the state c, e,
+// b.  Each step every CTA streams all of X (N x T) from L2 into shared memory
+// with bulk copies (each warp double-buffers its own run of k-rows), forms its
 // rows of U with FP32 (or FP64) FMAs, updates its rows of c and e, writes its
 // rows of the next X, and meets the other CTAs at a bounded grid barrier.  X is
-// double-buffered, so one barrier per step suffices.
+// double-buffered in global memory, so one barrier per step suffices.
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace cs {
 
@@ -31,6 +33,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTChunk = 64;  // trials per pass of the product
+constexpr int kChunkQuads = 4;  // k-quads (16 rows of X) per bulk copy
+
+__host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 template <typename CT>
 struct EulerArgs {
@@ -104,44 +109,100 @@ __device__ __forceinline__ void load4<float, __half>(const __half* p, float out[
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
-// U[r][tt] = sum_k Gsm[r][k] X[k][t0 + tt] for r < nr, tt < tc, written to the
-// reduction buffer `red` as the per-warp partials [w][r][tt]; the caller sums
-// over w.  Threads split k (in quads of 4) and t; lanes along t read X
-// coalesced, lanes along k read consecutive G quads.
+// Offset of element (r, t) of a coupling operand X.  X is stored in blocks of
+// kTChunk trials: block tc holds trials [64 tc, 64 tc + tw) as an Npad x tw
+// row-major matrix, so any run of k-rows of one block is contiguous in memory
+// and can be moved by one bulk copy.
+__device__ __forceinline__ size_t xoff(int r, int t, int T, int Npad) {
+  const int tc = t / kTChunk, tt = t % kTChunk;
+  const int tw = min(kTChunk, T - tc * kTChunk);
+  return (size_t)tc * Npad * kTChunk + (size_t)r * tw + tt;
+}
+
+// Per-warp partial products of one block of trials:
+//   U[r][tt] = sum_k Gsm[r][k] X[k][tt],  r < nr, tt < tw,
+// with the k range split into one contiguous run of k-quads per warp.  Each
+// warp streams its run of X through two private shared-memory slots: lane 0
+// issues a bulk copy of the next chunk (kChunkQuads quads of k-rows) while the
+// warp computes on the current one, completion signalled by the slot's
+// mbarrier.  Lanes split (t, k); lanes along t read X conflict-free, lanes
+// along k read consecutive quads of the G row.  On return the per-warp
+// partials are in `red` as [w][r][tt] (red aliases the slot ring, so the
+// whole CTA synchronises first).  Returns false if a copy wait timed out.
 template <typename GT, typename CT, int RB>
-__device__ __forceinline__ void product_partials(const GT* __restrict__ Gsm, int ldg, const CT* __restrict__ X,
-                                                 int T, int t0, int tc, int nr, int Npad, CT* red) {
-  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+__device__ __forceinline__ bool product_partials(const GT* __restrict__ Gsm, int Npad, const CT* __restrict__ Xblk,
+                                                 int tw, int nr, CT* ring, uint64_t* bars, unsigned& phases,
+                                                 long long timeout_cycles, int* err, CT* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   int TL = 1;
-  while (TL < tc && TL < 32) TL <<= 1;
+  while (TL < tw && TL < 32) TL <<= 1;
   const int KL = 32 / TL;
   const int tl = l % TL, kl = l / TL;
-  const int KS = kWarps * KL;
+  const bool okA = tl < tw, okB = (tl + TL) < tw;
   const int nq = Npad >> 2;
-  const int tA = t0 + tl, tB = t0 + tl + TL;
-  const bool okA = tl < tc, okB = (tl + TL) < tc;
+  const int qb = (int)((long long)nq * w / kWarps), qe = (int)((long long)nq * (w + 1) / kWarps);
+  const int nch = (qe - qb + kChunkQuads - 1) / kChunkQuads;
+  const size_t slot_elems = (size_t)kChunkQuads * 4 * tw;
+  CT* wslots = ring + (size_t)w * 2 * slot_elems;
+  uint64_t* wb = bars + 2 * w;
+  int issued = 0;
+  auto issue = [&](int ci) {
+    const int q0 = qb + ci * kChunkQuads;
+    const int cq = min(kChunkQuads, qe - q0);
+    const unsigned bytes = (unsigned)((size_t)cq * 4 * tw * sizeof(CT));
+    const int s = ci & 1;
+    mbar_arrive_expect_tx(wb + s, bytes);
+    bulk_copy_g2s(wslots + s * slot_elems, Xblk + (size_t)q0 * 4 * tw, bytes, wb + s);
+  };
+  if (l == 0) {
+    fence_proxy_async_global();
+    fence_proxy_async_shared();
+    if (nch > 0) issue(0);
+    if (nch > 1) issue(1);
+  }
+  issued = min(nch, 2);
   CT acc[RB][2];
 #pragma unroll
   for (int r = 0; r < RB; ++r) { acc[r][0] = CT(0); acc[r][1] = CT(0); }
-  for (int q = w * KL + kl; q < nq; q += KS) {
-    CT xa[4], xb[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const size_t row = (size_t)(4 * q + j) * T;
-      xa[j] = okA ? __ldcg(X + row + tA) : CT(0);
-      xb[j] = okB ? __ldcg(X + row + tB) : CT(0);
+  bool ok = true;
+  for (int ci = 0; ci < issued; ++ci) {
+    const int s = ci & 1;
+    const bool got = mbar_wait(wb + s, (phases >> s) & 1u, timeout_cycles);
+    phases ^= 1u << s;
+    if (!got) {
+      ok = false;
+      if (l == 0) set_error(err, DEV_TIMEOUT);
     }
+    if (ok) {
+      const CT* xs = wslots + s * slot_elems;
+      const int q0 = qb + ci * kChunkQuads;
+      const int cq = min(kChunkQuads, qe - q0);
+      for (int j = kl; j < cq; j += KL) {
+        CT xa[4], xb[4];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      if (r < nr) {
-        CT gv[4];
-        load4<CT, GT>(Gsm + (size_t)r * ldg + 4 * q, gv);
+        for (int jj = 0; jj < 4; ++jj) {
+          xa[jj] = okA ? xs[(4 * j + jj) * tw + tl] : CT(0);
+          xb[jj] = okB ? xs[(4 * j + jj) * tw + tl + TL] : CT(0);
+        }
+        const GT* gq = Gsm + 4 * (q0 + j);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[r][0] = fma(gv[j], xa[j], acc[r][0]);
-          acc[r][1] = fma(gv[j], xb[j], acc[r][1]);
+        for (int r = 0; r < RB; ++r) {
+          if (r < nr) {
+            CT gv[4];
+            load4<CT, GT>(gq + (size_t)r * Npad, gv);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              acc[r][0] = fma(gv[jj], xa[jj], acc[r][0]);
+              acc[r][1] = fma(gv[jj], xb[jj], acc[r][1]);
+            }
+          }
         }
       }
+    }
+    __syncwarp();
+    if (ok && ci + 2 < nch) {
+      if (l == 0) issue(ci + 2);
+      issued = ci + 3;
     }
   }
   // reduce over the k-lanes of the warp
@@ -152,39 +213,52 @@ __device__ __forceinline__ void product_partials(const GT* __restrict__ Gsm, int
       acc[r][1] += __shfl_xor_sync(0xffffffffu, acc[r][1], o);
     }
   }
+  __syncthreads();  // every warp is done with its slots: red may overwrite the ring
   if (kl == 0) {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       if (r < nr) {
-        if (okA) red[(w * RB + r) * kTChunk + tl] = acc[r][0];
-        if (okB) red[(w * RB + r) * kTChunk + tl + TL] = acc[r][1];
+        if (okA) red[(w * RB + r) * tw + tl] = acc[r][0];
+        if (okB) red[(w * RB + r) * tw + tl + TL] = acc[r][1];
       }
     }
   }
+  __syncthreads();
+  return ok;
 }
 
 template <typename GT, typename CT, int RB>
 __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int N = a.N, T = a.T, Npad = a.Npad;
   const int r0 = blockIdx.x * a.rows_per_cta;
   const int nr = max(0, min(a.rows_per_cta, N - r0));
+  const int twmax = min(T, kTChunk);
   GT* Gsm = reinterpret_cast<GT*>(smem_raw);
-  CT* red = reinterpret_cast<CT*>(smem_raw + (((size_t)RB * Npad * sizeof(GT) + 15) & ~(size_t)15));
+  const size_t g_bytes = align128((size_t)a.rows_per_cta * Npad * sizeof(GT));
+  CT* ring = reinterpret_cast<CT*>(smem_raw + g_bytes);
+  const size_t ring_bytes = align128((size_t)kWarps * 2 * kChunkQuads * 4 * twmax * sizeof(CT));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + g_bytes + ring_bytes);
+  CT* red = ring;
 
-  // Stage this CTA's rows of G_off (zero rows past the end).
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * kWarps; ++i) mbar_init(bars + i, 1);
+    fence_mbar_init();
+  }
+  // Stage this CTA's rows of G_off.
   {
     const GT* src = reinterpret_cast<const GT*>(a.Gs);
     const int per = (int)(16 / sizeof(GT));
     const int vec_per_row = Npad / per;
-    const int total = RB * vec_per_row;
+    const int total = nr * vec_per_row;
     for (int v = threadIdx.x; v < total; v += kThreads) {
       const int r = v / vec_per_row, cv = v % vec_per_row;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (r < nr) val = *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * Npad + cv * per);
-      *reinterpret_cast<uint4*>(Gsm + (size_t)r * Npad + cv * per) = val;
+      *reinterpret_cast<uint4*>(Gsm + (size_t)r * Npad + cv * per) =
+          *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * Npad + cv * per);
     }
   }
+  __syncthreads();
+  unsigned phases = 0;
   const double st = sqrt(a.tau);
   const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
   unsigned bar_k = 0;
@@ -193,22 +267,24 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   if (a.field == CS_FIELD_CN) {
     for (int idx = threadIdx.x; idx < nr * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
-      a.X0[(size_t)(r0 + r) * T + t] = CT(a.R[(size_t)(r0 + r) * T + t]);
+      a.X0[xoff(r0 + r, t, T, Npad)] = CT(a.R[(size_t)(r0 + r) * T + t]);
     }
+    fence_proxy_async_global();
     if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) return;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tc = min(kTChunk, T - t0);
-      product_partials<GT, CT, RB>(Gsm, Npad, a.X0, T, t0, tc, nr, Npad, red);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * tc; idx += kThreads) {
-        const int r = idx / tc, tt = idx % tc;
+      const int tw = min(kTChunk, T - t0);
+      product_partials<GT, CT, RB>(Gsm, Npad, a.X0 + (size_t)t0 * Npad, tw, nr, ring, bars, phases,
+                                   a.timeout_cycles, a.err, red);
+      for (int idx = threadIdx.x; idx < nr * tw; idx += kThreads) {
+        const int r = idx / tw, tt = idx % tw;
         CT v = CT(0);
-        for (int w = 0; w < kWarps; ++w) v += red[(w * RB + r) * kTChunk + tt];
+        for (int w = 0; w < kWarps; ++w) v += red[(w * RB + r) * tw + tt];
         const size_t o = (size_t)(r0 + r) * T + t0 + tt;
         const double Rr = a.R[o];
         const double bb = Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[r0 + r]) - a.theta;
         a.b[o] = CT(bb);
       }
+      fence_proxy_async_shared();
       __syncthreads();
     }
   } else {
@@ -226,8 +302,9 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     a.c[o] = c0;
     a.e[o] = CT(1);
     const CT Rr = CT(a.R[o]);
-    a.X1[o] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+    a.X1[xoff(r0 + r, t, T, Npad)] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
   }
+  fence_proxy_async_global();
   if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) return;
 
   // ---- Euler steps
@@ -239,13 +316,14 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     const bool last = (n + 1 == a.n_steps);
     const bool rec = n < a.record_steps;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tc = min(kTChunk, T - t0);
-      product_partials<GT, CT, RB>(Gsm, Npad, Xc, T, t0, tc, nr, Npad, red);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * tc; idx += kThreads) {
-        const int r = idx / tc, tt = idx % tc;
+      const int tw = min(kTChunk, T - t0);
+      product_partials<GT, CT, RB>(Gsm, Npad, Xc + (size_t)t0 * Npad, tw, nr, ring, bars, phases,
+                                   a.timeout_cycles, a.err, red);
+      CT* Xnb = Xn + (size_t)t0 * Npad;
+      for (int idx = threadIdx.x; idx < nr * tw; idx += kThreads) {
+        const int r = idx / tw, tt = idx % tw;
         CT U = CT(0);
-        for (int w = 0; w < kWarps; ++w) U += red[(w * RB + r) * kTChunk + tt];
+        for (int w = 0; w < kWarps; ++w) U += red[(w * RB + r) * tw + tt];
         const size_t o = (size_t)(r0 + r) * T + t0 + tt;
         const CT Rr = CT(a.R[o]);
         const CT f = wcoef * Rr * U + a.b[o];
@@ -255,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
         a.c[o] = cn;
         a.e[o] = en;
-        Xn[o] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        Xnb[(size_t)(r0 + r) * tw + tt] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
         if (rec) {
           const size_t ro = (size_t)n * N * T + o;
           a.rec_c[ro] = (double)cn;
@@ -263,6 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         }
         if (last) a.sigma[o] = cn > CT(0) ? 1 : 0;
       }
+      // the next X is read by bulk copies (async proxy) after the grid barrier, and
+      // the ring that held `red` is refilled by bulk copies
+      fence_proxy_async_global();
+      fence_proxy_async_shared();
       __syncthreads();
     }
     if (last) break;
@@ -291,8 +373,10 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
   a.bar = S.bar; a.err = S.err; a.timeout_cycles = timeout_cycles;
   a.phantom = (unsigned)prm.test_phantom_ctas;
 
-  const size_t smem = (((size_t)RB * P.Npad * sizeof(GT) + 15) & ~(size_t)15) +
-                      (size_t)kWarps * RB * kTChunk * sizeof(CT);
+  const int twmax = std::min(S.trials, kTChunk);
+  const size_t smem = align128((size_t)rows_per_cta * P.Npad * sizeof(GT)) +
+                      align128((size_t)kWarps * 2 * kChunkQuads * 4 * twmax * sizeof(CT)) +
+                      2 * kWarps * sizeof(uint64_t);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;  // rows of G_off do not fit on chip
   auto fn = euler_kernel<GT, CT, RB>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
