@@ -36,8 +36,10 @@ Readings where the paper is silent (each one is listed in the design doc):
   instance, trial, outer iteration, spin).
 * Trials are independent alternating runs; the kept result is the trial of
   lowest energy, ties going to the lower trial index.
-* A singular or indefinite G_SS (e.g. |S| >= M) is solved with a ridge
-  G_SS + eps I, eps = 1e-10 * mean(G_rr over S), and flagged.
+* G_SS counts as singular when a Cholesky pivot L_jj^2 is not above
+  1e-12 G_jj (for |S| > M the exact pivots are zero and rounding alone would
+  decide); it is then solved with a ridge G_SS + eps I,
+  eps = 1e-10 * mean(G_rr over S), and flagged.
 
 Pins: tests/test_oracle_pins.py checks this module against the brute-force
 minimum over all supports, exact noise-free recovery, the separable case
@@ -255,6 +257,22 @@ def cim_run(Goff, hz, R, eta, prm: Params, outer: int, inst: int = 0,
 
 
 # ---------------------------------------------------------------- the CDP refit
+PIVOT_TOL = 1e-12
+
+
+def _cholesky(Gss):
+    """Lower Cholesky factor of Gss, or None when a pivot L_jj^2 is not above
+    PIVOT_TOL * Gss_jj (numerically singular: e.g. |S| > M, where the exact pivots
+    are zero and only rounding decides their sign)."""
+    try:
+        L = np.linalg.cholesky(Gss)
+    except np.linalg.LinAlgError:
+        return None
+    if not np.all(np.diag(L) ** 2 > PIVOT_TOL * np.diag(Gss)):
+        return None
+    return L
+
+
 def refit_exact(G, hz, g, sigma):
     """R minimising 1/2||y - A(sigma o R)||^2 on S = {r : sigma_r = 1}; Jacobi fixed point off S.
 
@@ -266,11 +284,12 @@ def refit_exact(G, hz, g, sigma):
     singular = False
     if S.size:
         Gss = G[np.ix_(S, S)]
-        try:
-            L = np.linalg.cholesky(Gss)
-        except np.linalg.LinAlgError:
+        L = _cholesky(Gss)
+        if L is None:
             singular = True
-            L = np.linalg.cholesky(Gss + 1e-10 * np.mean(g[S]) * np.eye(S.size))
+            L = _cholesky(Gss + 1e-10 * np.mean(g[S]) * np.eye(S.size))
+            if L is None:
+                raise np.linalg.LinAlgError("ridge refit failed")
         z = scipy.linalg.solve_triangular(L, hz[S], lower=True)
         RS = scipy.linalg.solve_triangular(L.T, z, lower=False)
         R[S] = RS

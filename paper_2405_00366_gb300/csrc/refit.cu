@@ -6,7 +6,8 @@
 // Cholesky factorisation; off the support R_r is the Jacobi fixed point
 // (h^z_r - sum_{r' in S} G_rr' R_r') / G_rr, so R is defined for every r (the
 // local field of Eq. localfieldMFZ needs R_r' for every r').  A factorisation
-// that meets a non-positive pivot is redone on G_SS + eps I with
+// that meets a pivot not above 1e-12 times its diagonal entry (numerically
+// singular G_SS, e.g. |S| > M) is redone on G_SS + eps I with
 // eps = 1e-10 * mean(G_rr over S) and the solve is flagged.
 #include "common.cuh"
 #include "internal.h"
@@ -46,16 +47,19 @@ __device__ int support_list(const uint8_t* __restrict__ sigma, int N, int T, int
 }
 
 // In-place Cholesky of the n x n matrix W (lower triangle, column-major:
-// element (i, k) at W[k * n + i]), right-looking.  Returns false on a
-// non-positive or non-finite pivot.
-__device__ bool cholesky_lower(double* W, int n) {
+// element (i, k) at W[k * n + i]), right-looking.  Returns false when a pivot
+// is not above kPivotTol times the matrix's own diagonal entry (diag[j]) or is
+// not finite: the matrix is then numerically singular.
+constexpr double kPivotTol = 1e-12;
+
+__device__ bool cholesky_lower(double* W, int n, const double* diag) {
   __shared__ int ok_s;
   const int tid = threadIdx.x;
   for (int j = 0; j < n; ++j) {
     double* colj = W + (size_t)j * n;
     if (tid == 0) {
       const double d = colj[j];
-      ok_s = (d > 0.0 && isfinite(d)) ? 1 : 0;
+      ok_s = (d > kPivotTol * diag[j] && isfinite(d)) ? 1 : 0;
       if (ok_s) colj[j] = sqrt(d);
     }
     __syncthreads();
@@ -114,6 +118,7 @@ __global__ void __launch_bounds__(kRefitThreads) refit_exact_kernel(
   }
   double* W = work + (size_t)t * work_stride;
   double* x = W + (size_t)n * n;
+  double* dg = x + n;  // diagonal of the matrix being factorised
   __shared__ double ridge_s;
   if (threadIdx.x == 0) ridge_s = 0.0;
   __syncthreads();
@@ -123,8 +128,9 @@ __global__ void __launch_bounds__(kRefitThreads) refit_exact_kernel(
       const int k = (int)(e / n), i = (int)(e % n);
       if (i >= k) W[e] = G[(size_t)idx[i] * N + idx[k]] + (i == k ? ridge : 0.0);
     }
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) dg[i] = G[(size_t)idx[i] * N + idx[i]] + ridge;
     __syncthreads();
-    if (cholesky_lower(W, n)) break;
+    if (cholesky_lower(W, n, dg)) break;
     if (attempt == 1) { if (threadIdx.x == 0) set_error(err, DEV_NONFINITE); return; }
     // ridge eps = 1e-10 * mean(g_S)
     __shared__ double red_s[kRefitThreads / 32];

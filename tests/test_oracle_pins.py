@@ -158,6 +158,7 @@ def test_refit_singular_support_uses_ridge():
     G, hz, g = oracle.gram(inst.A, inst.y)
     sigma = np.ones(40, dtype=np.uint8)  # |S| = 40 > M = 10: G_SS has rank 10
     R, singular = oracle.refit_exact(G, hz, g, sigma)
+    assert singular
     assert np.all(np.isfinite(R))
     # the ridge solution interpolates y (residual ~ 0) like the minimum-norm solution
     assert np.linalg.norm(inst.y - inst.A @ R) < 1e-4 * np.linalg.norm(inst.y)
