@@ -78,6 +78,8 @@ typedef struct {
   int64_t timeout_ms;   /* bound on every device-side wait (grid barrier) */
   int32_t test_phantom_ctas; /* test hook: the grid barrier also waits for this many CTAs that
                                 do not exist, so it runs into timeout_ms; 0 in normal use */
+  int32_t cluster_size; /* CTAs per thread-block cluster of the Euler kernel: 0 = chosen by the
+                           library's planner, or 1, 2, 4, 8 */
 } cs_params;
 
 typedef struct cs_problem cs_problem;
@@ -111,9 +113,10 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
  * receives CS_STATS_LEN doubles:
  *   [0] kept trial index  [1] |sigma_hat|  [2] 1 if a refit used the ridge
  *   [3] device error word (0 = none)       [4] trials  [5] N  [6] M
+ *   [7] energy of the kept trial  [8] cluster size and [9] CTAs of the Euler kernel
  * Host pointers.  Returns CS_ETIMEOUT if a device wait timed out,
  * CS_ESINGULAR (with valid outputs) if the ridge was needed. */
-#define CS_STATS_LEN 8
+#define CS_STATS_LEN 10
 cs_status cs_result(cs_problem* p, double* x_hat, uint8_t* sigma_hat, double* energy,
                     double* stats);
 

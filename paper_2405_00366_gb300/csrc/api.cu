@@ -72,7 +72,7 @@ cudaError_t alloc(T** p, size_t elems) {
 }
 
 void free_solve(SolveDev& S, cudaStream_t st) {
-  void* ptrs[] = {S.R, S.c, S.e, S.b, S.X0, S.X1, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
+  void* ptrs[] = {S.R, S.X0, S.X1, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
                   S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular};
   for (void* q : ptrs) dev_free(q, st);
   S = SolveDev();
@@ -97,13 +97,11 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     const size_t N = (size_t)P.N, Np = (size_t)P.Npad, T = (size_t)trials;
     const size_t cb = compute_bytes(prm.precision);
     CS_CUDA(alloc(&S.R, N * T), "cudaMalloc R");
-    CS_CUDA(dev_alloc(&S.c, N * T * cb, P.stream), "cudaMalloc c");
-    CS_CUDA(dev_alloc(&S.e, N * T * cb, P.stream), "cudaMalloc e");
-    CS_CUDA(dev_alloc(&S.b, N * T * cb, P.stream), "cudaMalloc b");
-    CS_CUDA(dev_alloc(&S.X0, Np * T * cb, P.stream), "cudaMalloc X0");
-    CS_CUDA(dev_alloc(&S.X1, Np * T * cb, P.stream), "cudaMalloc X1");
-    CS_CUDA(cudaMemsetAsync(S.X0, 0, Np * T * cb, P.stream), "memset X0");
-    CS_CUDA(cudaMemsetAsync(S.X1, 0, Np * T * cb, P.stream), "memset X1");
+    const size_t T4 = (T + 3) / 4 * 4;
+    CS_CUDA(dev_alloc(&S.X0, Np * T4 * cb, P.stream), "cudaMalloc X0");
+    CS_CUDA(dev_alloc(&S.X1, Np * T4 * cb, P.stream), "cudaMalloc X1");
+    CS_CUDA(cudaMemsetAsync(S.X0, 0, Np * T4 * cb, P.stream), "memset X0");
+    CS_CUDA(cudaMemsetAsync(S.X1, 0, Np * T4 * cb, P.stream), "memset X1");
     CS_CUDA(alloc(&S.sigma, N * T), "cudaMalloc sigma");
     CS_CUDA(alloc(&S.energy, T), "cudaMalloc energy");
     CS_CUDA(alloc(&S.ssize, (size_t)prm.n_outer * T), "cudaMalloc ssize");
@@ -146,6 +144,9 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
   if (p->timeout_ms <= 0) return fail(CS_EINVAL, "timeout_ms must be > 0");
   if (p->test_phantom_ctas < 0 || p->test_phantom_ctas > 1024) return fail(CS_EINVAL, "bad test_phantom_ctas");
+  if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
+      p->cluster_size != 8)
+    return fail(CS_EINVAL, "cluster_size must be 0 (automatic), 1, 2, 4 or 8");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -294,7 +295,8 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
     if (e == cudaErrorInvalidConfiguration)
       return fail(CS_EINVAL, "N too large for the on-chip Euler kernel at this precision");
-    CS_CUDA(e, "euler launch");
+    if (e != cudaSuccess)
+      return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
     CS_CUDA(mark(p, TM_EULER, false), "event");
     CS_CUDA(mark(p, TM_REFIT, true), "event");
     CS_CUDA(launch_refit(P, S, *prm, i), "refit launch");
@@ -314,7 +316,9 @@ static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   if (!p->S.done) return fail(CS_ENOTREADY, "no solve queued on this problem");
   CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
   double st[CS_STATS_LEN];
-  CS_CUDA(cudaMemcpy(st, p->S.stats, sizeof(st), cudaMemcpyDeviceToHost), "copy stats");
+  CS_CUDA(cudaMemcpy(st, p->S.stats, 8 * sizeof(double), cudaMemcpyDeviceToHost), "copy stats");
+  st[8] = p->S.plan_cluster;
+  st[9] = p->S.plan_ctas;
   if (stats_out) std::memcpy(stats_out, st, sizeof(st));
   const int err = (int)st[3];
   if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a grid barrier timed out");

@@ -13,39 +13,56 @@
 //       q_r = (sqrt tau / 2) R_r (A^T y)_r - theta
 // with theta = sqrt(tau) eta^2 / 4 (Eq. MFZlocalfieldmain).
 //
-// Work split: CTA b owns a block of rows of G_off, which it keeps in shared
-// memory for the whole run (loaded once), and the same rows of the state c, e,
-// b.  Each step every CTA streams all of X (N x T) from L2 into shared memory
-// with bulk copies (each warp double-buffers its own run of k-rows), forms its
-// rows of U with FP32 (or FP64) FMAs, updates its rows of c and e, writes its
-// rows of the next X, and meets the other CTAs at a bounded grid barrier.  X is
-// double-buffered in global memory, so one barrier per step suffices.
+// Work split (2-D, over thread-block clusters of C CTAs):
+//  * cluster c owns rows [c*RPC, (c+1)*RPC) of G_off; CTA rank j of the cluster
+//    owns the j-th 1/C of the k range, so its block of G_off (RPC x N/C) stays
+//    in shared memory for the whole run;
+//  * each step, a producer warp streams this CTA's k rows of X (N/C x T) from
+//    L2 into a shared-memory ring with bulk copies (mbarrier full/empty
+//    handshake), while eight consumer warps form RPC x T partial products;
+//  * the C partials of a row are summed through distributed shared memory:
+//    CTA j reduces and updates rows [j*RPC/C, (j+1)*RPC/C) of its cluster,
+//    whose c, e, b stay in its shared memory, and writes their next X;
+//  * all CTAs then meet at a bounded grid barrier; X is double-buffered in
+//    global memory, so one barrier per step suffices.
+// Versus every CTA reading all of X, the cluster cuts the L2 -> SM traffic of
+// X by C.  C = 1 is the plain row-block split.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
 #include "tma.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace cs {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kTChunk = 64;  // trials per pass of the product
-constexpr int kChunkQuads = 4;  // k-quads (16 rows of X) per bulk copy
+constexpr int kConsumerWarps = 8;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
+constexpr int kTChunk = 64;                          // trials per block of X
+constexpr int kMaxRowsPerLane = 8;                   // accumulator rows per lane
 
 __host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ __forceinline__ int round4(int v) { return (v + 3) & ~3; }
 
 template <typename CT>
 struct EulerArgs {
-  int N, Npad, T, rows_per_cta;
+  int N, Npad, T;
+  int C;        // CTAs per cluster
+  int RPC;      // rows of G_off per cluster
+  int ORW;      // rows reduced and updated per CTA (RPC / C rounded up)
+  int kq;       // k-quads per CTA (the last rank may have fewer)
+  int kch;      // k rows per bulk copy (multiple of 4)
+  int slots;    // ring slots
+  int RW;       // rows per consumer warp (RG * MR; RPC_pad = 8 RW rows are staged)
+  int RPC_pad;  // staged rows per CTA (multiple of 8 RW >= RPC; padding rows are zero)
   const void* Gs;  // Npad x Npad storage-precision G_off
   const double* R;
   const double* hz;
-  CT* c;
-  CT* e;
-  CT* b;
   CT* X0;
   CT* X1;
   uint8_t* sigma;
@@ -68,11 +85,14 @@ struct EulerArgs {
   unsigned phantom;
 };
 
-__device__ __forceinline__ double pump_at(int n, int S, int kind, double p0, double p1, double p_thr,
-                                          double d, double dt, double t0, double width) {
-  if (kind == CS_PUMP_LINEAR) return p0 + (p1 - p0) * (double)n / (double)S;
-  const double t = (double)n * dt;
-  return (p_thr - d) + 2.0 * d / (1.0 + exp(-(t - t0) / width));
+// Pump rate at step n of a run of S steps, in the compute type: the linear ramp
+// p0 + (p1 - p0) n / S or the sigmoid of Eq. pumprateGACS at t = n dt.
+template <typename CT>
+__device__ __forceinline__ CT pump_at(int n, int S, int kind, double p0, double p1, double p_thr, double d, double dt,
+                                      double t0, double width) {
+  if (kind == CS_PUMP_LINEAR) return CT(p0) + CT(p1 - p0) * (CT(n) / CT(S));
+  const CT t = CT(n) * CT(dt);
+  return CT(p_thr - d) + CT(2.0 * d) / (CT(1) + exp(-(t - CT(t0)) / CT(width)));
 }
 
 // Four consecutive storage values widened to CT.
@@ -95,245 +115,274 @@ __device__ __forceinline__ void load4<double, double>(const double* p, double ou
 template <>
 __device__ __forceinline__ void load4<float, __nv_bfloat16>(const __nv_bfloat16* p, float out[4]) {
   const uint2 v = *reinterpret_cast<const uint2*>(p);
-  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&v.x);
-  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&v.y);
-  const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 template <>
 __device__ __forceinline__ void load4<float, __half>(const __half* p, float out[4]) {
   const uint2 v = *reinterpret_cast<const uint2*>(p);
-  const __half2 lo = *reinterpret_cast<const __half2*>(&v.x);
-  const __half2 hi = *reinterpret_cast<const __half2*>(&v.y);
-  const float2 a = __half22float2(lo), b = __half22float2(hi);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
-// Offset of element (r, t) of a coupling operand X.  X is stored in blocks of
-// kTChunk trials: block tc holds trials [64 tc, 64 tc + tw) as an Npad x tw
-// row-major matrix, so any run of k-rows of one block is contiguous in memory
-// and can be moved by one bulk copy.
-__device__ __forceinline__ size_t xoff(int r, int t, int T, int Npad) {
-  const int tc = t / kTChunk, tt = t % kTChunk;
-  const int tw = min(kTChunk, T - tc * kTChunk);
-  return (size_t)tc * Npad * kTChunk + (size_t)r * tw + tt;
+// X is stored in blocks of kTChunk trials: block t0 (t0 a multiple of 64) holds
+// trials [t0, t0 + tw) as an Npad x twp row-major matrix (twp = tw rounded up to
+// 4, padding columns zero), so any run of k rows of a block is contiguous and
+// moves with one bulk copy.
+__host__ __device__ __forceinline__ size_t xblock(int t0, int Npad) { return (size_t)t0 * Npad; }
+__host__ __device__ __forceinline__ int xwidth(int t0, int T) {
+  return round4(T - t0 < kTChunk ? T - t0 : kTChunk);
 }
 
-// Per-warp partial products of one block of trials:
-//   U[r][tt] = sum_k Gsm[r][k] X[k][tt],  r < nr, tt < tw,
-// with the k range split into one contiguous run of k-quads per warp.  Each
-// warp streams its run of X through two private shared-memory slots: lane 0
-// issues a bulk copy of the next chunk (kChunkQuads quads of k-rows) while the
-// warp computes on the current one, completion signalled by the slot's
-// mbarrier.  Lanes split (t, k); lanes along t read X conflict-free, lanes
-// along k read consecutive quads of the G row.  On return the per-warp
-// partials are in `red` as [w][r][tt] (red aliases the slot ring, so the
-// whole CTA synchronises first).  Returns false if a copy wait timed out.
-template <typename GT, typename CT, int RB>
-__device__ __forceinline__ bool product_partials(const GT* __restrict__ Gsm, int Npad, const CT* __restrict__ Xblk,
-                                                 int tw, int nr, CT* ring, uint64_t* bars, unsigned& phases,
-                                                 long long timeout_cycles, int* err, CT* red) {
+// Shared-memory layout of one CTA (byte offsets).
+struct Smem {
+  size_t g, ring, part, st, bars, total;
+};
+__host__ __device__ __forceinline__ Smem smem_layout(int RPC_pad, int kq, int slots, int kch, int twmax, int ORW,
+                                                     int T, size_t gbytes, size_t cbytes) {
+  const int RPC = RPC_pad;
+  Smem s;
+  s.g = 0;
+  s.ring = align128((size_t)RPC * kq * 4 * gbytes);
+  s.part = s.ring + align128((size_t)slots * kch * twmax * cbytes);
+  s.st = s.part + align128((size_t)RPC * twmax * cbytes);
+  s.bars = s.st + align128((size_t)4 * ORW * T * cbytes);
+  s.total = s.bars + 2 * (size_t)slots * sizeof(uint64_t);
+  return s;
+}
+
+// Partial products of this CTA's block for one block of trials:
+//   P[r][tt] = sum_{k in this CTA's range} G_off[row0 + r][k] X[k][tt].
+// Warp 8 (lane 0) streams the k rows of X through the ring; warps 0-7 compute.
+// `gctr` counts ring uses across calls so the mbarrier phases stay consistent.
+// Consumer lanes: CG = twp/4 (rounded up to a power of two) column groups of
+// four trials and RG = 32/CG row groups; a lane accumulates MR rows (its warp's
+// RW = RG * MR rows are interleaved over the row groups).  The inner loop loads
+// four k-rows of X and MR x 4 entries of G, then issues 16 MR independent FMAs.
+template <typename GT, typename CT, int MR>
+__device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
+                                                 const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
+                                                 CT* ring, CT* P, uint64_t* full, uint64_t* empty,
+                                                 unsigned& gctr) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  int TL = 1;
-  while (TL < tw && TL < 32) TL <<= 1;
-  const int KL = 32 / TL;
-  const int tl = l % TL, kl = l / TL;
-  const bool okA = tl < tw, okB = (tl + TL) < tw;
-  const int nq = Npad >> 2;
-  const int qb = (int)((long long)nq * w / kWarps), qe = (int)((long long)nq * (w + 1) / kWarps);
-  const int nch = (qe - qb + kChunkQuads - 1) / kChunkQuads;
-  const size_t slot_elems = (size_t)kChunkQuads * 4 * tw;
-  CT* wslots = ring + (size_t)w * 2 * slot_elems;
-  uint64_t* wb = bars + 2 * w;
-  int issued = 0;
-  auto issue = [&](int ci) {
-    const int q0 = qb + ci * kChunkQuads;
-    const int cq = min(kChunkQuads, qe - q0);
-    const unsigned bytes = (unsigned)((size_t)cq * 4 * tw * sizeof(CT));
-    const int s = ci & 1;
-    mbar_arrive_expect_tx(wb + s, bytes);
-    bulk_copy_g2s(wslots + s * slot_elems, Xblk + (size_t)q0 * 4 * tw, bytes, wb + s);
-  };
-  if (l == 0) {
-    fence_proxy_async_global();
-    fence_proxy_async_shared();
-    if (nch > 0) issue(0);
-    if (nch > 1) issue(1);
-  }
-  issued = min(nch, 2);
-  CT acc[RB][2];
-#pragma unroll
-  for (int r = 0; r < RB; ++r) { acc[r][0] = CT(0); acc[r][1] = CT(0); }
-  bool ok = true;
-  for (int ci = 0; ci < issued; ++ci) {
-    const int s = ci & 1;
-    const bool got = mbar_wait(wb + s, (phases >> s) & 1u, timeout_cycles);
-    phases ^= 1u << s;
-    if (!got) {
-      ok = false;
-      if (l == 0) set_error(err, DEV_TIMEOUT);
+  const int nch = (klen + a.kch - 1) / a.kch;
+  const int ldg = a.kq * 4;
+  if (w == kConsumerWarps) {
+    if (l == 0) {
+      fence_proxy_async_global();
+      for (int ci = 0; ci < nch; ++ci) {
+        const unsigned g = gctr + ci;
+        const int s = (int)(g % a.slots);
+        const unsigned u = g / a.slots;
+        if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
+          set_error(a.err, DEV_TIMEOUT);
+          break;
+        }
+        const int kr = min(a.kch, klen - ci * a.kch);
+        const unsigned bytes = (unsigned)((size_t)kr * twp * sizeof(CT));
+        mbar_arrive_expect_tx(full + s, bytes);
+        bulk_copy_g2s(ring + (size_t)s * a.kch * twp, Xblk + (size_t)(k0 + ci * a.kch) * twp, bytes, full + s);
+      }
     }
-    if (ok) {
-      const CT* xs = wslots + s * slot_elems;
-      const int q0 = qb + ci * kChunkQuads;
-      const int cq = min(kChunkQuads, qe - q0);
-      for (int j = kl; j < cq; j += KL) {
-        CT xa[4], xb[4];
+    gctr += nch;
+    return;
+  }
+  int CG = 1;
+  while (CG * 4 < twp) CG <<= 1;
+  const int RG = 32 / CG;
+  const int cgi = l % CG, rg = l / CG;
+  const bool colok = cgi * 4 < twp;
+  const int rbase = w * a.RW + rg;  // this lane's rows: rbase + RG * i, i < MR
+  CT acc[MR][4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          xa[jj] = okA ? xs[(4 * j + jj) * tw + tl] : CT(0);
-          xb[jj] = okB ? xs[(4 * j + jj) * tw + tl + TL] : CT(0);
-        }
-        const GT* gq = Gsm + 4 * (q0 + j);
+  for (int i = 0; i < MR; ++i)
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          if (r < nr) {
-            CT gv[4];
-            load4<CT, GT>(gq + (size_t)r * Npad, gv);
+    for (int q = 0; q < 4; ++q) acc[i][q] = CT(0);
+  bool ok = true;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok && colok) {
+      const CT* xs = ring + (size_t)s * a.kch * twp + cgi * 4;
+      const int kr = min(a.kch, klen - ci * a.kch);
+      const GT* gk = Gsm + (size_t)rbase * ldg + ci * a.kch;
+#pragma unroll 2
+      for (int kk = 0; kk < kr; kk += 4) {
+        CT xv[4][4], gv[MR][4];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              acc[r][0] = fma(gv[jj], xa[jj], acc[r][0]);
-              acc[r][1] = fma(gv[jj], xb[jj], acc[r][1]);
-            }
-          }
-        }
+        for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(kk + j) * twp, xv[j]);
+#pragma unroll
+        for (int i = 0; i < MR; ++i) load4<CT, GT>(gk + (size_t)(RG * i) * ldg + kk, gv[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][q] = fma(gv[i][j], xv[j][q], acc[i][q]);
       }
     }
     __syncwarp();
-    if (ok && ci + 2 < nch) {
-      if (l == 0) issue(ci + 2);
-      issued = ci + 3;
-    }
+    if (l == 0) mbar_arrive(empty + s);
   }
-  // reduce over the k-lanes of the warp
-  for (int o = TL; o < 32; o <<= 1) {
+  gctr += nch;
+  if (colok) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      acc[r][0] += __shfl_xor_sync(0xffffffffu, acc[r][0], o);
-      acc[r][1] += __shfl_xor_sync(0xffffffffu, acc[r][1], o);
-    }
-  }
-  __syncthreads();  // every warp is done with its slots: red may overwrite the ring
-  if (kl == 0) {
+    for (int i = 0; i < MR; ++i) {
+      const int r = rbase + RG * i;
+      if (r < nrows) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      if (r < nr) {
-        if (okA) red[(w * RB + r) * tw + tl] = acc[r][0];
-        if (okB) red[(w * RB + r) * tw + tl + TL] = acc[r][1];
+        for (int q = 0; q < 4; ++q) P[(size_t)r * twp + cgi * 4 + q] = acc[i][q];
       }
     }
   }
-  __syncthreads();
-  return ok;
 }
 
-template <typename GT, typename CT, int RB>
+template <typename GT, typename CT, int MR>
 __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = a.C;
+  const int j = (int)cluster.block_rank();
+  const int cl = blockIdx.x / C;
   const int N = a.N, T = a.T, Npad = a.Npad;
-  const int r0 = blockIdx.x * a.rows_per_cta;
-  const int nr = max(0, min(a.rows_per_cta, N - r0));
-  const int twmax = min(T, kTChunk);
-  GT* Gsm = reinterpret_cast<GT*>(smem_raw);
-  const size_t g_bytes = align128((size_t)a.rows_per_cta * Npad * sizeof(GT));
-  CT* ring = reinterpret_cast<CT*>(smem_raw + g_bytes);
-  const size_t ring_bytes = align128((size_t)kWarps * 2 * kChunkQuads * 4 * twmax * sizeof(CT));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + g_bytes + ring_bytes);
-  CT* red = ring;
+  const int row0 = cl * a.RPC;                     // first row of this cluster
+  const int nrows = max(0, min(a.RPC, N - row0));  // rows of this cluster
+  const int nq = Npad >> 2;
+  const int q0 = j * a.kq;
+  const int nqj = max(0, min(a.kq, nq - q0));      // k-quads of this CTA
+  const int k0 = q0 * 4, klen = nqj * 4;
+  const int own0 = j * a.ORW;                      // first owned row (cluster-local)
+  const int nown = max(0, min(a.ORW, nrows - own0));
+  const int twmax = round4(min(T, kTChunk));
+  const Smem L = smem_layout(a.RPC_pad, a.kq, a.slots, a.kch, twmax, a.ORW, T, sizeof(GT), sizeof(CT));
+  GT* Gsm = reinterpret_cast<GT*>(smem_raw + L.g);
+  CT* ring = reinterpret_cast<CT*>(smem_raw + L.ring);
+  CT* P = reinterpret_cast<CT*>(smem_raw + L.part);
+  CT* c_s = reinterpret_cast<CT*>(smem_raw + L.st);
+  CT* e_s = c_s + (size_t)a.ORW * T;
+  CT* b_s = e_s + (size_t)a.ORW * T;
+  CT* R_s = b_s + (size_t)a.ORW * T;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
+  uint64_t* empty = full + a.slots;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2 * kWarps; ++i) mbar_init(bars + i, 1);
+    for (int i = 0; i < a.slots; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, kConsumerWarps);
+    }
     fence_mbar_init();
   }
-  // Stage this CTA's rows of G_off.
+  // Stage this CTA's block of G_off: rows [row0, row0 + nrows), k in [k0, k0 + klen).
   {
     const GT* src = reinterpret_cast<const GT*>(a.Gs);
-    const int per = (int)(16 / sizeof(GT));
-    const int vec_per_row = Npad / per;
-    const int total = nr * vec_per_row;
+    const int ldg = a.kq * 4;
+    const int total = a.RPC_pad * nqj;
     for (int v = threadIdx.x; v < total; v += kThreads) {
-      const int r = v / vec_per_row, cv = v % vec_per_row;
-      *reinterpret_cast<uint4*>(Gsm + (size_t)r * Npad + cv * per) =
-          *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * Npad + cv * per);
+      const int r = v / nqj, q = v % nqj;
+      GT* d4 = Gsm + (size_t)r * ldg + 4 * q;
+      if (r < nrows) {
+        const GT* s4 = src + (size_t)(row0 + r) * Npad + k0 + 4 * q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d4[e] = s4[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d4[e] = GT(0.0f);
+      }
     }
   }
+  // owned R
+  for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
+    const int r = idx / T, t = idx % T;
+    R_s[idx] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
+  }
   __syncthreads();
-  unsigned phases = 0;
+  unsigned gctr = 0;
   const double st = sqrt(a.tau);
   const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
   unsigned bar_k = 0;
 
   // ---- prologue: b (or q), initial c and e, first X.
   if (a.field == CS_FIELD_CN) {
-    for (int idx = threadIdx.x; idx < nr * T; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
-      a.X0[xoff(r0 + r, t, T, Npad)] = CT(a.R[(size_t)(r0 + r) * T + t]);
+      const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
+      a.X0[xblock(t0, Npad) + (size_t)(row0 + own0 + r) * twp + (t - t0)] =
+          CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
     }
     fence_proxy_async_global();
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) return;
+    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tw = min(kTChunk, T - t0);
-      product_partials<GT, CT, RB>(Gsm, Npad, a.X0 + (size_t)t0 * Npad, tw, nr, ring, bars, phases,
-                                   a.timeout_cycles, a.err, red);
-      for (int idx = threadIdx.x; idx < nr * tw; idx += kThreads) {
+      const int tw = min(kTChunk, T - t0), twp = round4(tw);
+      cluster_partials<GT, CT, MR>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, ring, P, full, empty, gctr);
+      cluster.sync();
+      for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         CT v = CT(0);
-        for (int w = 0; w < kWarps; ++w) v += red[(w * RB + r) * tw + tt];
-        const size_t o = (size_t)(r0 + r) * T + t0 + tt;
-        const double Rr = a.R[o];
-        const double bb = Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[r0 + r]) - a.theta;
-        a.b[o] = CT(bb);
+        for (int jj = 0; jj < C; ++jj) v += cluster.map_shared_rank(P, jj)[(size_t)(own0 + r) * twp + tt];
+        const int gr = row0 + own0 + r;
+        const double Rr = a.R[(size_t)gr * T + t0 + tt];
+        b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
       }
-      fence_proxy_async_shared();
-      __syncthreads();
+      cluster.sync();
     }
   } else {
-    for (int idx = threadIdx.x; idx < nr * T; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
-      const size_t o = (size_t)(r0 + r) * T + t;
-      a.b[o] = CT((st / 2.0) * a.R[o] * a.hz[r0 + r] - a.theta);
+      const int gr = row0 + own0 + r;
+      b_s[idx] = CT((st / 2.0) * a.R[(size_t)gr * T + t] * a.hz[gr] - a.theta);
     }
   }
-  for (int idx = threadIdx.x; idx < nr * T; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
     const int r = idx / T, t = idx % T;
-    const size_t o = (size_t)(r0 + r) * T + t;
+    const int gr = row0 + own0 + r;
     const uint64_t key = run_key(a.seed, (uint64_t)a.instance, (uint64_t)t, (uint64_t)a.outer);
-    const CT c0 = CT(initial_amplitude(key, (uint64_t)(r0 + r), a.init_kind, a.init_scale));
-    a.c[o] = c0;
-    a.e[o] = CT(1);
-    const CT Rr = CT(a.R[o]);
-    a.X1[xoff(r0 + r, t, T, Npad)] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+    const CT c0 = CT(initial_amplitude(key, (uint64_t)gr, a.init_kind, a.init_scale));
+    c_s[idx] = c0;
+    e_s[idx] = CT(1);
+    const CT Rr = R_s[idx];
+    const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
+    a.X1[xblock(t0, Npad) + (size_t)gr * twp + (t - t0)] =
+        (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
   }
   fence_proxy_async_global();
-  if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) return;
+  if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
 
   // ---- Euler steps
   const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
   CT* Xc = a.X1;
   CT* Xn = a.X0;
   for (int n = 0; n < a.n_steps; ++n) {
-    const CT p = CT(pump_at(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width));
+    const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
     const bool last = (n + 1 == a.n_steps);
     const bool rec = n < a.record_steps;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tw = min(kTChunk, T - t0);
-      product_partials<GT, CT, RB>(Gsm, Npad, Xc + (size_t)t0 * Npad, tw, nr, ring, bars, phases,
-                                   a.timeout_cycles, a.err, red);
-      CT* Xnb = Xn + (size_t)t0 * Npad;
-      for (int idx = threadIdx.x; idx < nr * tw; idx += kThreads) {
+      const int tw = min(kTChunk, T - t0), twp = round4(tw);
+      cluster_partials<GT, CT, MR>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, ring, P, full, empty, gctr);
+      cluster.sync();
+      CT* Xnb = Xn + xblock(t0, Npad);
+      for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         CT U = CT(0);
-        for (int w = 0; w < kWarps; ++w) U += red[(w * RB + r) * tw + tt];
-        const size_t o = (size_t)(r0 + r) * T + t0 + tt;
-        const CT Rr = CT(a.R[o]);
-        const CT f = wcoef * Rr * U + a.b[o];
-        const CT cc = a.c[o], ee = a.e[o];
+        for (int jj = 0; jj < C; ++jj) U += cluster.map_shared_rank(P, jj)[(size_t)(own0 + r) * twp + tt];
+        const size_t so = (size_t)r * T + t0 + tt;
+        const CT Rr = R_s[so];
+        const CT f = wcoef * Rr * U + b_s[so];
+        const CT cc = c_s[so], ee = e_s[so];
         const CT c2 = cc * cc;
         const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
-        a.c[o] = cn;
-        a.e[o] = en;
-        Xnb[(size_t)(r0 + r) * tw + tt] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        c_s[so] = cn;
+        e_s[so] = en;
+        const int gr = row0 + own0 + r;
+        Xnb[(size_t)gr * twp + tt] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        const size_t o = (size_t)gr * T + t0 + tt;
         if (rec) {
           const size_t ro = (size_t)n * N * T + o;
           a.rec_c[ro] = (double)cn;
@@ -341,25 +390,149 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         }
         if (last) a.sigma[o] = cn > CT(0) ? 1 : 0;
       }
-      // the next X is read by bulk copies (async proxy) after the grid barrier, and
-      // the ring that held `red` is refilled by bulk copies
-      fence_proxy_async_global();
-      fence_proxy_async_shared();
-      __syncthreads();
+      // every CTA of the cluster has read this CTA's partials before they are rewritten
+      if (t0 + kTChunk < T) cluster.sync();
     }
     if (last) break;
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) return;
+    // the next X is read by bulk copies (async proxy) of every CTA after the barrier
+    fence_proxy_async_global();
+    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) break;
     CT* tmp = Xc; Xc = Xn; Xn = tmp;
+  }
+  cluster.sync();  // peers may still read this CTA's partials
+}
+
+thread_local const char* g_where = "";  // last CUDA call attempted by the launcher
+
+struct Plan {
+  int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, MR;
+  size_t smem;
+};
+
+template <typename CT>
+using EulerFn = void (*)(EulerArgs<CT>);
+
+template <typename GT, typename CT>
+EulerFn<CT> kernel_for(int MR) {
+  switch (MR) {
+    case 1: return euler_kernel<GT, CT, 1>;
+    case 2: return euler_kernel<GT, CT, 2>;
+    case 3: return euler_kernel<GT, CT, 3>;
+    case 4: return euler_kernel<GT, CT, 4>;
+    case 5: return euler_kernel<GT, CT, 5>;
+    case 6: return euler_kernel<GT, CT, 6>;
+    case 7: return euler_kernel<GT, CT, 7>;
+    default: return euler_kernel<GT, CT, 8>;
   }
 }
 
-template <typename GT, typename CT, int RB>
+// Work split for N and T on this GPU.  For each cluster size C in {1, 2, 4, 8}
+// (or only the caller's hint) take the largest number of clusters that is
+// resident at once with the footprint it implies (rows per lane MR, ring slots),
+// and keep the C with the lowest estimate of one step per CTA: FMAs at 128 per
+// clock, X bytes at 32 per clock, and a fixed cost per cluster rank for the
+// reduction through distributed shared memory.
+template <typename GT, typename CT>
+cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
+  const int N = (int)P.N, nq = (int)(P.Npad / 4);
+  const int twmax = round4(std::min(T, kTChunk));
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P.device);
+  if (e != cudaSuccess) { g_where = "cudaDeviceGetAttribute(optin)"; return e; }
+  int CG = 1;
+  while (CG * 4 < twmax) CG <<= 1;
+  const int RG = 32 / CG;
+  double best_cost = 0.0;
+  bool found = false;
+  Plan bp{};
+  const int cands[] = {1, 2, 4, 8};
+  for (int C : cands) {
+    if (hint > 0 && C != hint) continue;
+    if (C > nq) continue;
+    Plan pl{};
+    pl.C = C;
+    pl.kq = (nq + C - 1) / C;
+    pl.kch = std::max(4, std::min(pl.kq * 4, (int)((8192 / (twmax * sizeof(CT))) & ~(size_t)3)));
+    for (int NC = std::min(P.num_sms / C, N); NC >= 1; --NC) {
+      pl.RPC = (N + NC - 1) / NC;
+      pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
+      if (pl.NC != NC && NC != std::min(P.num_sms / C, N)) continue;
+      pl.MR = 0;
+      for (int mr = 1; mr <= kMaxRowsPerLane; ++mr)
+        if (kConsumerWarps * RG * mr >= pl.RPC) { pl.MR = mr; break; }
+      if (pl.MR == 0) break;  // fewer clusters only need more rows
+      pl.RW = RG * pl.MR;
+      pl.RPC_pad = kConsumerWarps * pl.RW;
+      pl.ORW = (pl.RPC + C - 1) / C;
+      EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR);
+      cudaFuncAttributes fa;
+      e = cudaFuncGetAttributes(&fa, fn);
+      if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
+      const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+      pl.slots = 0;
+      for (int slots = 8; slots >= 3; --slots) {
+        pl.smem = smem_layout(pl.RPC_pad, pl.kq, slots, pl.kch, twmax, pl.ORW, T, sizeof(GT), sizeof(CT)).total;
+        if (pl.smem <= cap) { pl.slots = slots; break; }
+      }
+      if (pl.slots == 0) break;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+      if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"; return e; }
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(NonPortableClusterSizeAllowed)"; return e; }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(C * pl.NC);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = pl.smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int maxc = 0;
+      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        maxc = 0;
+      }
+      if (pl.NC > maxc) continue;
+      const double fma = (double)pl.RPC_pad * pl.kq * 4 * T;
+      const double xbytes = (double)pl.kq * 4 * twmax * sizeof(CT) * ((T + kTChunk - 1) / kTChunk);
+      const double cost = fma / 128.0 + xbytes / 32.0 + 300.0 * C;
+      if (!found || cost < best_cost) {
+        best_cost = cost;
+        bp = pl;
+        found = true;
+      }
+      break;
+    }
+  }
+  if (!found) { g_where = "make_plan: no work split fits"; return cudaErrorInvalidConfiguration; }
+  *out = bp;
+  return cudaSuccess;
+}
+
+template <typename GT, typename CT>
 cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                         long long timeout_cycles, int rows_per_cta, int grid) {
+                         long long timeout_cycles) {
+  // plans depend only on (N, T, hint) for a given device and precision
+  static thread_local struct { int64_t N; int T, hint, dev; Plan pl; bool valid; } cache = {0, 0, 0, -1, {}, false};
+  Plan pl;
+  if (cache.valid && cache.N == P.N && cache.T == S.trials && cache.hint == prm.cluster_size &&
+      cache.dev == P.device) {
+    pl = cache.pl;
+  } else {
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, &pl);
+    if (e != cudaSuccess) return e;
+    cache.N = P.N; cache.T = S.trials; cache.hint = prm.cluster_size; cache.dev = P.device;
+    cache.pl = pl; cache.valid = true;
+  }
   EulerArgs<CT> a;
-  a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials; a.rows_per_cta = rows_per_cta;
+  a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials;
+  a.C = pl.C; a.RPC = pl.RPC; a.ORW = pl.ORW; a.kq = pl.kq; a.kch = pl.kch; a.slots = pl.slots; a.RW = pl.RW;
+  a.RPC_pad = pl.RPC_pad;
   a.Gs = P.Gs; a.R = S.R; a.hz = P.hz;
-  a.c = (CT*)S.c; a.e = (CT*)S.e; a.b = (CT*)S.b; a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
+  a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
   a.sigma = S.sigma;
   a.record_steps = (outer == 0) ? std::min(S.record_steps, prm.n_steps) : 0;
   a.rec_c = S.rec_c; a.rec_e = S.rec_e;
@@ -372,44 +545,50 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
   a.seed = prm.seed; a.instance = prm.instance; a.outer = outer;
   a.bar = S.bar; a.err = S.err; a.timeout_cycles = timeout_cycles;
   a.phantom = (unsigned)prm.test_phantom_ctas;
+  S.plan_cluster = pl.C;
+  S.plan_ctas = pl.C * pl.NC;
 
-  const int twmax = std::min(S.trials, kTChunk);
-  const size_t smem = align128((size_t)rows_per_cta * P.Npad * sizeof(GT)) +
-                      align128((size_t)kWarps * 2 * kChunkQuads * 4 * twmax * sizeof(CT)) +
-                      2 * kWarps * sizeof(uint64_t);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;  // rows of G_off do not fit on chip
-  auto fn = euler_kernel<GT, CT, RB>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(launch)"; return e; }
   e = cudaMemsetAsync(S.bar, 0, sizeof(unsigned), P.stream);
-  if (e != cudaSuccess) return e;
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, smem, P.stream);
-}
-
-template <typename GT, typename CT>
-cudaError_t launch_rb(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                      long long timeout_cycles) {
-  const int N = (int)P.N;
-  const int ctas = std::min(P.num_sms, N);
-  const int rows = (N + ctas - 1) / ctas;
-  const int grid = (N + rows - 1) / rows;
-  if (rows <= 2) return launch_typed<GT, CT, 2>(P, S, prm, outer, eta, timeout_cycles, rows, grid);
-  if (rows <= 4) return launch_typed<GT, CT, 4>(P, S, prm, outer, eta, timeout_cycles, rows, grid);
-  if (rows <= 8) return launch_typed<GT, CT, 8>(P, S, prm, outer, eta, timeout_cycles, rows, grid);
-  if (rows <= 16) return launch_typed<GT, CT, 16>(P, S, prm, outer, eta, timeout_cycles, rows, grid);
-  return cudaErrorInvalidConfiguration;  // N above 16 x SMs: not supported by this kernel
+  if (e != cudaSuccess) { g_where = "cudaMemsetAsync(barrier)"; return e; }
+  g_where = pl.C == 1 ? "cudaLaunchKernelEx(cooperative)" : "cudaLaunchKernelEx(cluster)";
+  // A cooperative launch guarantees that every CTA is resident, which the grid
+  // barrier needs; the runtime does not combine it with clusters, so a cluster
+  // launch relies on the planner keeping the grid within the resident cluster
+  // count (a shortfall would surface as CS_ETIMEOUT from the bounded barrier).
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  if (pl.C == 1) {
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+  } else {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = pl.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+  }
+  cfg.gridDim = dim3(pl.C * pl.NC);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = P.stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 }  // namespace
 
+const char* euler_last_call() { return g_where; }
+
 cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
                          long long timeout_cycles) {
   switch (prm.precision) {
-    case CS_P_FP64: return launch_rb<double, double>(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_FP32: return launch_rb<float, float>(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_BF16: return launch_rb<__nv_bfloat16, float>(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_FP16: return launch_rb<__half, float>(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_FP64: return launch_typed<double, double>(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_FP32: return launch_typed<float, float>(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_BF16: return launch_typed<__nv_bfloat16, float>(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_FP16: return launch_typed<__half, float>(P, S, prm, outer, eta, timeout_cycles);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,10 +44,7 @@ struct SolveDev {
   int trials = 0, n_outer = 0, record_steps = 0, precision = -1, cap_trials = 0, cap_outer = 0,
       cap_record = 0, cap_prec = -1;
   double* R = nullptr;          // N x T (FP64), refit signal
-  void* c = nullptr;            // N x T amplitudes (compute type)
-  void* e = nullptr;            // N x T error feedback
-  void* b = nullptr;            // N x T constant part of the injection
-  void* X0 = nullptr;           // Npad x T coupling operand, two buffers
+  void* X0 = nullptr;           // Npad x round4(T) coupling operand (blocks of 64 trials), two buffers
   void* X1 = nullptr;
   uint8_t* sigma = nullptr;     // N x T support
   double* energy = nullptr;     // T
@@ -64,6 +61,7 @@ struct SolveDev {
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
   bool done = false;
+  int plan_cluster = 0, plan_ctas = 0;  // work split of the last Euler launch
 };
 
 // Launchers (stream-ordered, no synchronisation).
@@ -71,6 +69,7 @@ cudaError_t launch_gram(const ProblemDev& P);
 cudaError_t launch_store_coupling(ProblemDev& P, int precision);
 cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer,
                          double eta, long long timeout_cycles);
+const char* euler_last_call();  // the CUDA call the last failing Euler launch stopped at
 cudaError_t launch_init_R(const ProblemDev& P, SolveDev& S);
 cudaError_t launch_refit(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer);
 cudaError_t launch_finish(const ProblemDev& P, SolveDev& S);
