@@ -145,6 +145,27 @@ cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g);
 #define CS_TIMING_LEN 4
 cs_status cs_problem_timing(cs_problem* p, double* ms, int64_t* launches);
 
+/* Per-trial objective E_t = 1/2 ||y - A (sigma_t o R_t)||^2 + lambda |sigma_t| in
+ * FP64, for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this entry point exists for callers that may not call
+ * cudaMalloc or any allocating routine, such as code running during CUDA graph
+ * capture, hosts that own all device memory through their own arena, or
+ * loops where an allocation is not allowed.  It allocates nothing.
+ *  A (M x N row-major), y (M), sigma (N x trials bytes, [r][t]), R (N x trials,
+ *  [r][t]) and energy (trials) are DEVICE pointers owned by the caller; the
+ *  kernel is queued on `stream` and the call returns without waiting.
+ *  Scratch: a fixed device array of 262144 int32 entries (1 MiB) inside the
+ *  library, held by every GPU that loads the library until exit; N * trials
+ *  must not exceed 262144 (CS_EINVAL otherwise).  Every call shares that array
+ *  and it keeps the last call's contents (each call writes every entry it
+ *  reads), so calls whose kernels overlap on the GPU (for example on two
+ *  streams) race and give wrong results; serialise them.
+ *  The first call on a device looks up the array's device address with that
+ *  device current; make that first call before any stream capture.
+ * Errors: CS_EINVAL (NULL pointer, sizes, lambda), CS_ECUDA (lookup or launch). */
+cs_status cs_objective_static(const double* A, const double* y, const uint8_t* sigma, const double* R, int64_t M,
+                              int64_t N, int32_t trials, double lambda, double* energy, void* stream);
+
 /* Sizes of a problem. */
 cs_status cs_problem_shape(const cs_problem* p, int64_t* M, int64_t* N);
 

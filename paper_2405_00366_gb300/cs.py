@@ -78,13 +78,15 @@ def lib():
         L.cs_trajectory.argtypes = [P, P, P]
         L.cs_problem_gram.argtypes = [P, P, P, P]
         L.cs_problem_timing.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+        L.cs_objective_static.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_double, P, P]
         L.cs_problem_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.cs_problem_destroy.argtypes = [P]
         L.cs_problem_destroy.restype = None
         L.cs_last_error.argtypes = []
         L.cs_last_error.restype = ctypes.c_char_p
         for name in ["cs_problem_create", "cs_solve", "cs_result", "cs_result_trials", "cs_trajectory",
-                     "cs_problem_gram", "cs_problem_shape", "cs_problem_timing"]:
+                     "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -204,6 +206,19 @@ def cs_problem_timing(problem):
     n = ctypes.c_int64()
     _check(lib().cs_problem_timing(problem, ms.ctypes.data, ctypes.byref(n)))
     return ms, n.value
+
+
+def cs_objective_static(A, y, sigma, R, lam: float, energy, stream=None) -> None:
+    """Per-trial objective into `energy` without any device allocation (see cs.h).
+    A (M, N), y (M,), R (N, T) float64, sigma (N, T) uint8 and energy (T,) float64
+    must be contiguous CUDA tensors; the work is queued on `stream`."""
+    M, N = (int(d) for d in A.shape)
+    T = int(R.shape[1])
+    for t in (A, y, sigma, R, energy):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("cs_objective_static takes contiguous CUDA tensors")
+    _check(lib().cs_objective_static(A.data_ptr(), y.data_ptr(), sigma.data_ptr(), R.data_ptr(), M, N, T,
+                                     float(lam), energy.data_ptr(), _stream_ptr(stream)))
 
 
 def cs_problem_shape(problem):

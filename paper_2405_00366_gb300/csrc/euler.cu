@@ -59,6 +59,7 @@ struct EulerArgs {
   int kch;      // k rows per bulk copy (multiple of 4)
   int slots;    // ring slots
   int RW;       // rows per consumer warp (RG * MR; RPC_pad = 8 RW rows are staged)
+  int RG;       // row groups of a warp
   int RPC_pad;  // staged rows per CTA (multiple of 8 RW >= RPC; padding rows are zero)
   const void* Gs;  // Npad x Npad storage-precision G_off
   const double* R;
@@ -158,9 +159,11 @@ __host__ __device__ __forceinline__ Smem smem_layout(int RPC_pad, int kq, int sl
 // Warp 8 (lane 0) streams the k rows of X through the ring; warps 0-7 compute.
 // `gctr` counts ring uses across calls so the mbarrier phases stay consistent.
 // Consumer lanes: CG = twp/4 (rounded up to a power of two) column groups of
-// four trials and RG = 32/CG row groups; a lane accumulates MR rows (its warp's
-// RW = RG * MR rows are interleaved over the row groups).  The inner loop loads
-// four k-rows of X and MR x 4 entries of G, then issues 16 MR independent FMAs.
+// four trials, RG row groups and KG = 32/(CG RG) k groups; a lane accumulates
+// MR rows x 4 trials (its warp's RW = RG * MR rows are interleaved over the row
+// groups) over every KG-th k-quad of each chunk, and the k groups are summed
+// with shuffles at the end.  The inner loop loads four k-rows of X and MR x 4
+// entries of G, then issues 16 MR independent FMAs.
 template <typename GT, typename CT, int MR>
 __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                  const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
@@ -191,8 +194,9 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
   }
   int CG = 1;
   while (CG * 4 < twp) CG <<= 1;
-  const int RG = 32 / CG;
-  const int cgi = l % CG, rg = l / CG;
+  const int RG = a.RG;             // row groups (power of two, CG * RG <= 32)
+  const int KG = 32 / (CG * RG);   // k groups: lanes that split the k rows of a chunk
+  const int cgi = l % CG, rg = (l / CG) % RG, kg = l / (CG * RG);
   const bool colok = cgi * 4 < twp;
   const int rbase = w * a.RW + rg;  // this lane's rows: rbase + RG * i, i < MR
   CT acc[MR][4];
@@ -214,7 +218,7 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
       const int kr = min(a.kch, klen - ci * a.kch);
       const GT* gk = Gsm + (size_t)rbase * ldg + ci * a.kch;
 #pragma unroll 2
-      for (int kk = 0; kk < kr; kk += 4) {
+      for (int kk = 4 * kg; kk < kr; kk += 4 * KG) {
         CT xv[4][4], gv[MR][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(kk + j) * twp, xv[j]);
@@ -232,7 +236,14 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
     if (l == 0) mbar_arrive(empty + s);
   }
   gctr += nch;
-  if (colok) {
+  // sum over the k groups of the warp
+  for (int o = CG * RG; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][q] += __shfl_xor_sync(0xffffffffu, acc[i][q], o);
+  }
+  if (colok && kg == 0) {
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
       const int r = rbase + RG * i;
@@ -405,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
 thread_local const char* g_where = "";  // last CUDA call attempted by the launcher
 
 struct Plan {
-  int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, MR;
+  int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, RG, MR;
   size_t smem;
 };
 
@@ -441,7 +452,6 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
   if (e != cudaSuccess) { g_where = "cudaDeviceGetAttribute(optin)"; return e; }
   int CG = 1;
   while (CG * 4 < twmax) CG <<= 1;
-  const int RG = 32 / CG;
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -457,10 +467,14 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
       pl.RPC = (N + NC - 1) / NC;
       pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
       if (pl.NC != NC && NC != std::min(P.num_sms / C, N)) continue;
-      pl.MR = 0;
-      for (int mr = 1; mr <= kMaxRowsPerLane; ++mr)
-        if (kConsumerWarps * RG * mr >= pl.RPC) { pl.MR = mr; break; }
-      if (pl.MR == 0) break;  // fewer clusters only need more rows
+      // rows per warp, then row groups (a power of two that fits beside the
+      // column groups) and rows per lane; leftover lanes split k
+      const int rw_need = (pl.RPC + kConsumerWarps - 1) / kConsumerWarps;
+      int RG = 1;
+      while (RG * 2 <= rw_need && CG * RG * 2 <= 32) RG <<= 1;
+      pl.RG = RG;
+      pl.MR = (rw_need + RG - 1) / RG;
+      if (pl.MR > kMaxRowsPerLane) break;  // fewer clusters only need more rows
       pl.RW = RG * pl.MR;
       pl.RPC_pad = kConsumerWarps * pl.RW;
       pl.ORW = (pl.RPC + C - 1) / C;
@@ -531,6 +545,7 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
   a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials;
   a.C = pl.C; a.RPC = pl.RPC; a.ORW = pl.ORW; a.kq = pl.kq; a.kch = pl.kch; a.slots = pl.slots; a.RW = pl.RW;
   a.RPC_pad = pl.RPC_pad;
+  a.RG = pl.RG;
   a.Gs = P.Gs; a.R = S.R; a.hz = P.hz;
   a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
   a.sigma = S.sigma;
