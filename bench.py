@@ -191,6 +191,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-step-s", type=float, default=8.0)
+    ap.add_argument("--n-outer", type=int, default=None,
+                    help="override the workload's outer iterations (short runs for profiling only)")
+    ap.add_argument("--n-steps", type=int, default=None,
+                    help="override the workload's Euler steps per run (short runs for profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 does not meet the timing rules", file=sys.stderr)
@@ -216,6 +220,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = cs_inputs.workload(WORKLOAD, seed=cs_inputs.WORKLOADS[WORKLOAD]["seed"] + rank)
+    if args.n_outer:
+        w["n_outer"] = args.n_outer
+    if args.n_steps:
+        w["n_steps"] = args.n_steps
     inst = cs_inputs.workload_instance(w)
     prm = cs.params_from_workload(w)
     T = w["trials"]

@@ -48,6 +48,9 @@ constexpr int kMaxRowsPerLane = 8;                   // accumulator rows per lan
 
 __host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
 __host__ __device__ __forceinline__ int round4(int v) { return (v + 3) & ~3; }
+// Consumer warps per column block of trials (one: every warp takes all trials of
+// a block; measured faster on GB300 than splitting the trials between warps).
+__host__ __device__ __forceinline__ int col_warps(int) { return 1; }
 
 template <typename CT>
 struct EulerArgs {
@@ -192,13 +195,18 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
     gctr += nch;
     return;
   }
+  // warp grid: WR row-warps x WC column-warps; a column-warp owns tcw trials
+  const int WC = col_warps(twp), WR = kConsumerWarps / WC;
+  const int wr = w % WR, wc = w / WR;
+  const int tcw = twp / WC;
   int CG = 1;
-  while (CG * 4 < twp) CG <<= 1;
+  while (CG * 4 < tcw) CG <<= 1;
   const int RG = a.RG;             // row groups (power of two, CG * RG <= 32)
   const int KG = 32 / (CG * RG);   // k groups: lanes that split the k rows of a chunk
   const int cgi = l % CG, rg = (l / CG) % RG, kg = l / (CG * RG);
-  const bool colok = cgi * 4 < twp;
-  const int rbase = w * a.RW + rg;  // this lane's rows: rbase + RG * i, i < MR
+  const bool colok = cgi * 4 < tcw;
+  const int col = wc * tcw + cgi * 4;  // first of this lane's four trials
+  const int rbase = wr * a.RW + rg;    // this lane's rows: rbase + RG * i, i < MR
   CT acc[MR][4];
 #pragma unroll
   for (int i = 0; i < MR; ++i)
@@ -214,7 +222,7 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
       if (l == 0) set_error(a.err, DEV_TIMEOUT);
     }
     if (ok && colok) {
-      const CT* xs = ring + (size_t)s * a.kch * twp + cgi * 4;
+      const CT* xs = ring + (size_t)s * a.kch * twp + col;
       const int kr = min(a.kch, klen - ci * a.kch);
       const GT* gk = Gsm + (size_t)rbase * ldg + ci * a.kch;
 #pragma unroll 2
@@ -249,10 +257,23 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
       const int r = rbase + RG * i;
       if (r < nrows) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) P[(size_t)r * twp + cgi * 4 + q] = acc[i][q];
+        for (int q = 0; q < 4; ++q) P[(size_t)r * twp + col + q] = acc[i][q];
       }
     }
   }
+}
+
+// Sum of the C cluster partials at offset `off` (all loads issued before the
+// adds; fixed order rank 0, 1, ...).
+template <typename CT>
+__device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, size_t off, int C) {
+  CT v[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) v[jj] = jj < C ? cluster.map_shared_rank(P, jj)[off] : CT(0);
+  CT s = v[0];
+#pragma unroll
+  for (int jj = 1; jj < 8; ++jj) s += v[jj];
+  return s;
 }
 
 template <typename GT, typename CT, int MR>
@@ -335,8 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
-        CT v = CT(0);
-        for (int jj = 0; jj < C; ++jj) v += cluster.map_shared_rank(P, jj)[(size_t)(own0 + r) * twp + tt];
+        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C);
         const int gr = row0 + own0 + r;
         const double Rr = a.R[(size_t)gr * T + t0 + tt];
         b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
@@ -380,8 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
-        CT U = CT(0);
-        for (int jj = 0; jj < C; ++jj) U += cluster.map_shared_rank(P, jj)[(size_t)(own0 + r) * twp + tt];
+        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C);
         const size_t so = (size_t)r * T + t0 + tt;
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
@@ -450,8 +469,9 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P.device);
   if (e != cudaSuccess) { g_where = "cudaDeviceGetAttribute(optin)"; return e; }
+  const int WC = col_warps(twmax), WR = kConsumerWarps / WC;
   int CG = 1;
-  while (CG * 4 < twmax) CG <<= 1;
+  while (CG * 4 < twmax / WC) CG <<= 1;
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -467,16 +487,17 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
       pl.RPC = (N + NC - 1) / NC;
       pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
       if (pl.NC != NC && NC != std::min(P.num_sms / C, N)) continue;
-      // rows per warp, then row groups (a power of two that fits beside the
-      // column groups) and rows per lane; leftover lanes split k
-      const int rw_need = (pl.RPC + kConsumerWarps - 1) / kConsumerWarps;
+      // rows per row-warp, then row groups (a power of two that fits beside the
+      // column groups, aiming at about four rows per lane) and rows per lane;
+      // leftover lanes split k
+      const int rw_need = (pl.RPC + WR - 1) / WR;
       int RG = 1;
-      while (RG * 2 <= rw_need && CG * RG * 2 <= 32) RG <<= 1;
+      while (RG * 4 < rw_need && CG * RG * 2 <= 32) RG <<= 1;
       pl.RG = RG;
       pl.MR = (rw_need + RG - 1) / RG;
       if (pl.MR > kMaxRowsPerLane) break;  // fewer clusters only need more rows
       pl.RW = RG * pl.MR;
-      pl.RPC_pad = kConsumerWarps * pl.RW;
+      pl.RPC_pad = WR * pl.RW;
       pl.ORW = (pl.RPC + C - 1) / C;
       EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR);
       cudaFuncAttributes fa;
