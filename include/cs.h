@@ -106,6 +106,18 @@ cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t
  * Errors: CS_EINVAL for bad parameters or trials < 1; CS_ENOMEM; CS_ECUDA. */
 cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
 
+/* Queue one full solve (Algorithm 1) of every problem ps[0..n) with the same
+ * parameters and `trials` (<= 64) trials each, as a batch: each outer iteration
+ * of all problems is one persistent launch in which every CTA takes whole
+ * problems from a device work queue (largest N first) and streams that
+ * problem's G_off tiles from memory, then one refit launch covers every
+ * (problem, trial).  Problem i draws its initial amplitudes with instance
+ * number i.  All problems must have been created on the same device and
+ * stream.  Results are read per problem with cs_result / cs_result_trials.
+ * Errors: CS_EINVAL (parameters, trials > 64, record_steps != 0, mixed
+ * streams), CS_ENOMEM, CS_ECUDA. */
+cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials);
+
 /* Wait for the last solve and copy out the kept trial (lowest energy, ties to
  * the lower trial index): x_hat = sigma o R (N doubles), sigma_hat (N bytes,
  * 0/1) and its energy (Eq. doublel0 with the problem's lambda, recomputed from

@@ -73,6 +73,7 @@ def lib():
         L.cs_problem_create.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_int, P,
                                         ctypes.POINTER(P)]
         L.cs_solve.argtypes = [P, ctypes.POINTER(cs_params), ctypes.c_int32]
+        L.cs_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(cs_params), ctypes.c_int32]
         L.cs_result.argtypes = [P, P, P, P, P]
         L.cs_result_trials.argtypes = [P, P, P, P, P]
         L.cs_trajectory.argtypes = [P, P, P]
@@ -85,7 +86,7 @@ def lib():
         L.cs_problem_destroy.restype = None
         L.cs_last_error.argtypes = []
         L.cs_last_error.restype = ctypes.c_char_p
-        for name in ["cs_problem_create", "cs_solve", "cs_result", "cs_result_trials", "cs_trajectory",
+        for name in ["cs_problem_create", "cs_solve", "cs_solve_batch", "cs_result", "cs_result_trials", "cs_trajectory",
                      "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -152,6 +153,12 @@ def cs_problem_create(A, y, lam: float, stream=None):
 
 def cs_solve(problem, params: cs_params, trials: int) -> None:
     _check(lib().cs_solve(problem, ctypes.byref(params), int(trials)))
+
+
+def cs_solve_batch(problems, params: cs_params, trials: int) -> None:
+    """Queue one batched solve of several problems (same stream) with shared parameters."""
+    arr = (ctypes.c_void_p * len(problems))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in problems])
+    _check(lib().cs_solve_batch(arr, len(problems), ctypes.byref(params), int(trials)))
 
 
 def cs_result(problem):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -72,25 +73,27 @@ cudaError_t alloc(T** p, size_t elems) {
 }
 
 void free_solve(SolveDev& S, cudaStream_t st) {
-  void* ptrs[] = {S.R, S.X0, S.X1, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
+  void* ptrs[] = {S.R, S.X0, S.X1, S.state, S.lead, S.job, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
                   S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular};
   for (void* q : ptrs) dev_free(q, st);
   S = SolveDev();
 }
 
 void free_problem(ProblemDev& P) {
-  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.flag};
+  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.Gt, P.flag};
   for (void* q : ptrs) dev_free(q, P.stream);
   P = ProblemDev();
 }
 
 size_t compute_bytes(int precision) { return precision == CS_P_FP64 ? 8 : 4; }
 
-// (Re)size the per-solve buffers for `trials`, n_outer and record_steps.
-cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int trials) {
+// (Re)size the per-solve buffers for `trials`, n_outer and record_steps.  A
+// batched solve (`pool` false) shares one refit workspace across its problems.
+cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int trials, bool pool = true) {
   const int rec = prm.record_steps > 0 ? std::min(prm.record_steps, prm.n_steps) : 0;
   const bool fits = S.R && trials <= S.cap_trials && prm.n_outer <= S.cap_outer && rec <= S.cap_record &&
-                    compute_bytes(prm.precision) <= compute_bytes(S.cap_prec < 0 ? 0 : S.cap_prec);
+                    compute_bytes(prm.precision) <= compute_bytes(S.cap_prec < 0 ? 0 : S.cap_prec) &&
+                    (!pool || S.work);
   if (!fits) {
     free_solve(S, P.stream);
     g_alloc_stream = P.stream;
@@ -106,8 +109,14 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     CS_CUDA(alloc(&S.energy, T), "cudaMalloc energy");
     CS_CUDA(alloc(&S.ssize, (size_t)prm.n_outer * T), "cudaMalloc ssize");
     CS_CUDA(alloc(&S.sidx, N * T), "cudaMalloc sidx");
-    S.work_elems = T * (N * N + 2 * N);
-    CS_CUDA(alloc(&S.work, S.work_elems), "cudaMalloc refit workspace");
+    CS_CUDA(alloc(&S.lead, T), "cudaMalloc lead");
+    CS_CUDA(alloc(&S.job, 1), "cudaMalloc job");
+    CS_CUDA(dev_alloc(&S.state, 3 * N * T * cb, P.stream), "cudaMalloc state");
+    if (pool) {
+      S.work_blocks = (int)std::min<size_t>(T, (size_t)P.num_sms);
+      S.work_stride = N * N + 2 * N;
+      CS_CUDA(alloc(&S.work, (size_t)S.work_blocks * S.work_stride), "cudaMalloc refit workspace");
+    }
     CS_CUDA(alloc(&S.rec_c, (size_t)rec * N * T), "cudaMalloc rec_c");
     CS_CUDA(alloc(&S.rec_e, (size_t)rec * N * T), "cudaMalloc rec_e");
     CS_CUDA(alloc(&S.x_hat, N), "cudaMalloc x_hat");
@@ -178,6 +187,32 @@ cudaError_t mark(cs_problem* p, int cat, bool begin) {
 }
 
 }  // namespace
+
+RefitJob make_job(const ProblemDev& P, const SolveDev& S) {
+  RefitJob J;
+  J.G = P.G;
+  J.hz = P.hz;
+  J.g = P.g;
+  J.A = P.A;
+  J.y = P.y;
+  J.sigma = S.sigma;
+  J.R = S.R;
+  J.sidx = S.sidx;
+  J.lead = S.lead;
+  J.ssize = S.ssize;
+  J.energy = S.energy;
+  J.x_hat = S.x_hat;
+  J.sigma_hat = S.sigma_hat;
+  J.stats = S.stats;
+  J.N = (int)P.N;
+  J.M = (int)P.M;
+  J.T = S.trials;
+  J.lambda = P.lambda;
+  J.singular = S.singular;
+  J.err = S.err;
+  return J;
+}
+
 }  // namespace cs
 
 using namespace cs;
@@ -231,7 +266,7 @@ cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t
   ProblemDev& P = p->P;
   P.M = M;
   P.N = N;
-  P.Npad = (N + 7) / 8 * 8;
+  P.Npad = (N + kPadN - 1) / kPadN * kPadN;
   P.lambda = lambda;
   P.stream = (cudaStream_t)stream;
   auto bail = [&](cs_status st) {
@@ -286,7 +321,9 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   int khz = 0;
   CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P.device), "clock rate");
   const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
-  CS_CUDA(launch_init_R(P, S), "init R");
+  const RefitJob hjob = make_job(P, S);
+  CS_CUDA(cudaMemcpyAsync(S.job, &hjob, sizeof(hjob), cudaMemcpyHostToDevice, P.stream), "copy job");
+  CS_CUDA(launch_init_R(S.job, 1, S.trials, P.num_sms, P.stream), "init R");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
   P.launches += 1;
   for (int i = 0; i < prm->n_outer; ++i) {
@@ -299,15 +336,110 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
       return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
     CS_CUDA(mark(p, TM_EULER, false), "event");
     CS_CUDA(mark(p, TM_REFIT, true), "event");
-    CS_CUDA(launch_refit(P, S, *prm, i), "refit launch");
+    CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream), "refit launch");
     CS_CUDA(mark(p, TM_REFIT, false), "event");
     P.launches += 2;
   }
   CS_CUDA(mark(p, TM_OTHER, true), "event");
-  CS_CUDA(launch_finish(P, S), "finish launch");
+  CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream), "finish launch");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
   P.launches += 2;
   S.done = true;
+  return CS_OK;
+}
+
+cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials) {
+  if (!ps || n < 1) return fail(CS_EINVAL, "need at least one problem");
+  cs_status st = check_params(prm, trials);
+  if (st != CS_OK) return st;
+  if (trials > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials");
+  if (prm->record_steps != 0) return fail(CS_EINVAL, "a batched solve does not record trajectories");
+  for (int i = 0; i < n; ++i) {
+    if (!ps[i]) return fail(CS_EINVAL, "problem is NULL");
+    if (ps[i]->P.stream != ps[0]->P.stream || ps[i]->P.device != ps[0]->P.device)
+      return fail(CS_EINVAL, "the problems of a batch must share one stream and device");
+  }
+  ProblemDev& P0 = ps[0]->P;
+  cudaStream_t stream = P0.stream;
+  g_alloc_stream = stream;
+  int64_t nmax = 0;
+  for (int i = 0; i < n; ++i) {
+    ProblemDev& P = ps[i]->P;
+    SolveDev& S = ps[i]->S;
+    S.done = false;
+    nmax = std::max(nmax, P.N);
+    CS_CUDA(launch_store_tiled(P, prm->precision), "store tiled coupling");
+    if ((st = ensure_solve(P, S, *prm, trials, false)) != CS_OK) return st;
+    CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), stream), "memset singular");
+  }
+  // batch-owned buffers, released (stream-ordered) after the last kernel
+  const size_t ib = batch_inst_bytes();
+  void* d_insts = nullptr;
+  int* d_order = nullptr;
+  int* d_queue = nullptr;
+  int* d_err = nullptr;
+  RefitJob* d_jobs = nullptr;
+  double* pool = nullptr;
+  const size_t stride = (size_t)nmax * nmax + 2 * (size_t)nmax;
+  int pool_blocks = std::min(n * trials, P0.num_sms);
+  while (pool_blocks > 1 && (double)pool_blocks * stride * 8.0 > 16e9) --pool_blocks;
+  CS_CUDA(dev_alloc(&d_insts, ib * n, stream), "cudaMalloc batch descriptors");
+  CS_CUDA(alloc(&d_order, n), "cudaMalloc batch order");
+  CS_CUDA(alloc(&d_queue, 1), "cudaMalloc batch queue");
+  CS_CUDA(alloc(&d_err, 1), "cudaMalloc batch error word");
+  CS_CUDA(alloc(&d_jobs, n), "cudaMalloc batch jobs");
+  CS_CUDA(alloc(&pool, (size_t)pool_blocks * stride), "cudaMalloc batch refit workspace");
+  CS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream), "memset err");
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ps[a]->P.N > ps[b]->P.N; });
+  CS_CUDA(cudaMemcpyAsync(d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, stream), "copy order");
+  std::vector<RefitJob> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    jobs[i] = make_job(ps[i]->P, ps[i]->S);
+    jobs[i].err = d_err;
+  }
+  CS_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), n * sizeof(RefitJob), cudaMemcpyHostToDevice, stream), "copy jobs");
+  int khz = 0;
+  CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P0.device), "clock rate");
+  const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
+  CS_CUDA(launch_init_R(d_jobs, n, trials, P0.num_sms, stream), "init R");
+  std::vector<unsigned char> hinst(ib * n);
+  for (int it = 0; it < prm->n_outer; ++it) {
+    for (int i = 0; i < n; ++i) {
+      const double eta = eta_at(it, *prm, ps[i]->P.lambda);
+      fill_batch_inst(hinst.data() + ib * i, ps[i]->P, ps[i]->S, prm->precision, std::sqrt(prm->tau) * eta * eta / 4.0,
+                      i);
+    }
+    CS_CUDA(cudaMemcpyAsync(d_insts, hinst.data(), ib * n, cudaMemcpyHostToDevice, stream), "copy descriptors");
+    BatchLaunch L;
+    L.insts = d_insts;
+    L.order = d_order;
+    L.n = n;
+    L.T = trials;
+    L.prm = prm;
+    L.queue = d_queue;
+    L.outer = it;
+    L.err = d_err;
+    L.timeout_cycles = timeout_cycles;
+    L.ctas = P0.num_sms;
+    cudaError_t e = launch_euler_batch(L, stream);
+    if (e == cudaErrorInvalidConfiguration) return fail(CS_EINVAL, "batched Euler kernel does not fit shared memory");
+    CS_CUDA(e, "batched euler launch");
+    CS_CUDA(launch_refit(d_jobs, n, trials, pool, stride, pool_blocks, it, stream), "batched refit launch");
+  }
+  CS_CUDA(launch_finish(d_jobs, n, trials, P0.num_sms, stream), "batched finish launch");
+  dev_free(d_insts, stream);
+  dev_free(d_order, stream);
+  dev_free(d_queue, stream);
+  dev_free(d_err, stream);
+  dev_free(d_jobs, stream);
+  dev_free(pool, stream);
+  for (int i = 0; i < n; ++i) {
+    ps[i]->S.done = true;
+    ps[i]->S.plan_cluster = 0;
+    ps[i]->S.plan_ctas = std::min(n, P0.num_sms);
+  }
   return CS_OK;
 }
 

@@ -1,0 +1,434 @@
+// Batched solves of many independent problems of uneven size (Algorithm 1 for
+// each): one outer iteration of every problem in one persistent launch.
+//
+// Each CTA takes whole problems from a device work queue (largest first, so the
+// tail is short) and runs a complete CIM run of the problem it took: the
+// prologue (b or q, initial c and e), every Euler step of Eq. mfeq1 /
+// Eq. GMFZEC5 with the field of Eq. localfieldMFZ or Eq. localfieldMFZBN, and
+// the readout sigma = H(c).  A problem never spans CTAs, so no inter-CTA
+// synchronisation is needed and the whole GPU streams independent problems.
+//
+// G_off of a problem is stored for streaming: tiles of kRT rows x kKC columns,
+// tile (rt, kc) contiguous, rows zero-padded to a multiple of kRT and columns
+// to Npad.  Inside a tile, the quad (4 columns) q of row r sits at position
+// q ^ (r & 7), so the lanes of a warp that read the same quad of eight
+// consecutive rows hit eight different banks.  Each step, for each row tile, a
+// producer warp streams the tile's G_off blocks and the matching k rows of X
+// into a shared-memory ring with bulk copies (mbarrier full/empty handshake);
+// eight consumer warps accumulate the tile's rows of U = G_off X, then update
+// those rows of c and e (kept in global memory, L2-resident) and write their
+// next X.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "kernels_common.cuh"
+#include "tma.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kBWarps = 8;                     // consumer warps
+constexpr int kBThreads = (kBWarps + 1) * 32;  // + one producer warp
+constexpr int kRT = 128;                       // rows per tile (16 per consumer warp)
+constexpr int kKC = 32;                        // columns (k) per tile
+
+template <typename GT> __device__ __forceinline__ GT to_storage(double v);
+template <> __device__ __forceinline__ double to_storage<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_storage<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __half to_storage<__half>(double v) { return __double2half(v); }
+
+// Tiled, swizzled copy of G_off (see the file comment).
+template <typename GT>
+__global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int nrt, int nkc) {
+  const size_t total = (size_t)nrt * nkc * kRT * kKC;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = idx / (kRT * kKC);
+    const int within = (int)(idx % (kRT * kKC));
+    const int r = within / kKC, kp = within % kKC;
+    const int rt = (int)(tile / nkc), kc = (int)(tile % nkc);
+    const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    const int row = rt * kRT + r, col = kc * kKC + k;
+    const double v = (row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
+    Gt[idx] = to_storage<GT>(v);
+  }
+}
+
+template <typename CT>
+struct BInst {
+  int N, nrt, nkc;         // rows, row tiles, column tiles (nkc * kKC = Npad)
+  const void* Gt;          // tiled G_off
+  const double* R;         // N x T
+  const double* hz;        // N
+  CT* X0;                  // Npad x twp, rows >= N zero
+  CT* X1;
+  CT* state;               // c, e, b: 3 x N x T
+  uint8_t* sigma;          // N x T
+  double theta;            // sqrt(tau) eta^2 / 4 of this problem
+  int inst;                // instance number of the initial-amplitude key
+};
+
+template <typename CT>
+struct BArgs {
+  const BInst<CT>* insts;
+  const int* order;  // processing order (largest first)
+  int n;
+  int T, twp, slots;
+  int* queue;
+  int n_steps;
+  double dt;
+  int pump_kind;
+  double p0, p1, p_thr, d, t0, width;
+  double beta, tau, Kj;
+  int field, init_kind;
+  double init_scale;
+  uint64_t seed;
+  int outer;
+  int* err;
+  long long timeout_cycles;
+};
+
+__host__ __device__ __forceinline__ size_t b_slot_bytes(int twp, size_t gbytes, size_t cbytes) {
+  return align128((size_t)kRT * kKC * gbytes + (size_t)kKC * twp * cbytes);
+}
+
+// Partial-free product of one row tile: U[r][tt] = sum_k G_off[rt*kRT + r][k] X[k][tt]
+// for r < kRT, written to P (kRT x twp).  Lane layout: CG column groups of four
+// trials, RG row groups, KG k groups (CG RG KG = 32), MR = 16 / RG rows per lane.
+template <typename GT, typename CT, int MR>
+__device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
+                                             int rt, unsigned char* ring, size_t slot, CT* P, uint64_t* full,
+                                             uint64_t* empty, unsigned& gctr, unsigned* issued) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int twp = a.twp, nkc = I.nkc;
+  const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
+  const unsigned xbytes = (unsigned)(kKC * twp * sizeof(CT));
+  bool ok = true;
+  if (w == kBWarps) {
+    if (l == 0) {
+      fence_proxy_async_global();
+      const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const unsigned g = gctr + kc;
+        const int s = (int)(g % a.slots);
+        const unsigned u = g / a.slots;
+        if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
+          set_error(a.err, DEV_TIMEOUT);
+          break;
+        }
+        unsigned char* dst = ring + (size_t)s * slot;
+        issued[s] = g + 1;
+        mbar_arrive_expect_tx(full + s, (unsigned)gtile + xbytes);
+        bulk_copy_g2s(dst, gsrc + (size_t)kc * kRT * kKC, (unsigned)gtile, full + s);
+        bulk_copy_g2s(dst + gtile, X + (size_t)kc * kKC * twp, xbytes, full + s);
+      }
+    }
+    gctr += nkc;
+    return true;
+  }
+  int CG = 1;
+  while (CG * 4 < twp) CG <<= 1;
+  const int RG = 16 / MR;
+  const int KG = 32 / (CG * RG);
+  const int cgi = l % CG, rg = (l / CG) % RG, kg = l / (CG * RG);
+  const bool colok = cgi * 4 < twp;
+  const int col = cgi * 4;
+  const int rbase = w * 16 + rg;  // rows rbase + RG * i, i < MR
+  CT acc[MR][4];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = CT(0);
+  for (int kc = 0; kc < nkc; ++kc) {
+    const unsigned g = gctr + kc;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok && colok) {
+      const GT* gt = reinterpret_cast<const GT*>(ring + (size_t)s * slot);
+      const CT* xs = reinterpret_cast<const CT*>(ring + (size_t)s * slot + gtile) + col;
+#pragma unroll 2
+      for (int q = kg; q < kKC / 4; q += KG) {
+        CT xv[4][4], gv[MR][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(4 * q + j) * twp, xv[j]);
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int r = rbase + RG * i;
+          load4<CT, GT>(gt + (size_t)r * kKC + 4 * (q ^ (r & 7)), gv[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) acc[i][qq] = fma(gv[i][j], xv[j][qq], acc[i][qq]);
+      }
+    }
+    __syncwarp();
+    if (l == 0) mbar_arrive(empty + s);
+  }
+  gctr += nkc;
+  for (int o = CG * RG; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) acc[i][qq] += __shfl_xor_sync(0xffffffffu, acc[i][qq], o);
+  }
+  if (colok && kg == 0) {
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+      const int r = rbase + RG * i;
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) P[(size_t)r * twp + col + qq] = acc[i][qq];
+    }
+  }
+  return ok;
+}
+
+// One CIM run of problem I.  Returns false (in every thread) if a wait timed out.
+template <typename GT, typename CT, int MR>
+__device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned char* ring, size_t slot, CT* P,
+                             uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued) {
+  const int T = a.T, twp = a.twp, N = I.N;
+  const size_t NT = (size_t)N * T;
+  CT* c = I.state;
+  CT* e = I.state + NT;
+  CT* b = I.state + 2 * NT;
+  const double st = sqrt(a.tau);
+  const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
+  bool ok = true;
+  // ---- prologue
+  if (a.field == CS_FIELD_CN) {
+    for (size_t idx = threadIdx.x; idx < NT; idx += kBThreads) {
+      const int r = (int)(idx / T), t = (int)(idx % T);
+      I.X0[(size_t)r * twp + t] = CT(I.R[idx]);
+    }
+    fence_proxy_async_global();
+    __syncthreads();
+    for (int rt = 0; rt < I.nrt && ok; ++rt) {
+      ok = __syncthreads_and(tile_product<GT, CT, MR>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued));
+      for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
+        const int r = rt * kRT + idx / T, t = idx % T;
+        if (r >= N) continue;
+        const double v = (double)P[(size_t)(idx / T) * twp + t];
+        const size_t o = (size_t)r * T + t;
+        b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta);
+      }
+      __syncthreads();
+    }
+  } else {
+    for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
+      const int r = (int)(o / T);
+      b[o] = CT((st / 2.0) * I.R[o] * I.hz[r] - I.theta);
+    }
+  }
+  for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
+    const int r = (int)(o / T), t = (int)(o % T);
+    const uint64_t key = run_key(a.seed, (uint64_t)I.inst, (uint64_t)t, (uint64_t)a.outer);
+    const CT c0 = CT(initial_amplitude(key, (uint64_t)r, a.init_kind, a.init_scale));
+    c[o] = c0;
+    e[o] = CT(1);
+    const CT Rr = CT(I.R[o]);
+    I.X1[(size_t)r * twp + t] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+  }
+  fence_proxy_async_global();
+  __syncthreads();
+  // ---- Euler steps
+  const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
+  CT* Xc = I.X1;
+  CT* Xn = I.X0;
+  for (int n = 0; n < a.n_steps && ok; ++n) {
+    const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
+    const bool last = (n + 1 == a.n_steps);
+    for (int rt = 0; rt < I.nrt && ok; ++rt) {
+      ok = __syncthreads_and(tile_product<GT, CT, MR>(a, I, Xc, rt, ring, slot, P, full, empty, gctr, issued));
+      for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
+        const int rl = idx / T, t = idx % T, r = rt * kRT + rl;
+        if (r >= N) continue;
+        const size_t o = (size_t)r * T + t;
+        const CT U = P[(size_t)rl * twp + t];
+        const CT Rr = CT(I.R[o]);
+        const CT f = wcoef * Rr * U + b[o];
+        const CT cc = c[o], ee = e[o];
+        const CT c2 = cc * cc;
+        const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
+        const CT en = ee + dt * (-beta * (c2 - tau) * ee);
+        c[o] = cn;
+        e[o] = en;
+        Xn[(size_t)r * twp + t] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    fence_proxy_async_global();
+    __syncthreads();
+    CT* tmp = Xc; Xc = Xn; Xn = tmp;
+  }
+  return ok;
+}
+
+template <typename GT, typename CT, int MR>
+__global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT));
+  unsigned char* ring = smem_raw;
+  CT* P = reinterpret_cast<CT*>(smem_raw + (size_t)a.slots * slot);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + align128((size_t)kRT * a.twp * sizeof(CT)));
+  uint64_t* empty = full + a.slots;
+  __shared__ int s_next;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.slots; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, kBWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned gctr = 0;
+  unsigned issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // producer: 1 + last ring use issued per slot
+  bool ok = true;
+  while (ok) {
+    if (threadIdx.x == 0) s_next = ld_volatile(a.err) != 0 ? a.n : atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int qi = s_next;
+    __syncthreads();
+    if (qi >= a.n) break;
+    const BInst<CT> I = a.insts[a.order[qi]];
+    ok = run_instance<GT, CT, MR>(a, I, ring, slot, P, full, empty, gctr, issued);
+  }
+  // After a timeout, let any copy still in flight land before the CTA exits.
+  if (!ok && threadIdx.x == kBWarps * 32) {
+    for (int s = 0; s < a.slots; ++s)
+      if (issued[s] > 0) mbar_wait(full + s, (issued[s] - 1) / a.slots & 1u, a.timeout_cycles);
+  }
+}
+
+template <typename GT, typename CT, int MR>
+cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
+  const int twp = round4(L.T);
+  const size_t slot = b_slot_bytes(twp, sizeof(GT), sizeof(CT));
+  auto fn = euler_batch_kernel<GT, CT, MR>;
+  int optin = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  const size_t fixed = align128((size_t)kRT * twp * sizeof(CT));
+  const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+  int slots = 8;
+  while (slots > 2 && (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t) > cap) --slots;
+  const size_t smem = (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t);
+  if (smem > cap) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BArgs<CT> a;
+  a.insts = reinterpret_cast<const BInst<CT>*>(L.insts);
+  a.order = L.order;
+  a.n = L.n;
+  a.T = L.T;
+  a.twp = twp;
+  a.slots = slots;
+  a.queue = L.queue;
+  a.n_steps = L.prm->n_steps;
+  a.dt = L.prm->dt;
+  a.pump_kind = L.prm->pump_kind;
+  a.p0 = L.prm->p0; a.p1 = L.prm->p1; a.p_thr = L.prm->p_thr; a.d = L.prm->d; a.t0 = L.prm->t0;
+  a.width = L.prm->width;
+  a.beta = L.prm->beta; a.tau = L.prm->tau; a.Kj = L.prm->K * L.prm->j;
+  a.field = L.prm->field; a.init_kind = L.prm->init_kind; a.init_scale = L.prm->init_scale;
+  a.seed = L.prm->seed;
+  a.outer = L.outer;
+  a.err = L.err;
+  a.timeout_cycles = L.timeout_cycles;
+  e = cudaMemsetAsync(L.queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  euler_batch_kernel<GT, CT, MR><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename GT, typename CT>
+cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
+  int CG = 1;
+  while (CG * 4 < round4(L.T)) CG <<= 1;
+  const int RG = std::min(16, 32 / CG);
+  switch (16 / RG) {
+    case 1: return launch_batch_typed<GT, CT, 1>(L, st);
+    case 2: return launch_batch_typed<GT, CT, 2>(L, st);
+    case 4: return launch_batch_typed<GT, CT, 4>(L, st);
+    default: return launch_batch_typed<GT, CT, 8>(L, st);
+  }
+}
+
+}  // namespace
+
+size_t batch_inst_bytes() { return sizeof(BInst<double>) > sizeof(BInst<float>) ? sizeof(BInst<double>) : sizeof(BInst<float>); }
+
+int64_t tiled_elems(int64_t N, int64_t Npad) {
+  const int64_t nrt = (N + kRT - 1) / kRT;
+  return nrt * kRT * Npad;
+}
+
+cudaError_t launch_store_tiled(ProblemDev& P, int precision) {
+  if (P.gt_prec == precision && P.Gt) return cudaSuccess;
+  if (P.Gt) { dev_free(P.Gt, P.stream); P.Gt = nullptr; P.gt_prec = -1; }
+  const size_t gb = precision == CS_P_FP64 ? 8 : precision == CS_P_FP32 ? 4 : 2;
+  const int64_t elems = tiled_elems(P.N, P.Npad);
+  cudaError_t e = dev_alloc(&P.Gt, (size_t)elems * gb, P.stream);
+  if (e != cudaSuccess) return e;
+  const int N = (int)P.N, nrt = (int)((P.N + kRT - 1) / kRT), nkc = (int)(P.Npad / kKC);
+  const int blocks = P.num_sms * 4;
+  switch (precision) {
+    case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc); break;
+    case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc); break;
+    case CS_P_BF16:
+      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc);
+      break;
+    case CS_P_FP16: store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) P.gt_prec = precision;
+  return e;
+}
+
+// Host description of one problem for the batched kernel, written into `dst`
+// (a BInst of the precision's compute type).
+void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst) {
+  if (precision == CS_P_FP64) {
+    BInst<double> I;
+    I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
+    I.Gt = P.Gt; I.R = S.R; I.hz = P.hz;
+    I.X0 = (double*)S.X0; I.X1 = (double*)S.X1; I.state = (double*)S.state; I.sigma = S.sigma;
+    I.theta = theta; I.inst = inst;
+    *reinterpret_cast<BInst<double>*>(dst) = I;
+  } else {
+    BInst<float> I;
+    I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
+    I.Gt = P.Gt; I.R = S.R; I.hz = P.hz;
+    I.X0 = (float*)S.X0; I.X1 = (float*)S.X1; I.state = (float*)S.state; I.sigma = S.sigma;
+    I.theta = theta; I.inst = inst;
+    *reinterpret_cast<BInst<float>*>(dst) = I;
+  }
+}
+
+cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st) {
+  switch (L.prm->precision) {
+    case CS_P_FP64: return launch_batch_mr<double, double>(L, st);
+    case CS_P_FP32: return launch_batch_mr<float, float>(L, st);
+    case CS_P_BF16: return launch_batch_mr<__nv_bfloat16, float>(L, st);
+    case CS_P_FP16: return launch_batch_mr<__half, float>(L, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cs

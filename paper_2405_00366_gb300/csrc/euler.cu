@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "kernels_common.cuh"
 #include "tma.cuh"
 
 namespace cg = cooperative_groups;
@@ -46,8 +47,6 @@ constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
 constexpr int kTChunk = 64;                          // trials per block of X
 constexpr int kMaxRowsPerLane = 8;                   // accumulator rows per lane
 
-__host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
-__host__ __device__ __forceinline__ int round4(int v) { return (v + 3) & ~3; }
 // Consumer warps per column block of trials (one: every warp takes all trials of
 // a block; measured faster on GB300 than splitting the trials between warps).
 __host__ __device__ __forceinline__ int col_warps(int) { return 1; }
@@ -88,48 +87,6 @@ struct EulerArgs {
   long long timeout_cycles;
   unsigned phantom;
 };
-
-// Pump rate at step n of a run of S steps, in the compute type: the linear ramp
-// p0 + (p1 - p0) n / S or the sigmoid of Eq. pumprateGACS at t = n dt.
-template <typename CT>
-__device__ __forceinline__ CT pump_at(int n, int S, int kind, double p0, double p1, double p_thr, double d, double dt,
-                                      double t0, double width) {
-  if (kind == CS_PUMP_LINEAR) return CT(p0) + CT(p1 - p0) * (CT(n) / CT(S));
-  const CT t = CT(n) * CT(dt);
-  return CT(p_thr - d) + CT(2.0 * d) / (CT(1) + exp(-(t - CT(t0)) / CT(width)));
-}
-
-// Four consecutive storage values widened to CT.
-template <typename CT, typename GT>
-__device__ __forceinline__ void load4(const GT* p, CT out[4]) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) out[j] = widen<CT, GT>(p[j]);
-}
-template <>
-__device__ __forceinline__ void load4<float, float>(const float* p, float out[4]) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-}
-template <>
-__device__ __forceinline__ void load4<double, double>(const double* p, double out[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p);
-  const double2 b = *reinterpret_cast<const double2*>(p + 2);
-  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
-}
-template <>
-__device__ __forceinline__ void load4<float, __nv_bfloat16>(const __nv_bfloat16* p, float out[4]) {
-  const uint2 v = *reinterpret_cast<const uint2*>(p);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
-  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
-}
-template <>
-__device__ __forceinline__ void load4<float, __half>(const __half* p, float out[4]) {
-  const uint2 v = *reinterpret_cast<const uint2*>(p);
-  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
-}
 
 // X is stored in blocks of kTChunk trials: block t0 (t0 a multiple of 64) holds
 // trials [t0, t0 + tw) as an Npad x twp row-major matrix (twp = tw rounded up to

@@ -22,9 +22,13 @@ void dev_free(void* p, cudaStream_t s);
 // around each group of launches on the problem's stream, and a launch count.
 enum { TM_GRAM = 0, TM_EULER = 1, TM_REFIT = 2, TM_OTHER = 3, TM_COUNT = 4 };
 
+// Rows of G_off are padded to this multiple (k quads of the Euler kernels and
+// the 32-column tiles of the streamed layout).
+constexpr int64_t kPadN = 32;
+
 // Device buffers of one problem (all owned by the library).
 struct ProblemDev {
-  int64_t M = 0, N = 0, Npad = 0;  // Npad: N rounded up to a multiple of 8
+  int64_t M = 0, N = 0, Npad = 0;  // Npad: N rounded up to a multiple of kPadN
   double lambda = 0.0;
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
@@ -35,8 +39,32 @@ struct ProblemDev {
   double* g = nullptr;    // N, diag G
   void* Gs = nullptr;     // Npad x Npad, G in storage precision with zero diagonal and zero padding
   int gs_prec = -1;       // precision held in Gs
+  void* Gt = nullptr;     // G_off in storage precision, tiled for streaming (batched solves)
+  int gt_prec = -1;
   int* flag = nullptr;    // device word: nonzero if A or y had a non-finite value
   int64_t launches = 0;   // kernels launched by the last create + solve
+};
+
+// What the refit, objective and selection kernels need of one problem.
+struct RefitJob {
+  const double* G;
+  const double* hz;
+  const double* g;
+  const double* A;
+  const double* y;
+  const uint8_t* sigma;  // N x T
+  double* R;             // N x T
+  int* sidx;             // T x N support index lists
+  int* lead;             // T: trial whose refit this trial copies (itself if none)
+  int32_t* ssize;        // n_outer x T support sizes
+  double* energy;        // T
+  double* x_hat;         // N
+  uint8_t* sigma_hat;    // N
+  double* stats;         // CS_STATS_LEN
+  int N, M, T;
+  double lambda;
+  int* singular;
+  int* err;
 };
 
 // Per-solve device state, sized by (N, trials).
@@ -46,12 +74,15 @@ struct SolveDev {
   double* R = nullptr;          // N x T (FP64), refit signal
   void* X0 = nullptr;           // Npad x round4(T) coupling operand (blocks of 64 trials), two buffers
   void* X1 = nullptr;
+  void* state = nullptr;        // 3 x N x T amplitudes, feedback, injection constant (streamed kernel)
   uint8_t* sigma = nullptr;     // N x T support
   double* energy = nullptr;     // T
   int32_t* ssize = nullptr;     // n_outer x T support sizes
   int32_t* sidx = nullptr;      // T x N support index lists
-  double* work = nullptr;       // refit workspace, T x N x N doubles (lazily sized)
-  size_t work_elems = 0;
+  int32_t* lead = nullptr;      // T
+  double* work = nullptr;       // refit workspace pool
+  size_t work_stride = 0;       // doubles per pool block
+  int work_blocks = 0;
   double* rec_c = nullptr;      // record_steps x N x T
   double* rec_e = nullptr;
   double* x_hat = nullptr;      // N, kept trial
@@ -60,9 +91,29 @@ struct SolveDev {
   unsigned* bar = nullptr;      // grid barrier counter
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
+  RefitJob* job = nullptr;      // this problem's refit job (device copy)
   bool done = false;
   int plan_cluster = 0, plan_ctas = 0;  // work split of the last Euler launch
 };
+
+RefitJob make_job(const ProblemDev& P, const SolveDev& S);
+
+// One outer iteration of a batch of problems in one launch (batch.cu).
+struct BatchLaunch {
+  const void* insts;   // device array of per-problem descriptors (fill_batch_inst)
+  const int* order;    // device array: processing order, largest first
+  int n, T;
+  const cs_params* prm;
+  int* queue;          // device work counter
+  int outer;
+  int* err;
+  long long timeout_cycles;
+  int ctas;            // CTAs to launch (one per SM)
+};
+size_t batch_inst_bytes();
+void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst);
+cudaError_t launch_store_tiled(ProblemDev& P, int precision);
+cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);
 
 // Launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gram(const ProblemDev& P);
@@ -70,8 +121,9 @@ cudaError_t launch_store_coupling(ProblemDev& P, int precision);
 cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer,
                          double eta, long long timeout_cycles);
 const char* euler_last_call();  // the CUDA call the last failing Euler launch stopped at
-cudaError_t launch_init_R(const ProblemDev& P, SolveDev& S);
-cudaError_t launch_refit(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer);
-cudaError_t launch_finish(const ProblemDev& P, SolveDev& S);
+cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
+cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
+                         int outer, cudaStream_t st);
+cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
 
 }  // namespace cs

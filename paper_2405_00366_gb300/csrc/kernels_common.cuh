@@ -1,0 +1,54 @@
+// Device helpers shared by the Euler kernels: sizes, the pump schedule in the
+// compute type, and widening loads of four consecutive storage values.
+#pragma once
+
+#include "common.cuh"
+
+namespace cs {
+
+__host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ __forceinline__ int round4(int v) { return (v + 3) & ~3; }
+
+// Pump rate at step n of a run of S steps, in the compute type: the linear ramp
+// p0 + (p1 - p0) n / S or the sigmoid of Eq. pumprateGACS at t = n dt.
+template <typename CT>
+__device__ __forceinline__ CT pump_at(int n, int S, int kind, double p0, double p1, double p_thr, double d, double dt,
+                                      double t0, double width) {
+  if (kind == CS_PUMP_LINEAR) return CT(p0) + CT(p1 - p0) * (CT(n) / CT(S));
+  const CT t = CT(n) * CT(dt);
+  return CT(p_thr - d) + CT(2.0 * d) / (CT(1) + exp(-(t - CT(t0)) / CT(width)));
+}
+
+// Four consecutive storage values widened to CT.
+template <typename CT, typename GT>
+__device__ __forceinline__ void load4(const GT* p, CT out[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = widen<CT, GT>(p[j]);
+}
+template <>
+__device__ __forceinline__ void load4<float, float>(const float* p, float out[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double, double>(const double* p, double out[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load4<float, __nv_bfloat16>(const __nv_bfloat16* p, float out[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load4<float, __half>(const __half* p, float out[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
+}  // namespace cs

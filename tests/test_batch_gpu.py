@@ -1,0 +1,118 @@
+"""Batched solves of uneven problems (cs_solve_batch) and reduced-precision coupling
+storage, against the FP64 oracle.
+
+Problem i of a batch draws its initial amplitudes with instance number i, so the
+oracle runs each problem with inst=i.  FP64/FP32 batches must reproduce the
+oracle's supports exactly; BF16/FP16 storage of G_off changes the trajectories,
+so those are gated on the final support and the RMSE (within 1e-3 of the
+oracle's) only.
+"""
+import numpy as np
+import pytest
+import torch
+
+import cs_inputs
+import oracle
+from paper_2405_00366_gb300 import cs
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_KEYS = {"n_outer", "n_steps", "dt", "pump_kind", "p0", "p1", "p_thr", "d", "t0", "width", "beta", "tau",
+               "K", "j", "eta_init", "eta_end", "velo", "init_kind", "init_scale", "field", "refit", "seed"}
+
+
+def oracle_params(w):
+    return oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS})
+
+
+def run_batch(insts, w, trials):
+    prm = cs.params_from_workload(w)
+    hs = [cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam) for i in insts]
+    try:
+        cs.cs_solve_batch(hs, prm, trials)
+        out = []
+        for h in hs:
+            x, s, E, st, status = cs.cs_result(h)
+            R, sig, Es, ss = cs.cs_result_trials(h, trials, w["n_outer"])
+            out.append(dict(x_hat=x, sigma=s, energy=E, stats=st, R=R, sigmas=sig, energies=Es, support_sizes=ss))
+    finally:
+        for h in hs:
+            cs.cs_problem_destroy(h)
+    return out
+
+
+def uneven(sizes, seed=5, lam=0.03):
+    return [cs_inputs.random_instance(N, max(1, int(0.6 * N)), max(1, N // 10), 0.01, lam, seed=seed + i)
+            for i, N in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_oracle(precision):
+    insts = uneven([40, 150, 333, 130, 257, 9])
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=500, precision=precision, seed=4)
+    T = 3
+    g = run_batch(insts, w, T)
+    for i, inst in enumerate(insts):
+        r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)
+        np.testing.assert_array_equal(g[i]["support_sizes"], r["support_sizes"])
+        np.testing.assert_array_equal(g[i]["sigmas"], r["sigmas"])
+        tol = 1e-9 if precision == "fp64" else 1e-5
+        np.testing.assert_allclose(g[i]["x_hat"], r["x_hat"], rtol=0, atol=tol)
+        np.testing.assert_allclose(g[i]["energies"], r["energies"], rtol=1e-9 if precision == "fp64" else 1e-6)
+        assert int(g[i]["stats"][0]) == r["best_trial"]
+
+
+def test_batch_equals_individual_solves():
+    """A problem gives the same support and signal alone (cs_solve, instance i) and in a batch."""
+    insts = uneven([64, 200, 96], seed=11)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp32", seed=2)
+    g = run_batch(insts, w, 4)
+    for i, inst in enumerate(insts):
+        prm = cs.params_from_workload(w, instance=i)
+        h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+        try:
+            cs.cs_solve(h, prm, 4)
+            x, s, E, st, _ = cs.cs_result(h)
+            R, sig, Es, ss = cs.cs_result_trials(h, 4, w["n_outer"])
+        finally:
+            cs.cs_problem_destroy(h)
+        np.testing.assert_array_equal(sig, g[i]["sigmas"])
+        np.testing.assert_allclose(x, g[i]["x_hat"], rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_reduced_precision_support_and_rmse(precision):
+    """G_off stored in BF16 / FP16 with FP32 accumulation, single solve and batch,
+    gated on the final support and on RMSE within 1e-3 of the FP64 oracle's."""
+    w = cs_inputs.workload("trials64_n2000_fp32", N=500, M=300, nnz=50, n_outer=4, n_steps=800, precision=precision)
+    inst = cs_inputs.workload_instance(w)
+    T = 4
+    prm = cs.params_from_workload(w)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        cs.cs_solve(h, prm, T)
+        x, s, E, st, _ = cs.cs_result(h)
+    finally:
+        cs.cs_problem_destroy(h)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T)
+    np.testing.assert_array_equal(s, r["sigma"])
+    assert abs(oracle.rmse(x, inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+    g = run_batch([inst], w, T)
+    np.testing.assert_array_equal(g[0]["sigma"], r["sigma"])
+    assert abs(oracle.rmse(g[0]["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+
+
+def test_batch_uneven_bf16_shapes():
+    """Uneven instances in the shape of the batched workload (alpha in {0.3, 0.5, 0.7},
+    a in {0.05, 0.1, 0.2}, 16 trials, BF16), scaled down: every result is a valid
+    refit (zero gradient on its support) and its energy is the recomputed objective."""
+    insts = cs_inputs.uneven_batch(8, 256, 700, [0.3, 0.5, 0.7], [0.05, 0.1, 0.2], 0.01, 0.03, seed=3)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300, precision="bf16", seed=1)
+    g = run_batch(insts, w, 16)
+    for inst, res in zip(insts, g):
+        S = np.flatnonzero(res["sigma"])
+        resid = inst.y - inst.A[:, S] @ res["x_hat"][S]
+        assert res["energy"] == pytest.approx(0.5 * resid @ resid + inst.lam * S.size, rel=1e-10)
+        if 0 < S.size < inst.M:
+            grad = inst.A[:, S].T @ resid
+            assert np.abs(grad).max() <= 1e-8 * max(1.0, np.linalg.norm(inst.A.T @ inst.y))
