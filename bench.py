@@ -248,6 +248,7 @@ def main():
         out, tm = finish(one_solve())
 
     step_ms, euler_ms, launches = [], 0.0, 0
+    phase_ms = [0.0, 0.0, 0.0, 0.0]
     results = None
     if dist:
         dist.barrier()
@@ -266,6 +267,8 @@ def main():
             step_ms.append(ev0.elapsed_time(ev1))
             euler_ms += tm[0][1]
             launches += tm[1]
+            for k in range(4):
+                phase_ms[k] += tm[0][k]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -328,6 +331,7 @@ def main():
                 "h2d_bytes_per_step": (inst.A.size + inst.y.size) * 8,
                 "d2h_bytes_per_step": inst.N * 8 + inst.N + 8 + cs.CS_STATS_LEN * 8},
         "gpu_launches": launches,
+        "breakdown_ms_per_step": {k: v / args.steps for k, v in zip(["gram", "euler", "refit", "other"], phase_ms)},
         "clocks": ck,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -80,6 +80,8 @@ typedef struct {
                                 do not exist, so it runs into timeout_ms; 0 in normal use */
   int32_t cluster_size; /* CTAs per thread-block cluster of the Euler kernel: 0 = chosen by the
                            library's planner, or 1, 2, 4, 8 */
+  int32_t max_ctas;     /* at most this many CTAs (SMs) per Euler launch, 0 = all; lets solves
+                           on different streams share the GPU */
 } cs_params;
 
 typedef struct cs_problem cs_problem;
@@ -183,6 +185,48 @@ cs_status cs_problem_shape(const cs_problem* p, int64_t* M, int64_t* N);
 
 /* Release everything the problem owns.  NULL is ignored. */
 void cs_problem_destroy(cs_problem* p);
+
+/* ---- Serving: a continuous-batching request loop over the solver.
+ * A server owns `max_slots` CUDA streams on the current device and a worker
+ * thread.  Submitted requests wait in arrival order; one is admitted when a
+ * slot is free and its device-memory estimate fits what is left of
+ * `hbm_budget_bytes`.  An admitted request forms its problem (Gram on the GPU)
+ * and queues its solve on its slot's stream with at most
+ * max(1, SMs / max_slots) CTAs per Euler launch (unless params.max_ctas is
+ * set) and cooperative launches, so the solves of several requests overlap on
+ * the GPU.  When a solve finishes, the worker copies its result to host memory
+ * and releases its device memory and slot at once.  A result is the same
+ * whether the request ran alone or among others (same work split, fixed
+ * summation order). */
+typedef struct cs_server cs_server;
+
+/* Errors: CS_EINVAL (max_slots outside [1, 256], zero budget), CS_ECUDA. */
+cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server** out);
+
+/* Queue one reconstruction: A (M x N row-major) and y (M) are HOST pointers,
+ * copied before the call returns; params and trials as for cs_solve (the
+ * server sets cluster_size = 1 and, if 0, max_ctas).  *ticket names the
+ * request.  Errors: CS_EINVAL, CS_ENOMEM if the request can never fit the
+ * budget. */
+cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,
+                           const cs_params* prm, int32_t trials, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the request has finished (or failed). */
+cs_status cs_server_poll(cs_server* sv, uint64_t ticket, int32_t* done);
+
+/* Block until the request has finished, at most timeout_ms (CS_ENOTREADY after). */
+cs_status cs_server_wait(cs_server* sv, uint64_t ticket, int64_t timeout_ms);
+
+/* Copy a finished request's result (host pointers, any may be NULL) and forget
+ * the ticket: x_hat (N), sigma_hat (N), energy, stats (CS_STATS_LEN, as for
+ * cs_result) and times[3] = submit, start (admission) and finish instants in
+ * seconds of a monotonic clock.  Returns the solve's status (CS_OK,
+ * CS_ESINGULAR or its error), CS_ENOTREADY if it has not finished. */
+cs_status cs_server_result(cs_server* sv, uint64_t ticket, double* x_hat, uint8_t* sigma_hat, double* energy,
+                           double* stats, double* times);
+
+/* Finish running requests, drop queued ones, release everything. */
+void cs_server_destroy(cs_server* sv);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* cs_last_error(void);

@@ -47,7 +47,7 @@ class cs_params(ctypes.Structure):
         ("field", ctypes.c_int32), ("refit", ctypes.c_int32), ("jacobi_dt", ctypes.c_double),
         ("jacobi_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
-        ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
+        ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
     ]
 
 
@@ -81,13 +81,22 @@ def lib():
         L.cs_problem_timing.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
         L.cs_objective_static.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_double, P, P]
+        L.cs_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(P)]
+        L.cs_server_submit.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+        L.cs_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
+        L.cs_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64]
+        L.cs_server_result.argtypes = [P, ctypes.c_uint64, P, P, P, P, P]
+        L.cs_server_destroy.argtypes = [P]
+        L.cs_server_destroy.restype = None
         L.cs_problem_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.cs_problem_destroy.argtypes = [P]
         L.cs_problem_destroy.restype = None
         L.cs_last_error.argtypes = []
         L.cs_last_error.restype = ctypes.c_char_p
         for name in ["cs_problem_create", "cs_solve", "cs_solve_batch", "cs_result", "cs_result_trials", "cs_trajectory",
-                     "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static"]:
+                     "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static",
+                     "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_wait", "cs_server_result"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -226,6 +235,49 @@ def cs_objective_static(A, y, sigma, R, lam: float, energy, stream=None) -> None
             raise ValueError("cs_objective_static takes contiguous CUDA tensors")
     _check(lib().cs_objective_static(A.data_ptr(), y.data_ptr(), sigma.data_ptr(), R.data_ptr(), M, N, T,
                                      float(lam), energy.data_ptr(), _stream_ptr(stream)))
+
+
+def cs_server_create(hbm_budget_bytes: int, max_slots: int):
+    h = ctypes.c_void_p()
+    _check(lib().cs_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+    return h
+
+
+def cs_server_submit(server, A, y, lam: float, params: cs_params, trials: int) -> int:
+    """Queue one request (host arrays); returns its ticket."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    t = ctypes.c_uint64()
+    _check(lib().cs_server_submit(server, A.ctypes.data, y.ctypes.data, A.shape[0], A.shape[1], float(lam),
+                                  ctypes.byref(params), int(trials), ctypes.byref(t)))
+    return t.value
+
+
+def cs_server_poll(server, ticket: int) -> bool:
+    d = ctypes.c_int32()
+    _check(lib().cs_server_poll(server, ticket, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def cs_server_wait(server, ticket: int, timeout_ms: int = 600000) -> None:
+    _check(lib().cs_server_wait(server, ticket, int(timeout_ms)))
+
+
+def cs_server_result(server, ticket: int, N: int):
+    """(x_hat, sigma_hat, energy, stats, times[submit, start, done], status) of a finished request."""
+    x = np.empty(N)
+    s = np.empty(N, dtype=np.uint8)
+    e = ctypes.c_double()
+    st = np.empty(CS_STATS_LEN)
+    tm = np.empty(3)
+    status = _check(lib().cs_server_result(server, ticket, x.ctypes.data, s.ctypes.data, ctypes.addressof(e),
+                                           st.ctypes.data, tm.ctypes.data), allow=(CS_OK, CS_ESINGULAR))
+    return x, s, e.value, st, tm, status
+
+
+def cs_server_destroy(server) -> None:
+    if server:
+        lib().cs_server_destroy(server)
 
 
 def cs_problem_shape(problem):

@@ -156,6 +156,7 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
       p->cluster_size != 8)
     return fail(CS_EINVAL, "cluster_size must be 0 (automatic), 1, 2, 4 or 8");
+  if (p->max_ctas < 0) return fail(CS_EINVAL, "max_ctas must be >= 0");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -422,7 +423,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
     L.outer = it;
     L.err = d_err;
     L.timeout_cycles = timeout_cycles;
-    L.ctas = P0.num_sms;
+    L.ctas = prm->max_ctas > 0 ? std::min(prm->max_ctas, P0.num_sms) : P0.num_sms;
     cudaError_t e = launch_euler_batch(L, stream);
     if (e == cudaErrorInvalidConfiguration) return fail(CS_EINVAL, "batched Euler kernel does not fit shared memory");
     CS_CUDA(e, "batched euler launch");

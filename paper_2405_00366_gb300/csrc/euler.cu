@@ -420,8 +420,9 @@ EulerFn<CT> kernel_for(int MR) {
 // clock, X bytes at 32 per clock, and a fixed cost per cluster rank for the
 // reduction through distributed shared memory.
 template <typename GT, typename CT>
-cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
+cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, Plan* out) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
+  const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
   const int twmax = round4(std::min(T, kTChunk));
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P.device);
@@ -440,10 +441,11 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, Plan* out) {
     pl.C = C;
     pl.kq = (nq + C - 1) / C;
     pl.kch = std::max(4, std::min(pl.kq * 4, (int)((8192 / (twmax * sizeof(CT))) & ~(size_t)3)));
-    for (int NC = std::min(P.num_sms / C, N); NC >= 1; --NC) {
+    if (sms < C) continue;
+    for (int NC = std::min(sms / C, N); NC >= 1; --NC) {
       pl.RPC = (N + NC - 1) / NC;
       pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
-      if (pl.NC != NC && NC != std::min(P.num_sms / C, N)) continue;
+      if (pl.NC != NC && NC != std::min(sms / C, N)) continue;
       // rows per row-warp, then row groups (a power of two that fits beside the
       // column groups, aiming at about four rows per lane) and rows per lane;
       // leftover lanes split k
@@ -508,16 +510,16 @@ template <typename GT, typename CT>
 cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
                          long long timeout_cycles) {
   // plans depend only on (N, T, hint) for a given device and precision
-  static thread_local struct { int64_t N; int T, hint, dev; Plan pl; bool valid; } cache = {0, 0, 0, -1, {}, false};
+  static thread_local struct { int64_t N; int T, hint, cap, dev; Plan pl; bool valid; } cache = {0, 0, 0, 0, -1, {}, false};
   Plan pl;
   if (cache.valid && cache.N == P.N && cache.T == S.trials && cache.hint == prm.cluster_size &&
-      cache.dev == P.device) {
+      cache.cap == prm.max_ctas && cache.dev == P.device) {
     pl = cache.pl;
   } else {
-    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, &pl);
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, &pl);
     if (e != cudaSuccess) return e;
-    cache.N = P.N; cache.T = S.trials; cache.hint = prm.cluster_size; cache.dev = P.device;
-    cache.pl = pl; cache.valid = true;
+    cache.N = P.N; cache.T = S.trials; cache.hint = prm.cluster_size; cache.cap = prm.max_ctas;
+    cache.dev = P.device; cache.pl = pl; cache.valid = true;
   }
   EulerArgs<CT> a;
   a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials;

@@ -1,0 +1,91 @@
+"""The continuous-batching server: requests of different shapes admitted by free
+slot and HBM budget, overlapping on the GPU, each giving the same result alone
+and in the mix, and the FP64 one matching the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import cs_inputs
+import oracle
+from paper_2405_00366_gb300 import cs
+
+ORACLE_KEYS = {"n_outer", "n_steps", "dt", "pump_kind", "p0", "p1", "p_thr", "d", "t0", "width", "beta", "tau",
+               "K", "j", "eta_init", "eta_end", "velo", "init_kind", "init_scale", "field", "refit", "seed"}
+
+
+def _requests():
+    base = cs_inputs.WORKLOADS["single_n200_fp64"]
+    return [
+        (cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=0), dict(base, n_outer=3, n_steps=600), 1),
+        (cs_inputs.random_instance(333, 200, 30, 0.01, 0.03, seed=1),
+         dict(base, n_outer=2, n_steps=500, precision="fp32"), 4),
+        (cs_inputs.random_instance(256, 128, 26, 0.01, 0.03, seed=2),
+         dict(base, n_outer=2, n_steps=500, precision="bf16"), 16),
+        (cs_inputs.random_instance(150, 90, 15, 0.01, 0.03, seed=3),
+         dict(base, n_outer=2, n_steps=400, precision="fp32", field="bn"), 2),
+    ]
+
+
+def _serve(reqs, slots=3, budget=8 << 30):
+    sv = cs.cs_server_create(budget, slots)
+    try:
+        tickets = [cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
+                   for inst, w, T in reqs]
+        out = []
+        for (inst, w, T), t in zip(reqs, tickets):
+            cs.cs_server_wait(sv, t)
+            assert cs.cs_server_poll(sv, t)
+            out.append(cs.cs_server_result(sv, t, inst.N))
+    finally:
+        cs.cs_server_destroy(sv)
+    return out
+
+
+@pytest.mark.gpu
+def test_results_same_alone_and_in_the_mix():
+    reqs = _requests()
+    mixed = _serve(reqs)
+    for k, req in enumerate(reqs):
+        alone = _serve([req])[0]
+        np.testing.assert_array_equal(alone[0], mixed[k][0])  # x_hat, bit for bit
+        np.testing.assert_array_equal(alone[1], mixed[k][1])
+        assert alone[2] == mixed[k][2]
+    # the FP64 request against the oracle
+    inst, w, T = reqs[0]
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS}),
+                     trials=T)
+    np.testing.assert_array_equal(mixed[0][1], r["sigma"])
+    np.testing.assert_allclose(mixed[0][0], r["x_hat"], rtol=0, atol=1e-9)
+
+
+@pytest.mark.gpu
+def test_budget_admission_and_ticket_lifecycle():
+    reqs = [_requests()[1]] * 3  # about 6.5 MB of device memory each
+    # room for one request at a time: each starts after the previous finished
+    sv = cs.cs_server_create(10 << 20, 3)
+    try:
+        with pytest.raises(cs.CSError) as ei:  # can never fit
+            big = cs_inputs.random_instance(4000, 100, 10, 0.0, 0.1, seed=9)
+            cs.cs_server_submit(sv, big.A, big.y, big.lam, cs.cs_params_default(), 64)
+        assert ei.value.status == cs.CS_ENOMEM
+        tickets = [cs.cs_server_submit(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in reqs]
+        times = []
+        for (inst, w, T), t in zip(reqs, tickets):
+            cs.cs_server_wait(sv, t)
+            res = cs.cs_server_result(sv, t, inst.N)
+            times.append(res[4])
+            with pytest.raises(cs.CSError):  # the ticket is gone once its result is read
+                cs.cs_server_result(sv, t, inst.N)
+        for a, b in zip(times, times[1:]):
+            assert b[1] >= a[2] - 1e-3  # admitted only after the previous one finished
+    finally:
+        cs.cs_server_destroy(sv)
+
+
+def test_server_argument_checks_need_no_gpu():
+    h = ctypes.c_void_p()
+    assert cs.lib().cs_server_create(0, 2, ctypes.byref(h)) == cs.CS_EINVAL
+    assert cs.lib().cs_server_create(1 << 30, 0, ctypes.byref(h)) == cs.CS_EINVAL
+    d = ctypes.c_int32()
+    assert cs.lib().cs_server_poll(None, 1, ctypes.byref(d)) == cs.CS_EINVAL
