@@ -47,8 +47,9 @@ enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1 };   /* normal equations / damped
 enum { CS_PUMP_LINEAR = 0, CS_PUMP_SIGMOID = 1 };   /* p0 -> p1 ramp / Eq. pumprateGACS */
 enum { CS_INIT_UNIFORM = 0, CS_INIT_NORMAL = 1 };   /* U(-s, s) / N(0, s^2) */
 /* Storage precision of the coupling matrix G and arithmetic of the Euler loop:
- * FP64 keeps G and the amplitudes in double; the others accumulate in float. */
-enum { CS_P_FP64 = 0, CS_P_FP32 = 1, CS_P_BF16 = 2, CS_P_FP16 = 3 };
+ * FP64 keeps G and the amplitudes in double; the others accumulate in float.
+ * FP8 is E4M3 with one FP32 scale per row of G_off (its largest magnitude / 448). */
+enum { CS_P_FP64 = 0, CS_P_FP32 = 1, CS_P_BF16 = 2, CS_P_FP16 = 3, CS_P_FP8 = 4 };
 
 /* Run parameters (Methods and Numerical experiments of the paper).
  * Fill with cs_params_default() and override. */

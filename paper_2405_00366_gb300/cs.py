@@ -24,10 +24,10 @@ CS_FIELD_CN, CS_FIELD_BN = 0, 1
 CS_REFIT_EXACT, CS_REFIT_JACOBI = 0, 1
 CS_PUMP_LINEAR, CS_PUMP_SIGMOID = 0, 1
 CS_INIT_UNIFORM, CS_INIT_NORMAL = 0, 1
-CS_P_FP64, CS_P_FP32, CS_P_BF16, CS_P_FP16 = 0, 1, 2, 3
+CS_P_FP64, CS_P_FP32, CS_P_BF16, CS_P_FP16, CS_P_FP8 = 0, 1, 2, 3, 4
 CS_STATS_LEN = 10
 
-PRECISIONS = {"fp64": CS_P_FP64, "fp32": CS_P_FP32, "bf16": CS_P_BF16, "fp16": CS_P_FP16}
+PRECISIONS = {"fp64": CS_P_FP64, "fp32": CS_P_FP32, "bf16": CS_P_BF16, "fp16": CS_P_FP16, "fp8": CS_P_FP8}
 FIELDS = {"cn": CS_FIELD_CN, "bn": CS_FIELD_BN}
 PUMPS = {"linear": CS_PUMP_LINEAR, "sigmoid": CS_PUMP_SIGMOID}
 INITS = {"uniform": CS_INIT_UNIFORM, "normal": CS_INIT_NORMAL}

@@ -80,7 +80,7 @@ void free_solve(SolveDev& S, cudaStream_t st) {
 }
 
 void free_problem(ProblemDev& P) {
-  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.Gt, P.flag};
+  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.Gt, P.gscale, P.flag};
   for (void* q : ptrs) dev_free(q, P.stream);
   P = ProblemDev();
 }
@@ -148,7 +148,7 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->init_kind != CS_INIT_UNIFORM && p->init_kind != CS_INIT_NORMAL) return fail(CS_EINVAL, "bad init_kind");
   if (p->field != CS_FIELD_CN && p->field != CS_FIELD_BN) return fail(CS_EINVAL, "bad field");
   if (p->refit != CS_REFIT_EXACT) return fail(CS_EINVAL, "only the exact refit is available");
-  if (p->precision < CS_P_FP64 || p->precision > CS_P_FP16) return fail(CS_EINVAL, "bad precision");
+  if (p->precision < CS_P_FP64 || p->precision > CS_P_FP8) return fail(CS_EINVAL, "bad precision");
   if (p->eta_init > 0.0 && !(p->velo > 0.0)) return fail(CS_EINVAL, "velo must be > 0 with an eta schedule");
   if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
   if (p->timeout_ms <= 0) return fail(CS_EINVAL, "timeout_ms must be > 0");

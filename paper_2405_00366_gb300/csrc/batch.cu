@@ -39,10 +39,15 @@ template <> __device__ __forceinline__ double to_storage<double>(double v) { ret
 template <> __device__ __forceinline__ float to_storage<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 template <> __device__ __forceinline__ __half to_storage<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_fp8_e4m3 to_storage<__nv_fp8_e4m3>(double v) {
+  return __nv_fp8_e4m3((float)v);
+}
 
-// Tiled, swizzled copy of G_off (see the file comment).
+// Tiled, swizzled copy of G_off (see the file comment), divided by its row
+// scales when the storage type is row-scaled.
 template <typename GT>
-__global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int nrt, int nkc) {
+__global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int nrt, int nkc,
+                                   const float* __restrict__ gscale) {
   const size_t total = (size_t)nrt * nkc * kRT * kKC;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -52,7 +57,8 @@ __global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict_
     const int rt = (int)(tile / nkc), kc = (int)(tile % nkc);
     const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
     const int row = rt * kRT + r, col = kc * kKC + k;
-    const double v = (row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
+    double v = (row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
+    if constexpr (row_scaled<GT>::value) v = row < N ? v / gscale[row] : 0.0;
     Gt[idx] = to_storage<GT>(v);
   }
 }
@@ -61,6 +67,7 @@ template <typename CT>
 struct BInst {
   int N, nrt, nkc;         // rows, row tiles, column tiles (nkc * kKC = Npad)
   const void* Gt;          // tiled G_off
+  const float* gscale;     // row scales (FP8 storage)
   const double* R;         // N x T
   const double* hz;        // N
   CT* X0;                  // Npad x twp, rows >= N zero
@@ -217,7 +224,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int r = rt * kRT + idx / T, t = idx % T;
         if (r >= N) continue;
-        const double v = (double)P[(size_t)(idx / T) * twp + t];
+        const double v = (double)(P[(size_t)(idx / T) * twp + t] * row_scale<GT, CT>(I.gscale, r));
         const size_t o = (size_t)r * T + t;
         b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta);
       }
@@ -253,7 +260,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
         const int rl = idx / T, t = idx % T, r = rt * kRT + rl;
         if (r >= N) continue;
         const size_t o = (size_t)r * T + t;
-        const CT U = P[(size_t)rl * twp + t];
+        const CT U = P[(size_t)rl * twp + t] * row_scale<GT, CT>(I.gscale, r);
         const CT Rr = CT(I.R[o]);
         const CT f = wcoef * Rr * U + b[o];
         const CT cc = c[o], ee = e[o];
@@ -381,19 +388,27 @@ int64_t tiled_elems(int64_t N, int64_t Npad) {
 cudaError_t launch_store_tiled(ProblemDev& P, int precision) {
   if (P.gt_prec == precision && P.Gt) return cudaSuccess;
   if (P.Gt) { dev_free(P.Gt, P.stream); P.Gt = nullptr; P.gt_prec = -1; }
-  const size_t gb = precision == CS_P_FP64 ? 8 : precision == CS_P_FP32 ? 4 : 2;
+  const size_t gb = storage_bytes(precision);
   const int64_t elems = tiled_elems(P.N, P.Npad);
   cudaError_t e = dev_alloc(&P.Gt, (size_t)elems * gb, P.stream);
   if (e != cudaSuccess) return e;
   const int N = (int)P.N, nrt = (int)((P.N + kRT - 1) / kRT), nkc = (int)(P.Npad / kKC);
   const int blocks = P.num_sms * 4;
+  float* sc = P.gscale;
   switch (precision) {
-    case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc); break;
-    case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc); break;
+    case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc, sc); break;
+    case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc, sc); break;
     case CS_P_BF16:
-      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc);
+      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc, sc);
       break;
-    case CS_P_FP16: store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc); break;
+    case CS_P_FP16:
+      store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc, sc);
+      break;
+    case CS_P_FP8:
+      if ((e = ensure_row_scales(P)) != cudaSuccess) return e;
+      store_tiled_kernel<__nv_fp8_e4m3><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_fp8_e4m3*)P.Gt, N, nrt, nkc,
+                                                                      P.gscale);
+      break;
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();
@@ -407,14 +422,14 @@ void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int prec
   if (precision == CS_P_FP64) {
     BInst<double> I;
     I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
-    I.Gt = P.Gt; I.R = S.R; I.hz = P.hz;
+    I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
     I.X0 = (double*)S.X0; I.X1 = (double*)S.X1; I.state = (double*)S.state; I.sigma = S.sigma;
     I.theta = theta; I.inst = inst;
     *reinterpret_cast<BInst<double>*>(dst) = I;
   } else {
     BInst<float> I;
     I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
-    I.Gt = P.Gt; I.R = S.R; I.hz = P.hz;
+    I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
     I.X0 = (float*)S.X0; I.X1 = (float*)S.X1; I.state = (float*)S.state; I.sigma = S.sigma;
     I.theta = theta; I.inst = inst;
     *reinterpret_cast<BInst<float>*>(dst) = I;
@@ -427,6 +442,7 @@ cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st) {
     case CS_P_FP32: return launch_batch_mr<float, float>(L, st);
     case CS_P_BF16: return launch_batch_mr<__nv_bfloat16, float>(L, st);
     case CS_P_FP16: return launch_batch_mr<__half, float>(L, st);
+    case CS_P_FP8: return launch_batch_mr<__nv_fp8_e4m3, float>(L, st);
     default: return cudaErrorInvalidValue;
   }
 }

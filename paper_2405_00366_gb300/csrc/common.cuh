@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "../../include/cs.h"
@@ -18,6 +19,12 @@ template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; 
 template <> __device__ __forceinline__ float to_f32<double>(double v) { return (float)v; }
 template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<__nv_fp8_e4m3>(__nv_fp8_e4m3 v) { return float(v); }
+
+// Storage types whose values carry a per-row scale (the row's largest |G_off|
+// over the format's largest finite value): only FP8.
+template <typename GT> struct row_scaled { static constexpr bool value = false; };
+template <> struct row_scaled<__nv_fp8_e4m3> { static constexpr bool value = true; };
 
 // widen a storage value to the compute type CT
 template <typename CT, typename GT> __device__ __forceinline__ CT widen(GT v) { return (CT)to_f32(v); }

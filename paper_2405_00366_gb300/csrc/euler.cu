@@ -64,6 +64,7 @@ struct EulerArgs {
   int RG;       // row groups of a warp
   int RPC_pad;  // staged rows per CTA (multiple of 8 RW >= RPC; padding rows are zero)
   const void* Gs;  // Npad x Npad storage-precision G_off
+  const float* gscale;  // row scales of G_off (FP8 storage only)
   const double* R;
   const double* hz;
   CT* X0;
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
-        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C);
         const int gr = row0 + own0 + r;
+        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr);
         const double Rr = a.R[(size_t)gr * T + t0 + tt];
         b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
       }
@@ -357,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
-        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C);
+        const CT U =
+            sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, row0 + own0 + r);
         const size_t so = (size_t)r * T + t0 + tt;
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
@@ -527,7 +529,7 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
   a.C = pl.C; a.RPC = pl.RPC; a.ORW = pl.ORW; a.kq = pl.kq; a.kch = pl.kch; a.slots = pl.slots; a.RW = pl.RW;
   a.RPC_pad = pl.RPC_pad;
   a.RG = pl.RG;
-  a.Gs = P.Gs; a.R = S.R; a.hz = P.hz;
+  a.Gs = P.Gs; a.gscale = P.gscale; a.R = S.R; a.hz = P.hz;
   a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
   a.sigma = S.sigma;
   a.record_steps = (outer == 0) ? std::min(S.record_steps, prm.n_steps) : 0;
@@ -585,6 +587,7 @@ cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm,
     case CS_P_FP32: return launch_typed<float, float>(P, S, prm, outer, eta, timeout_cycles);
     case CS_P_BF16: return launch_typed<__nv_bfloat16, float>(P, S, prm, outer, eta, timeout_cycles);
     case CS_P_FP16: return launch_typed<__half, float>(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_FP8: return launch_typed<__nv_fp8_e4m3, float>(P, S, prm, outer, eta, timeout_cycles);
     default: return cudaErrorInvalidValue;
   }
 }

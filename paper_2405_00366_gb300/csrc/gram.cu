@@ -93,16 +93,40 @@ template <> __device__ __forceinline__ double narrow<double>(double v) { return 
 template <> __device__ __forceinline__ float narrow<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 template <> __device__ __forceinline__ __half narrow<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_fp8_e4m3 narrow<__nv_fp8_e4m3>(double v) {
+  return __nv_fp8_e4m3((float)v);
+}
 
-// Gs = G with a zero diagonal, rounded to GT, zero-padded to Npad x Npad.
+// Gs = G with a zero diagonal, rounded to GT (divided by its row's scale when GT
+// is row-scaled), zero-padded to Npad x Npad.
 template <typename GT>
-__global__ void store_coupling_kernel(const double* __restrict__ G, GT* __restrict__ Gs, int N, int Npad) {
+__global__ void store_coupling_kernel(const double* __restrict__ G, GT* __restrict__ Gs, int N, int Npad,
+                                      const float* __restrict__ gscale) {
   const size_t total = (size_t)Npad * Npad;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / Npad), j = (int)(idx % Npad);
-    const double v = (i < N && j < N && i != j) ? G[(size_t)i * N + j] : 0.0;
+    double v = (i < N && j < N && i != j) ? G[(size_t)i * N + j] : 0.0;
+    if constexpr (row_scaled<GT>::value) v = i < N ? v / gscale[i] : 0.0;
     Gs[idx] = narrow<GT>(v);
+  }
+}
+
+// Row scales for FP8 storage: s_r = max_{k != r} |G_rk| / 448 (E4M3's largest
+// finite value), 1 for an all-zero row.  One block per row.
+__global__ void row_scale_kernel(const double* __restrict__ G, float* __restrict__ gscale, int N) {
+  __shared__ double red[8];
+  const int r = blockIdx.x;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    if (k != r) m = fmax(m, fabs(G[(size_t)r * N + k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
+    gscale[r] = mm > 0.0 ? (float)(mm / 448.0) : 1.0f;
   }
 }
 
@@ -123,8 +147,17 @@ size_t storage_bytes(int precision) {
   switch (precision) {
     case CS_P_FP64: return 8;
     case CS_P_FP32: return 4;
+    case CS_P_FP8: return 1;
     default: return 2;
   }
+}
+
+cudaError_t ensure_row_scales(ProblemDev& P) {
+  if (P.gscale) return cudaSuccess;
+  cudaError_t e = dev_alloc((void**)&P.gscale, (size_t)P.N * sizeof(float), P.stream);
+  if (e != cudaSuccess) return e;
+  row_scale_kernel<<<(int)P.N, 256, 0, P.stream>>>(P.G, P.gscale, (int)P.N);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_store_coupling(ProblemDev& P, int precision) {
@@ -135,11 +168,19 @@ cudaError_t launch_store_coupling(ProblemDev& P, int precision) {
   if (e != cudaSuccess) return e;
   const int N = (int)P.N, Npad = (int)P.Npad;
   const int blocks = P.num_sms * 4;
+  float* sc = P.gscale;
   switch (precision) {
-    case CS_P_FP64: store_coupling_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gs, N, Npad); break;
-    case CS_P_FP32: store_coupling_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gs, N, Npad); break;
-    case CS_P_BF16: store_coupling_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gs, N, Npad); break;
-    case CS_P_FP16: store_coupling_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gs, N, Npad); break;
+    case CS_P_FP64: store_coupling_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gs, N, Npad, sc); break;
+    case CS_P_FP32: store_coupling_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gs, N, Npad, sc); break;
+    case CS_P_BF16:
+      store_coupling_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gs, N, Npad, sc);
+      break;
+    case CS_P_FP16: store_coupling_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gs, N, Npad, sc); break;
+    case CS_P_FP8:
+      if ((e = ensure_row_scales(P)) != cudaSuccess) return e;
+      store_coupling_kernel<__nv_fp8_e4m3><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_fp8_e4m3*)P.Gs, N, Npad,
+                                                                         P.gscale);
+      break;
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();

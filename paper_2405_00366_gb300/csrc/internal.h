@@ -41,6 +41,7 @@ struct ProblemDev {
   int gs_prec = -1;       // precision held in Gs
   void* Gt = nullptr;     // G_off in storage precision, tiled for streaming (batched solves)
   int gt_prec = -1;
+  float* gscale = nullptr; // N row scales of G_off for FP8 storage (largest |G_off[r][k]| / 448)
   int* flag = nullptr;    // device word: nonzero if A or y had a non-finite value
   int64_t launches = 0;   // kernels launched by the last create + solve
 };
@@ -113,6 +114,8 @@ struct BatchLaunch {
 size_t batch_inst_bytes();
 void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst);
 cudaError_t launch_store_tiled(ProblemDev& P, int precision);
+cudaError_t ensure_row_scales(ProblemDev& P);
+size_t storage_bytes(int precision);
 cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);
 
 // Launchers (stream-ordered, no synchronisation).

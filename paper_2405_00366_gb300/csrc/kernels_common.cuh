@@ -51,4 +51,21 @@ __device__ __forceinline__ void load4<float, __half>(const __half* p, float out[
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
+template <>
+__device__ __forceinline__ void load4<float, __nv_fp8_e4m3>(const __nv_fp8_e4m3* p, float out[4]) {
+  const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(v & 0xffffu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(v >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
+// Scale of row r of G_off in its storage type (1 unless the type is row-scaled).
+template <typename GT, typename CT>
+__device__ __forceinline__ CT row_scale(const float* gscale, int r) {
+  if constexpr (row_scaled<GT>::value) return CT(gscale[r]);
+  return CT(1);
+}
+
 }  // namespace cs

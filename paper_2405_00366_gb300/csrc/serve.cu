@@ -54,7 +54,7 @@ struct Request {
 size_t request_bytes(int64_t M, int64_t N, int trials, int precision) {
   const size_t n = (size_t)N, m = (size_t)M, T = (size_t)trials;
   const size_t np = (n + cs::kPadN - 1) / cs::kPadN * cs::kPadN;
-  const size_t gb = precision == CS_P_FP64 ? 8 : precision == CS_P_FP32 ? 4 : 2;
+  const size_t gb = cs::storage_bytes(precision);
   const size_t cb = precision == CS_P_FP64 ? 8 : 4;
   size_t b = m * n * 8 + n * n * 8 + np * np * gb;          // A, G, G_off
   b += n * T * (8 + 3 * cb + 1 + 4) + 2 * np * ((T + 3) / 4 * 4) * cb;  // R, state, sigma, sidx, X
