@@ -114,6 +114,11 @@ WORKLOADS = {
     "trials64_n2000_fp32": dict(
         N=2000, M=1200, nnz=200, nu=0.01, lam=0.03, seed=0, trials=64,
         n_outer=30, n_steps=2000, precision="fp32", **_COMMON),
+    # 128 x 128 Haar-sparse image through a subsampled 2-D DCT (N=16384, M=4915),
+    # 8 trials, FP16 storage; K = 0.1 as in the paper's MRI runs
+    "mri_n16384_fp16": dict(
+        mri_side=128, N=16384, M=4915, nnz=1638, nu=0.0, lam=0.01, seed=0, trials=8,
+        n_outer=40, n_steps=3000, precision="fp16", **dict(_COMMON, K=0.1)),
 }
 
 
@@ -126,4 +131,77 @@ def workload(name: str, **overrides):
 
 def workload_instance(w) -> Instance:
     """The seeded instance of a workload dict."""
+    if "mri_side" in w:
+        return mri_instance(w["mri_side"], w["nnz"] / w["N"], w["M"] / w["N"], w["lam"], w["seed"])
     return random_instance(w["N"], w["M"], w["nnz"], w["nu"], w["lam"], w["seed"])
+
+
+def haar_1d_matrix(n: int) -> np.ndarray:
+    """Orthonormal multilevel 1-D Haar transform of length n (a power of two), as a
+    matrix H1 with coefficients = H1 @ signal: averages and differences of
+    neighbouring pairs scaled by 1/sqrt(2), applied again to the averages."""
+    if n & (n - 1):
+        raise ValueError("n must be a power of two")
+    H = np.eye(n)
+    m = n
+    while m > 1:
+        half = m // 2
+        step = np.eye(n)
+        blk = np.zeros((m, m))
+        for k in range(half):
+            blk[k, 2 * k] = blk[k, 2 * k + 1] = 1.0 / math.sqrt(2.0)
+            blk[half + k, 2 * k] = 1.0 / math.sqrt(2.0)
+            blk[half + k, 2 * k + 1] = -1.0 / math.sqrt(2.0)
+        step[:m, :m] = blk
+        H = step @ H
+        m = half
+    return H
+
+
+def dct_1d_matrix(n: int) -> np.ndarray:
+    """Orthonormal DCT-II matrix: row u is c_u cos(pi (2x + 1) u / (2n))."""
+    x = np.arange(n)
+    u = np.arange(n)[:, None]
+    D = np.cos(math.pi * (2 * x[None, :] + 1) * u / (2 * n))
+    D[0] *= math.sqrt(1.0 / n)
+    D[1:] *= math.sqrt(2.0 / n)
+    return D
+
+
+def mri_instance(n_side: int = 128, sparsity: float = 0.1, alpha: float = 0.3, lam: float = 0.01,
+                 seed: int = 0) -> Instance:
+    """MRI-shaped synthetic problem (stand-in for the paper's brain image, which is
+    not available): an n x n image sparse in the 2-D Haar domain, observed through
+    a variable-density subsample of its orthonormal 2-D DCT.
+
+    x0: a fraction `sparsity` of the N = n^2 Haar coefficients nonzero, positions
+    uniform, values Laplace(0, 1).  The 2-D Haar transform is the separable one
+    (the 1-D multilevel transform along each axis), so with image = Haar^T x0 and
+    measured frequencies f_i = (u_i, v_i), row i of A = S DCT2 Haar^T is
+    kron(H1 phi_u, H1 phi_v), phi_u the u-th DCT basis vector.  M = round(alpha N)
+    frequencies are drawn without replacement with density
+    p(u, v) ~ max(0.02, (1 - sqrt(u^2 + v^2) / (sqrt(2) n))^2), DC always kept.
+    The rows of A are orthonormal; y = A x0 (noise-free).  Draw order: support,
+    values, frequencies.
+    """
+    n = n_side
+    N = n * n
+    M = int(round(alpha * N))
+    rng = np.random.default_rng(seed)
+    K = int(round(sparsity * N))
+    support = np.sort(rng.choice(N, size=K, replace=False))
+    x0 = np.zeros(N)
+    x0[support] = rng.laplace(0.0, 1.0, size=K)
+    xi = np.zeros(N, dtype=np.uint8)
+    xi[support] = 1
+    u, v = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    dens = np.maximum(0.02, (1.0 - np.sqrt(u ** 2 + v ** 2) / (math.sqrt(2.0) * n)) ** 2).ravel()
+    dens[0] = 0.0
+    dens /= dens.sum()
+    freq = np.concatenate([[0], rng.choice(N, size=M - 1, replace=False, p=dens)])
+    H1 = haar_1d_matrix(n)
+    B = H1 @ dct_1d_matrix(n).T  # column u = H1 phi_u
+    fu, fv = freq // n, freq % n
+    A = np.einsum("mi,mj->mij", B[:, fu].T, B[:, fv].T).reshape(M, N)
+    y = A @ x0
+    return Instance(A=np.ascontiguousarray(A), y=y, x0=x0, xi=xi, lam=float(lam))

@@ -83,6 +83,8 @@ typedef struct {
                            library's planner, or 1, 2, 4, 8 */
   int32_t max_ctas;     /* at most this many CTAs (SMs) per Euler launch, 0 = all; lets solves
                            on different streams share the GPU */
+  int32_t stream_g;     /* 0: keep G_off on chip when it fits, else stream its tiles from memory
+                           every step; 1: always stream (FP32/BF16/FP16/FP8 only) */
 } cs_params;
 
 typedef struct cs_problem cs_problem;

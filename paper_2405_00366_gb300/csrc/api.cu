@@ -80,7 +80,7 @@ void free_solve(SolveDev& S, cudaStream_t st) {
 }
 
 void free_problem(ProblemDev& P) {
-  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.Gt, P.gscale, P.flag};
+  void* ptrs[] = {P.A, P.y, P.G, P.hz, P.g, P.Gs, P.Gt, P.Gt2, P.gscale, P.flag};
   for (void* q : ptrs) dev_free(q, P.stream);
   P = ProblemDev();
 }
@@ -157,6 +157,8 @@ cs_status check_params(const cs_params* p, int trials) {
       p->cluster_size != 8)
     return fail(CS_EINVAL, "cluster_size must be 0 (automatic), 1, 2, 4 or 8");
   if (p->max_ctas < 0) return fail(CS_EINVAL, "max_ctas must be >= 0");
+  if (p->stream_g != 0 && p->stream_g != 1) return fail(CS_EINVAL, "stream_g must be 0 or 1");
+  if (p->stream_g == 1 && p->precision == CS_P_FP64) return fail(CS_EINVAL, "FP64 G_off is never streamed");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)

@@ -34,15 +34,6 @@ constexpr int kBThreads = (kBWarps + 1) * 32;  // + one producer warp
 constexpr int kRT = 128;                       // rows per tile (16 per consumer warp)
 constexpr int kKC = 32;                        // columns (k) per tile
 
-template <typename GT> __device__ __forceinline__ GT to_storage(double v);
-template <> __device__ __forceinline__ double to_storage<double>(double v) { return v; }
-template <> __device__ __forceinline__ float to_storage<float>(double v) { return (float)v; }
-template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
-template <> __device__ __forceinline__ __half to_storage<__half>(double v) { return __double2half(v); }
-template <> __device__ __forceinline__ __nv_fp8_e4m3 to_storage<__nv_fp8_e4m3>(double v) {
-  return __nv_fp8_e4m3((float)v);
-}
-
 // Tiled, swizzled copy of G_off (see the file comment), divided by its row
 // scales when the storage type is row-scaled.
 template <typename GT>

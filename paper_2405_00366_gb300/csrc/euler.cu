@@ -30,6 +30,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -61,6 +62,10 @@ struct EulerArgs {
   int kch;      // k rows per bulk copy (multiple of 4)
   int slots;    // ring slots
   int RW;       // rows per consumer warp (RG * MR; RPC_pad = 8 RW rows are staged)
+  size_t slot_bytes;  // bytes of one ring slot
+  size_t xoff;        // offset of the X chunk inside a slot (after the G tile when streaming)
+  const void* Gt2;    // streamed G_off tiles [cluster][k tile][RPC_pad][32] (streaming plans)
+  int nkct;           // k tiles of 32 columns (Npad / 32)
   int RG;       // row groups of a warp
   int RPC_pad;  // staged rows per CTA (multiple of 8 RW >= RPC; padding rows are zero)
   const void* Gs;  // Npad x Npad storage-precision G_off
@@ -98,21 +103,45 @@ __host__ __device__ __forceinline__ int xwidth(int t0, int T) {
   return round4(T - t0 < kTChunk ? T - t0 : kTChunk);
 }
 
-// Shared-memory layout of one CTA (byte offsets).
+// Shared-memory layout of one CTA (byte offsets): resident G block (absent when
+// streaming), ring, partials, owned state, mbarriers.
 struct Smem {
   size_t g, ring, part, st, bars, total;
 };
-__host__ __device__ __forceinline__ Smem smem_layout(int RPC_pad, int kq, int slots, int kch, int twmax, int ORW,
-                                                     int T, size_t gbytes, size_t cbytes) {
-  const int RPC = RPC_pad;
+__host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t slot_bytes, int slots, int RPC_pad,
+                                                     int twmax, int ORW, int T, size_t cbytes) {
   Smem s;
   s.g = 0;
-  s.ring = align128((size_t)RPC * kq * 4 * gbytes);
-  s.part = s.ring + align128((size_t)slots * kch * twmax * cbytes);
-  s.st = s.part + align128((size_t)RPC * twmax * cbytes);
+  s.ring = align128(gbytes_block);
+  s.part = s.ring + align128((size_t)slots * slot_bytes);
+  s.st = s.part + align128((size_t)RPC_pad * twmax * cbytes);
   s.bars = s.st + align128((size_t)4 * ORW * T * cbytes);
   s.total = s.bars + 2 * (size_t)slots * sizeof(uint64_t);
   return s;
+}
+
+// Streamed G_off tiles of a cluster plan: tile (cluster c, k tile kc) holds rows
+// [c RPC, c RPC + RPC_pad) (zero past the cluster's rows and past N) and
+// columns [32 kc, 32 kc + 32), contiguous, with the quad q of row r at
+// q ^ (r & 7) so that the row groups of a warp read distinct banks.
+constexpr int kStreamK = 32;
+
+template <typename GT>
+__global__ void store_cluster_tiles_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int RPC,
+                                           int RPC_pad, int NC, int nkct, const float* __restrict__ gscale) {
+  const size_t total = (size_t)NC * nkct * RPC_pad * kStreamK;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t tile = idx / ((size_t)RPC_pad * kStreamK);
+    const int within = (int)(idx % ((size_t)RPC_pad * kStreamK));
+    const int r = within / kStreamK, kp = within % kStreamK;
+    const int c = (int)(tile / nkct), kc = (int)(tile % nkct);
+    const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    const int row = c * RPC + r, col = kc * kStreamK + k;
+    double v = (r < RPC && row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
+    if constexpr (row_scaled<GT>::value) v = (r < RPC && row < N) ? v / gscale[row] : 0.0;
+    Gt[idx] = to_storage<GT>(v);
+  }
 }
 
 // Partial products of this CTA's block for one block of trials:
@@ -125,11 +154,11 @@ __host__ __device__ __forceinline__ Smem smem_layout(int RPC_pad, int kq, int sl
 // groups) over every KG-th k-quad of each chunk, and the k groups are summed
 // with shuffles at the end.  The inner loop loads four k-rows of X and MR x 4
 // entries of G, then issues 16 MR independent FMAs.
-template <typename GT, typename CT, int MR>
+template <typename GT, typename CT, int MR, bool STREAM>
 __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                  const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
-                                                 CT* ring, CT* P, uint64_t* full, uint64_t* empty,
-                                                 unsigned& gctr) {
+                                                 int cl, unsigned char* ring, CT* P, uint64_t* full,
+                                                 uint64_t* empty, unsigned& gctr) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   const int ldg = a.kq * 4;
@@ -146,8 +175,17 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
         }
         const int kr = min(a.kch, klen - ci * a.kch);
         const unsigned bytes = (unsigned)((size_t)kr * twp * sizeof(CT));
-        mbar_arrive_expect_tx(full + s, bytes);
-        bulk_copy_g2s(ring + (size_t)s * a.kch * twp, Xblk + (size_t)(k0 + ci * a.kch) * twp, bytes, full + s);
+        unsigned char* slot = ring + (size_t)s * a.slot_bytes;
+        if constexpr (STREAM) {
+          const unsigned gtb = (unsigned)((size_t)a.RPC_pad * kStreamK * sizeof(GT));
+          const size_t kc = (size_t)(k0 + ci * a.kch) / kStreamK;
+          const GT* src = reinterpret_cast<const GT*>(a.Gt2) + ((size_t)cl * a.nkct + kc) * a.RPC_pad * kStreamK;
+          mbar_arrive_expect_tx(full + s, gtb + bytes);
+          bulk_copy_g2s(slot, src, gtb, full + s);
+        } else {
+          mbar_arrive_expect_tx(full + s, bytes);
+        }
+        bulk_copy_g2s(slot + a.xoff, Xblk + (size_t)(k0 + ci * a.kch) * twp, bytes, full + s);
       }
     }
     gctr += nch;
@@ -180,16 +218,24 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
       if (l == 0) set_error(a.err, DEV_TIMEOUT);
     }
     if (ok && colok) {
-      const CT* xs = ring + (size_t)s * a.kch * twp + col;
+      const CT* xs = reinterpret_cast<const CT*>(ring + (size_t)s * a.slot_bytes + a.xoff) + col;
       const int kr = min(a.kch, klen - ci * a.kch);
-      const GT* gk = Gsm + (size_t)rbase * ldg + ci * a.kch;
+      const GT* gk = STREAM ? reinterpret_cast<const GT*>(ring + (size_t)s * a.slot_bytes) + (size_t)rbase * kStreamK
+                            : Gsm + (size_t)rbase * ldg + ci * a.kch;
 #pragma unroll 2
       for (int kk = 4 * kg; kk < kr; kk += 4 * KG) {
         CT xv[4][4], gv[MR][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(kk + j) * twp, xv[j]);
 #pragma unroll
-        for (int i = 0; i < MR; ++i) load4<CT, GT>(gk + (size_t)(RG * i) * ldg + kk, gv[i]);
+        for (int i = 0; i < MR; ++i) {
+          if constexpr (STREAM) {
+            const int r = rbase + RG * i;
+            load4<CT, GT>(gk + (size_t)(RG * i) * kStreamK + 4 * ((kk >> 2) ^ (r & 7)), gv[i]);
+          } else {
+            load4<CT, GT>(gk + (size_t)(RG * i) * ldg + kk, gv[i]);
+          }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -234,7 +280,7 @@ __device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, si
   return s;
 }
 
-template <typename GT, typename CT, int MR>
+template <typename GT, typename CT, int MR, bool STREAM>
 __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -251,9 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   const int own0 = j * a.ORW;                      // first owned row (cluster-local)
   const int nown = max(0, min(a.ORW, nrows - own0));
   const int twmax = round4(min(T, kTChunk));
-  const Smem L = smem_layout(a.RPC_pad, a.kq, a.slots, a.kch, twmax, a.ORW, T, sizeof(GT), sizeof(CT));
+  const Smem L = smem_layout(STREAM ? 0 : (size_t)a.RPC_pad * a.kq * 4 * sizeof(GT), a.slot_bytes, a.slots,
+                             a.RPC_pad, twmax, a.ORW, T, sizeof(CT));
   GT* Gsm = reinterpret_cast<GT*>(smem_raw + L.g);
-  CT* ring = reinterpret_cast<CT*>(smem_raw + L.ring);
+  unsigned char* ring = smem_raw + L.ring;
   CT* P = reinterpret_cast<CT*>(smem_raw + L.part);
   CT* c_s = reinterpret_cast<CT*>(smem_raw + L.st);
   CT* e_s = c_s + (size_t)a.ORW * T;
@@ -270,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     fence_mbar_init();
   }
   // Stage this CTA's block of G_off: rows [row0, row0 + nrows), k in [k0, k0 + klen).
-  {
+  if (!STREAM) {
     const GT* src = reinterpret_cast<const GT*>(a.Gs);
     const int ldg = a.kq * 4;
     const int total = a.RPC_pad * nqj;
@@ -310,7 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      cluster_partials<GT, CT, MR>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, ring, P, full, empty, gctr);
+      cluster_partials<GT, CT, MR, STREAM>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P, full,
+                                            empty, gctr);
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
@@ -353,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     const bool rec = n < a.record_steps;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      cluster_partials<GT, CT, MR>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, ring, P, full, empty, gctr);
+      cluster_partials<GT, CT, MR, STREAM>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P, full,
+                                            empty, gctr);
       cluster.sync();
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
@@ -395,34 +444,49 @@ thread_local const char* g_where = "";  // last CUDA call attempted by the launc
 
 struct Plan {
   int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, RG, MR;
-  size_t smem;
+  bool stream;
+  size_t smem, slot_bytes, xoff;
 };
 
 template <typename CT>
 using EulerFn = void (*)(EulerArgs<CT>);
 
-template <typename GT, typename CT>
-EulerFn<CT> kernel_for(int MR) {
+template <typename GT, typename CT, bool STREAM>
+EulerFn<CT> kernel_for_s(int MR) {
   switch (MR) {
-    case 1: return euler_kernel<GT, CT, 1>;
-    case 2: return euler_kernel<GT, CT, 2>;
-    case 3: return euler_kernel<GT, CT, 3>;
-    case 4: return euler_kernel<GT, CT, 4>;
-    case 5: return euler_kernel<GT, CT, 5>;
-    case 6: return euler_kernel<GT, CT, 6>;
-    case 7: return euler_kernel<GT, CT, 7>;
-    default: return euler_kernel<GT, CT, 8>;
+    case 1: return euler_kernel<GT, CT, 1, STREAM>;
+    case 2: return euler_kernel<GT, CT, 2, STREAM>;
+    case 3: return euler_kernel<GT, CT, 3, STREAM>;
+    case 4: return euler_kernel<GT, CT, 4, STREAM>;
+    case 5: return euler_kernel<GT, CT, 5, STREAM>;
+    case 6: return euler_kernel<GT, CT, 6, STREAM>;
+    case 7: return euler_kernel<GT, CT, 7, STREAM>;
+    default: return euler_kernel<GT, CT, 8, STREAM>;
   }
+}
+
+// Streaming (G_off tiles from memory every step) is built for the reduced
+// storage types only; FP64 problems must fit on chip.
+template <typename GT> struct streamable { static constexpr bool value = !std::is_same<GT, double>::value; };
+
+template <typename GT, typename CT>
+EulerFn<CT> kernel_for(int MR, bool stream) {
+  if constexpr (streamable<GT>::value) {
+    if (stream) return kernel_for_s<GT, CT, true>(MR);
+  }
+  return kernel_for_s<GT, CT, false>(MR);
 }
 
 // Work split for N and T on this GPU.  For each cluster size C in {1, 2, 4, 8}
 // (or only the caller's hint) take the largest number of clusters that is
 // resident at once with the footprint it implies (rows per lane MR, ring slots),
-// and keep the C with the lowest estimate of one step per CTA: FMAs at 128 per
-// clock, X bytes at 32 per clock, and a fixed cost per cluster rank for the
-// reduction through distributed shared memory.
+// first with G_off resident in shared memory and, if that cannot fit, with
+// G_off tiles streamed from memory every step.  Keep the plan with the lowest
+// estimate of one step per CTA: FMAs at 128 per clock, X bytes at 32 per clock,
+// streamed G bytes at 22 per clock (one SM's share of HBM), and a fixed cost per
+// cluster rank for the reduction through distributed shared memory.
 template <typename GT, typename CT>
-cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, Plan* out) {
+cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
   const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
   const int twmax = round4(std::min(T, kTChunk));
@@ -436,72 +500,86 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, Plan* 
   bool found = false;
   Plan bp{};
   const int cands[] = {1, 2, 4, 8};
-  for (int C : cands) {
-    if (hint > 0 && C != hint) continue;
-    if (C > nq) continue;
-    Plan pl{};
-    pl.C = C;
-    pl.kq = (nq + C - 1) / C;
-    // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
-    pl.kch = std::max(4, std::min(pl.kq * 4, (int)((16384 / (twmax * sizeof(CT))) & ~(size_t)3)));
-    if (sms < C) continue;
-    for (int NC = std::min(sms / C, N); NC >= 1; --NC) {
-      pl.RPC = (N + NC - 1) / NC;
-      pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
-      if (pl.NC != NC && NC != std::min(sms / C, N)) continue;
-      // rows per row-warp, then row groups (a power of two that fits beside the
-      // column groups, aiming at about four rows per lane) and rows per lane;
-      // leftover lanes split k
-      const int rw_need = (pl.RPC + WR - 1) / WR;
-      int RG = 1;
-      while (RG * 4 < rw_need && CG * RG * 2 <= 32) RG <<= 1;
-      pl.RG = RG;
-      pl.MR = (rw_need + RG - 1) / RG;
-      if (pl.MR > kMaxRowsPerLane) break;  // fewer clusters only need more rows
-      pl.RW = RG * pl.MR;
-      pl.RPC_pad = WR * pl.RW;
-      pl.ORW = (pl.RPC + C - 1) / C;
-      EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR);
-      cudaFuncAttributes fa;
-      e = cudaFuncGetAttributes(&fa, fn);
-      if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
-      const size_t cap = (size_t)optin - fa.sharedSizeBytes;
-      pl.slots = 0;
-      for (int slots = 8; slots >= 3; --slots) {
-        pl.smem = smem_layout(pl.RPC_pad, pl.kq, slots, pl.kch, twmax, pl.ORW, T, sizeof(GT), sizeof(CT)).total;
-        if (pl.smem <= cap) { pl.slots = slots; break; }
+  for (int pass = force_stream ? 1 : 0; pass < 2 && !found; ++pass) {
+    const bool stream = pass == 1;
+    if (stream && !streamable<GT>::value) break;
+    for (int C : cands) {
+      if (hint > 0 && C != hint) continue;
+      if (C > nq || sms < C) continue;
+      Plan pl{};
+      pl.C = C;
+      pl.stream = stream;
+      if (stream) {
+        pl.kq = ((nq + C - 1) / C + 7) / 8 * 8;  // whole 32-column tiles per rank
+        pl.kch = kStreamK;
+      } else {
+        pl.kq = (nq + C - 1) / C;
+        // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
+        pl.kch = std::max(4, std::min(pl.kq * 4, (int)((16384 / (twmax * sizeof(CT))) & ~(size_t)3)));
       }
-      if (pl.slots == 0) break;
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-      if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"; return e; }
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(NonPortableClusterSizeAllowed)"; return e; }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = C;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(C * pl.NC);
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = pl.smem;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int maxc = 0;
-      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)fn, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        maxc = 0;
+      for (int NC = std::min(sms / C, N); NC >= 1; --NC) {
+        pl.RPC = (N + NC - 1) / NC;
+        pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
+        if (pl.NC != NC && NC != std::min(sms / C, N)) continue;
+        // rows per row-warp, then row groups (a power of two that fits beside the
+        // column groups, aiming at about four rows per lane) and rows per lane;
+        // leftover lanes split k
+        const int rw_need = (pl.RPC + WR - 1) / WR;
+        int RG = 1;
+        while (RG * 4 < rw_need && CG * RG * 2 <= 32) RG <<= 1;
+        pl.RG = RG;
+        pl.MR = (rw_need + RG - 1) / RG;
+        if (pl.MR > kMaxRowsPerLane) break;  // fewer clusters only need more rows
+        pl.RW = RG * pl.MR;
+        pl.RPC_pad = WR * pl.RW;
+        pl.ORW = (pl.RPC + C - 1) / C;
+        EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, stream);
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
+        const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+        const size_t gblock = stream ? 0 : (size_t)pl.RPC_pad * pl.kq * 4 * sizeof(GT);
+        const size_t gtile = stream ? (size_t)pl.RPC_pad * kStreamK * sizeof(GT) : 0;
+        pl.xoff = align128(gtile);
+        pl.slot_bytes = align128(pl.xoff + (size_t)pl.kch * twmax * sizeof(CT));
+        pl.slots = 0;
+        for (int slots = 8; slots >= (stream ? 2 : 3); --slots) {
+          pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
+          if (pl.smem <= cap) { pl.slots = slots; break; }
+        }
+        if (pl.slots == 0) break;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+        if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"; return e; }
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(NonPortableClusterSizeAllowed)"; return e; }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C * pl.NC);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = pl.smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, (void*)fn, &cfg) != cudaSuccess) {
+          cudaGetLastError();
+          maxc = 0;
+        }
+        if (pl.NC > maxc) continue;
+        const double fma = (double)pl.RPC_pad * pl.kq * 4 * T;
+        const double xbytes = (double)pl.kq * 4 * twmax * sizeof(CT) * ((T + kTChunk - 1) / kTChunk);
+        const double gbytes = stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) : 0.0;
+        const double cost = fma / 128.0 + xbytes / 32.0 + gbytes / 22.0 + 300.0 * C;
+        if (!found || cost < best_cost) {
+          best_cost = cost;
+          bp = pl;
+          found = true;
+        }
+        break;
       }
-      if (pl.NC > maxc) continue;
-      const double fma = (double)pl.RPC_pad * pl.kq * 4 * T;
-      const double xbytes = (double)pl.kq * 4 * twmax * sizeof(CT) * ((T + kTChunk - 1) / kTChunk);
-      const double cost = fma / 128.0 + xbytes / 32.0 + 300.0 * C;
-      if (!found || cost < best_cost) {
-        best_cost = cost;
-        bp = pl;
-        found = true;
-      }
-      break;
     }
   }
   if (!found) { g_where = "make_plan: no work split fits"; return cudaErrorInvalidConfiguration; }
@@ -509,25 +587,60 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, Plan* 
   return cudaSuccess;
 }
 
+// Streamed G_off tiles for a plan, rebuilt when the precision or split changes.
+template <typename GT>
+cudaError_t ensure_cluster_tiles(ProblemDev& P, int precision, const Plan& pl) {
+  if (P.Gt2 && P.gt2_prec == precision && P.gt2_rpc == pl.RPC && P.gt2_rpcpad == pl.RPC_pad && P.gt2_nc == pl.NC)
+    return cudaSuccess;
+  if (P.Gt2) { dev_free(P.Gt2, P.stream); P.Gt2 = nullptr; P.gt2_prec = -1; }
+  if (row_scaled<GT>::value) {
+    cudaError_t e = ensure_row_scales(P);
+    if (e != cudaSuccess) return e;
+  }
+  const int nkct = (int)(P.Npad / kStreamK);
+  const size_t elems = (size_t)pl.NC * nkct * pl.RPC_pad * kStreamK;
+  cudaError_t e = dev_alloc(&P.Gt2, elems * sizeof(GT), P.stream);
+  if (e != cudaSuccess) return e;
+  store_cluster_tiles_kernel<GT><<<P.num_sms * 4, 256, 0, P.stream>>>(P.G, (GT*)P.Gt2, (int)P.N, pl.RPC, pl.RPC_pad,
+                                                                        pl.NC, nkct, P.gscale);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  P.gt2_prec = precision;
+  P.gt2_rpc = pl.RPC;
+  P.gt2_rpcpad = pl.RPC_pad;
+  P.gt2_nc = pl.NC;
+  return cudaSuccess;
+}
+
 template <typename GT, typename CT>
-cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
                          long long timeout_cycles) {
   // plans depend only on (N, T, hint) for a given device and precision
-  static thread_local struct { int64_t N; int T, hint, cap, dev; Plan pl; bool valid; } cache = {0, 0, 0, 0, -1, {}, false};
+  static thread_local struct { int64_t N; int T, hint, cap, strm, dev; Plan pl; bool valid; } cache = {
+      0, 0, 0, 0, 0, -1, {}, false};
   Plan pl;
   if (cache.valid && cache.N == P.N && cache.T == S.trials && cache.hint == prm.cluster_size &&
-      cache.cap == prm.max_ctas && cache.dev == P.device) {
+      cache.cap == prm.max_ctas && cache.strm == prm.stream_g && cache.dev == P.device) {
     pl = cache.pl;
   } else {
-    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, &pl);
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl);
     if (e != cudaSuccess) return e;
     cache.N = P.N; cache.T = S.trials; cache.hint = prm.cluster_size; cache.cap = prm.max_ctas;
-    cache.dev = P.device; cache.pl = pl; cache.valid = true;
+    cache.strm = prm.stream_g; cache.dev = P.device; cache.pl = pl; cache.valid = true;
   }
   EulerArgs<CT> a;
   a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials;
   a.C = pl.C; a.RPC = pl.RPC; a.ORW = pl.ORW; a.kq = pl.kq; a.kch = pl.kch; a.slots = pl.slots; a.RW = pl.RW;
   a.RPC_pad = pl.RPC_pad;
+  a.slot_bytes = pl.slot_bytes;
+  a.xoff = pl.xoff;
+  a.nkct = (int)(P.Npad / kStreamK);
+  a.Gt2 = nullptr;
+  if (pl.stream) {
+    cudaError_t e = ensure_cluster_tiles<GT>(P, prm.precision, pl);
+    if (e != cudaSuccess) { g_where = "streamed G_off tiles"; return e; }
+    a.Gt2 = P.Gt2;
+  }
   a.RG = pl.RG;
   a.Gs = P.Gs; a.gscale = P.gscale; a.R = S.R; a.hz = P.hz;
   a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
@@ -546,7 +659,7 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
   S.plan_cluster = pl.C;
   S.plan_ctas = pl.C * pl.NC;
 
-  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR);
+  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, pl.stream);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(launch)"; return e; }
   e = cudaMemsetAsync(S.bar, 0, sizeof(unsigned), P.stream);
@@ -580,7 +693,7 @@ cudaError_t launch_typed(const ProblemDev& P, SolveDev& S, const cs_params& prm,
 
 const char* euler_last_call() { return g_where; }
 
-cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+cudaError_t launch_euler(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
                          long long timeout_cycles) {
   switch (prm.precision) {
     case CS_P_FP64: return launch_typed<double, double>(P, S, prm, outer, eta, timeout_cycles);

@@ -42,6 +42,8 @@ struct ProblemDev {
   void* Gt = nullptr;     // G_off in storage precision, tiled for streaming (batched solves)
   int gt_prec = -1;
   float* gscale = nullptr; // N row scales of G_off for FP8 storage (largest |G_off[r][k]| / 448)
+  void* Gt2 = nullptr;    // G_off tiles of a streaming Euler plan (see euler.cu)
+  int gt2_prec = -1, gt2_rpc = 0, gt2_rpcpad = 0, gt2_nc = 0;
   int* flag = nullptr;    // device word: nonzero if A or y had a non-finite value
   int64_t launches = 0;   // kernels launched by the last create + solve
 };
@@ -121,7 +123,7 @@ cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);
 // Launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gram(const ProblemDev& P);
 cudaError_t launch_store_coupling(ProblemDev& P, int precision);
-cudaError_t launch_euler(const ProblemDev& P, SolveDev& S, const cs_params& prm, int outer,
+cudaError_t launch_euler(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer,
                          double eta, long long timeout_cycles);
 const char* euler_last_call();  // the CUDA call the last failing Euler launch stopped at
 cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);

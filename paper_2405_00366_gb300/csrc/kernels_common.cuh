@@ -61,6 +61,16 @@ __device__ __forceinline__ void load4<float, __nv_fp8_e4m3>(const __nv_fp8_e4m3*
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
+// A double rounded to a storage type (round to nearest; FP8 saturates to finite).
+template <typename GT> __device__ __forceinline__ GT to_storage(double v);
+template <> __device__ __forceinline__ double to_storage<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_storage<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __half to_storage<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_fp8_e4m3 to_storage<__nv_fp8_e4m3>(double v) {
+  return __nv_fp8_e4m3((float)v);
+}
+
 // Scale of row r of G_off in its storage type (1 unless the type is row-scaled).
 template <typename GT, typename CT>
 __device__ __forceinline__ CT row_scale(const float* gscale, int r) {
