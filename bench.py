@@ -321,7 +321,7 @@ def main():
                        "p99": ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]},
         "quality": {"rmse": oracle.rmse(x_hat, inst.x0), "hamming": oracle.hamming_loss(sigma_hat, inst.xi),
                     "energy": energy, "support": int(stats[1])},
-        "roofline": {"kernel": "euler_kernel<float,float,16>", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "euler_kernel<float, float, MR, false> (FP32 G_off resident on chip)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": (f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                      f"(max SM clock, {peak_kind})"),

@@ -147,7 +147,9 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->pump_kind == CS_PUMP_SIGMOID && !(p->width > 0.0)) return fail(CS_EINVAL, "sigmoid width must be > 0");
   if (p->init_kind != CS_INIT_UNIFORM && p->init_kind != CS_INIT_NORMAL) return fail(CS_EINVAL, "bad init_kind");
   if (p->field != CS_FIELD_CN && p->field != CS_FIELD_BN) return fail(CS_EINVAL, "bad field");
-  if (p->refit != CS_REFIT_EXACT) return fail(CS_EINVAL, "only the exact refit is available");
+  if (p->refit != CS_REFIT_EXACT && p->refit != CS_REFIT_JACOBI) return fail(CS_EINVAL, "bad refit");
+  if (p->refit == CS_REFIT_JACOBI && (!(p->jacobi_dt > 0.0) || !std::isfinite(p->jacobi_dt) || p->jacobi_iters < 1))
+    return fail(CS_EINVAL, "the damped Jacobi refit needs jacobi_dt > 0 and jacobi_iters >= 1");
   if (p->precision < CS_P_FP64 || p->precision > CS_P_FP8) return fail(CS_EINVAL, "bad precision");
   if (p->eta_init > 0.0 && !(p->velo > 0.0)) return fail(CS_EINVAL, "velo must be > 0 with an eta schedule");
   if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
@@ -191,7 +193,7 @@ cudaError_t mark(cs_problem* p, int cat, bool begin) {
 
 }  // namespace
 
-RefitJob make_job(const ProblemDev& P, const SolveDev& S) {
+RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) {
   RefitJob J;
   J.G = P.G;
   J.hz = P.hz;
@@ -213,6 +215,9 @@ RefitJob make_job(const ProblemDev& P, const SolveDev& S) {
   J.lambda = P.lambda;
   J.singular = S.singular;
   J.err = S.err;
+  J.refit = prm.refit;
+  J.jacobi_iters = prm.jacobi_iters;
+  J.jacobi_dt = prm.jacobi_dt;
   return J;
 }
 
@@ -324,7 +329,7 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   int khz = 0;
   CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P.device), "clock rate");
   const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
-  const RefitJob hjob = make_job(P, S);
+  const RefitJob hjob = make_job(P, S, *prm);
   CS_CUDA(cudaMemcpyAsync(S.job, &hjob, sizeof(hjob), cudaMemcpyHostToDevice, P.stream), "copy job");
   CS_CUDA(launch_init_R(S.job, 1, S.trials, P.num_sms, P.stream), "init R");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
@@ -399,7 +404,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   CS_CUDA(cudaMemcpyAsync(d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, stream), "copy order");
   std::vector<RefitJob> jobs(n);
   for (int i = 0; i < n; ++i) {
-    jobs[i] = make_job(ps[i]->P, ps[i]->S);
+    jobs[i] = make_job(ps[i]->P, ps[i]->S, *prm);
     jobs[i].err = d_err;
   }
   CS_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), n * sizeof(RefitJob), cudaMemcpyHostToDevice, stream), "copy jobs");

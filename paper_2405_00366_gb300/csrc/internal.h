@@ -68,6 +68,9 @@ struct RefitJob {
   double lambda;
   int* singular;
   int* err;
+  int refit;             // CS_REFIT_EXACT or CS_REFIT_JACOBI
+  int jacobi_iters;      // damped Jacobi sweeps per outer iteration
+  double jacobi_dt;      // damped Jacobi step
 };
 
 // Per-solve device state, sized by (N, trials).

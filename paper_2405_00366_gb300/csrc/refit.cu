@@ -11,6 +11,9 @@
 // singular G_SS, e.g. |S| > M) is redone on G_SS + eps I with
 // eps = 1e-10 * mean(G_rr over S) and the solve is flagged.
 //
+// The damped Jacobi refit of the paper (refit = CS_REFIT_JACOBI) is the other
+// option: a fixed number of relaxed sweeps from the trial's current R.
+//
 // The exact refit depends on the support only, so trials of a problem whose
 // supports are identical share one factorisation: the first such trial (the
 // "leader") is refitted and the others copy its R.
@@ -32,44 +35,159 @@ __device__ bool same_support(const uint8_t* __restrict__ sigma, int N, int T, in
   return __syncthreads_or(diff) == 0;
 }
 
-// Refit of trial t of job J with the workspace W (n^2 + 2n doubles, n = |S|).
-__device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, double* W) {
+__device__ __forceinline__ size_t packed_off(int k, int n) { return (size_t)k * n - (size_t)k * (k - 1) / 2; }
+
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int i = 0; i < kRefitThreads / 32; ++i) m = fmax(m, scratch[i]);
+  return m;
+}
+
+// Mixed-precision solve of G_SS x = (A^T y)_S: FP32 Cholesky of G_SS held packed
+// (lower triangle, column-major) in shared memory, then FP64 iterative
+// refinement: r = h^z_S - G_SS x in FP64 from the FP64 G, d = (L L^T)^-1 r in
+// FP32, x += d, until the residual stops shrinking.  Returns false (in every
+// thread) when a pivot is not above 1e-5 G_jj, i.e. the matrix is too close to
+// singular for an FP32 factor, or when the residual does not fall below
+// 1e-12 |h^z_S|; the caller then takes the FP64 factorisation.  x and r are
+// global FP64 vectors of length n; Lp and d live in shared memory.
+__device__ bool solve_mixed(const RefitJob& J, const int* idx, int n, float* Lp, float* d, double* x, double* r) {
+  const int N = J.N, tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  constexpr int nw = kRefitThreads / 32;
+  __shared__ int ok_s;
+  __shared__ double red_s[kRefitThreads / 32];
+  for (int k = w; k < n; k += nw) {
+    const double* Gk = J.G + (size_t)idx[k] * N;
+    float* ck = Lp + packed_off(k, n);
+    for (int i = k + l; i < n; i += 32) ck[i - k] = (float)Gk[idx[i]];
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    float* cj = Lp + packed_off(j, n);
+    if (tid == 0) {
+      const float dj = cj[0];
+      ok_s = (dj > 1e-5f * (float)J.g[idx[j]] && isfinite(dj)) ? 1 : 0;
+      if (ok_s) cj[0] = sqrtf(dj);
+    }
+    __syncthreads();
+    if (!ok_s) return false;
+    const float ljj = cj[0];
+    for (int i = j + 1 + tid; i < n; i += kRefitThreads) cj[i - j] /= ljj;
+    __syncthreads();
+    for (int k = j + 1 + w; k < n; k += nw) {
+      const float lkj = cj[k - j];
+      float* ck = Lp + packed_off(k, n);
+      for (int i = k + l; i < n; i += 32) ck[i - k] = fmaf(-cj[i - j], lkj, ck[i - k]);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += kRefitThreads) {
+    x[i] = 0.0;
+    r[i] = J.hz[idx[i]];
+  }
+  double rn0 = 0.0;
+  for (int i = tid; i < n; i += kRefitThreads) rn0 = fmax(rn0, fabs(J.hz[idx[i]]));
+  rn0 = block_max(rn0, red_s);
+  if (rn0 == 0.0) return true;
+  double prev = rn0;
+  for (int it = 0; it < 8; ++it) {
+    if (w == 0) {
+      for (int i = l; i < n; i += 32) d[i] = (float)r[i];
+      __syncwarp();
+      for (int k = 0; k < n; ++k) {  // L z = d
+        const float* ck = Lp + packed_off(k, n);
+        const float zk = d[k] / ck[0];
+        __syncwarp();
+        if (l == 0) d[k] = zk;
+        for (int i = k + 1 + l; i < n; i += 32) d[i] = fmaf(-ck[i - k], zk, d[i]);
+        __syncwarp();
+      }
+      for (int k = n - 1; k >= 0; --k) {  // L^T d = z
+        const float* ck = Lp + packed_off(k, n);
+        float s = 0.f;
+        for (int i = k + 1 + l; i < n; i += 32) s = fmaf(ck[i - k], d[i], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float xk = (d[k] - s) / ck[0];
+        __syncwarp();
+        if (l == 0) d[k] = xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += kRefitThreads) x[i] += (double)d[i];
+    __syncthreads();
+    for (int i = w; i < n; i += nw) {
+      const double* Gi = J.G + (size_t)idx[i] * N;
+      double s = 0.0;
+      for (int k = l; k < n; k += 32) s = fma(Gi[idx[k]], x[k], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) r[i] = J.hz[idx[i]] - s;
+    }
+    __syncthreads();
+    double rm = 0.0;
+    for (int i = tid; i < n; i += kRefitThreads) rm = fmax(rm, fabs(r[i]));
+    rm = block_max(rm, red_s);
+    if (rm <= 1e-14 * rn0 || (it >= 1 && rm > 0.5 * prev)) return rm <= 1e-12 * rn0;
+    prev = rm;
+  }
+  return prev <= 1e-12 * rn0;
+}
+
+// Refit of trial t of job J.  W is this block's global workspace (n^2 + 2n
+// doubles); `smem` (smem_bytes) holds the FP32 factor of the mixed-precision
+// path, taken when it fits and succeeds; otherwise the FP64 factorisation.
+__device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, double* W, float* smem,
+                          size_t smem_bytes) {
   const int N = J.N, T = J.T;
   if (n == 0) {
     for (int r = threadIdx.x; r < N; r += kRefitThreads) J.R[(size_t)r * T + t] = J.hz[r] / J.g[r];
     return;
   }
-  double* x = W + (size_t)n * n;
-  double* dg = x + n;  // diagonal of the matrix being factorised
-  __shared__ double ridge_s;
-  __shared__ double red_s[kRefitThreads / 32];
-  if (threadIdx.x == 0) ridge_s = 0.0;
-  __syncthreads();
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    const double ridge = ridge_s;
-    for (size_t e = threadIdx.x; e < (size_t)n * n; e += kRefitThreads) {
-      const int k = (int)(e / n), i = (int)(e % n);
-      if (i >= k) W[e] = J.G[(size_t)idx[i] * N + idx[k]] + (i == k ? ridge : 0.0);
-    }
-    for (int i = threadIdx.x; i < n; i += kRefitThreads) dg[i] = J.G[(size_t)idx[i] * N + idx[i]] + ridge;
-    __syncthreads();
-    if (cholesky_lower(W, n, dg)) break;
-    if (attempt == 1) {
-      if (threadIdx.x == 0) set_error(J.err, DEV_NONFINITE);
-      return;
-    }
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += kRefitThreads) s += J.g[idx[i]];
-    s = block_sum(s, red_s);
-    if (threadIdx.x == 0) {
-      ridge_s = 1e-10 * s / n;
-      atomicExch(J.singular, 1);
-    }
-    __syncthreads();
+  double* x;
+  const size_t packed = (size_t)n * (n + 1) / 2;
+  bool done = false;
+  if ((packed + (size_t)n) * sizeof(float) <= smem_bytes) {
+    x = W;
+    done = solve_mixed(J, idx, n, smem, smem + packed, W, W + n);
   }
-  for (int i = threadIdx.x; i < n; i += kRefitThreads) x[i] = J.hz[idx[i]];
-  __syncthreads();
-  if (threadIdx.x < 32) cholesky_solve_warp(W, n, x);
+  if (!done) {
+    x = W + (size_t)n * n;
+    double* dg = x + n;  // diagonal of the matrix being factorised
+    __shared__ double ridge_s;
+    __shared__ double red_s[kRefitThreads / 32];
+    if (threadIdx.x == 0) ridge_s = 0.0;
+    __syncthreads();
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const double ridge = ridge_s;
+      for (size_t e = threadIdx.x; e < (size_t)n * n; e += kRefitThreads) {
+        const int k = (int)(e / n), i = (int)(e % n);
+        if (i >= k) W[e] = J.G[(size_t)idx[i] * N + idx[k]] + (i == k ? ridge : 0.0);
+      }
+      for (int i = threadIdx.x; i < n; i += kRefitThreads) dg[i] = J.G[(size_t)idx[i] * N + idx[i]] + ridge;
+      __syncthreads();
+      if (cholesky_lower(W, n, dg)) break;
+      if (attempt == 1) {
+        if (threadIdx.x == 0) set_error(J.err, DEV_NONFINITE);
+        return;
+      }
+      double s = 0.0;
+      for (int i = threadIdx.x; i < n; i += kRefitThreads) s += J.g[idx[i]];
+      s = block_sum(s, red_s);
+      if (threadIdx.x == 0) {
+        ridge_s = 1e-10 * s / n;
+        atomicExch(J.singular, 1);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) x[i] = J.hz[idx[i]];
+    __syncthreads();
+    if (threadIdx.x < 32) cholesky_solve_warp(W, n, x);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += kRefitThreads) J.R[(size_t)idx[i] * T + t] = x[i];
   // off the support: one warp per row r
@@ -85,17 +203,56 @@ __device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, doubl
   __syncthreads();
 }
 
+// Damped Jacobi CDP of trial t (the paper's iteration for random data), warm
+// started from the trial's current R: each sweep forms, for every r,
+// R~_r = (h^z_r - sum_{r' in S, r' != r} G_rr' R_r') / G_rr from a snapshot of
+// R_S (xs, n doubles) and moves R_r by jacobi_dt (R~_r - R_r).  One warp per row.
+__device__ void jacobi_one(const RefitJob& J, int t, const int* idx, int n, double* xs) {
+  const int N = J.N, T = J.T, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int sweep = 0; sweep < J.jacobi_iters; ++sweep) {
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) xs[i] = J.R[(size_t)idx[i] * T + t];
+    __syncthreads();
+    for (int r = w; r < N; r += kRefitThreads / 32) {
+      const double* Gr = J.G + (size_t)r * N;
+      double s = 0.0;
+      for (int i = l; i < n; i += 32) {
+        const int c = idx[i];
+        if (c != r) s = fma(Gr[c], xs[i], s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) {
+        double* Rr = J.R + (size_t)r * T + t;
+        const double Rt = (J.hz[r] - s) / J.g[r];
+        *Rr = *Rr + J.jacobi_dt * (Rt - *Rr);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Refit of every (job, trial) item whose support is not a copy of an earlier
 // trial's; items are spread over the grid, block b owns workspace b of the pool.
 __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __restrict__ jobs, int T, int items,
                                                               double* __restrict__ pool, size_t pool_stride,
-                                                              int outer) {
+                                                              int outer, size_t smem_bytes) {
+  extern __shared__ __align__(16) float refit_smem[];
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const RefitJob& J = jobs[it / T];
     const int t = it % T;
     if (ld_volatile(J.err) != 0) continue;
     int* idx = J.sidx + (size_t)t * J.N;
     const int n = support_list(J.sigma, J.N, T, t, idx);
+    if (J.refit == CS_REFIT_JACOBI) {  // depends on the trial's own R: no sharing
+      if (threadIdx.x == 0) {
+        J.ssize[(size_t)outer * T + t] = n;
+        J.lead[t] = t;
+      }
+      double* xs = (size_t)n * sizeof(double) <= smem_bytes ? reinterpret_cast<double*>(refit_smem)
+                                                             : pool + (size_t)blockIdx.x * pool_stride;
+      jacobi_one(J, t, idx, n, xs);
+      __syncthreads();
+      continue;
+    }
     int lead = t;
     for (int u = 0; u < t; ++u)
       if (same_support(J.sigma, J.N, T, t, u)) { lead = u; break; }
@@ -103,7 +260,7 @@ __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __
       J.ssize[(size_t)outer * T + t] = n;
       J.lead[t] = lead;
     }
-    if (lead == t) refit_one(J, t, idx, n, pool + (size_t)blockIdx.x * pool_stride);
+    if (lead == t) refit_one(J, t, idx, n, pool + (size_t)blockIdx.x * pool_stride, refit_smem, smem_bytes);
     __syncthreads();
   }
 }
@@ -199,7 +356,22 @@ cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, c
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
                          int outer, cudaStream_t st) {
   const int items = njobs * T;
-  refit_kernel<<<std::min(items, pool_blocks), kRefitThreads, 0, st>>>(jobs, T, items, pool, pool_stride, outer);
+  // shared memory for the FP32 factor of the mixed-precision refit (|S| up to about 310)
+  static thread_local size_t smem = 0;
+  if (smem == 0) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, refit_kernel);
+    if (e != cudaSuccess) return e;
+    smem = std::min<size_t>(200 * 1024, (size_t)optin - fa.sharedSizeBytes);
+    e = cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  refit_kernel<<<std::min(items, pool_blocks), kRefitThreads, smem, st>>>(jobs, T, items, pool, pool_stride, outer,
+                                                                           smem);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   follow_kernel<<<std::min(items, 4096), 256, 0, st>>>(jobs, T, items);

@@ -185,6 +185,34 @@ def test_singular_support_uses_ridge():
     assert np.linalg.norm(inst.y - inst.A @ g["x_hat"]) < 1e-4 * np.linalg.norm(inst.y)
 
 
+@pytest.mark.parametrize("precision,trials", [("fp64", 1), ("fp32", 4)])
+def test_jacobi_refit_matches_oracle(precision, trials):
+    """refit = damped Jacobi (step 0.1, 100 sweeps from the trial's current R, the paper's
+    CDP for random data): supports identical to the oracle's and R, on and off the
+    support, to 1e-9 (FP64) / 1e-5 (FP32 Euler)."""
+    inst = cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=0)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=5, n_steps=800, precision=precision, refit="jacobi")
+    g = gpu_solve(inst, w, trials)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=trials)
+    np.testing.assert_array_equal(g["support_sizes"], r["support_sizes"])
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    np.testing.assert_allclose(g["R"], r["R"], rtol=0, atol=tol)
+    np.testing.assert_allclose(g["energies"], r["energies"], rtol=1e-9 if precision == "fp64" else 1e-6)
+
+
+def test_large_support_takes_fp64_factorisation():
+    """Supports of more than about 310 entries do not fit the FP32 factor in shared memory
+    and take the FP64 Cholesky; against the oracle: identical supports, R to 1e-8."""
+    inst = cs_inputs.random_instance(900, 760, 420, 0.0, 0.005, seed=4)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=500, precision="fp64")
+    g = gpu_solve(inst, w, 2)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=2)
+    assert r["support_sizes"].max() > 320
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_allclose(g["R"], r["R"], rtol=0, atol=1e-8)
+
+
 def test_trials64_full_size_properties():
     """The N = 2000, 64-trial workload at full size (30 x 2000 steps), in the launch
     configuration the benchmark times.  The oracle runs trials 0 and 1 for the first two
