@@ -54,7 +54,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     """Compile csrc/*.cu and link libcs.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs

@@ -1,0 +1,11 @@
+// Euler kernels and launcher for bf16 storage of G_off (compute type float).
+#include "euler_impl.cuh"
+
+namespace cs {
+
+cudaError_t launch_euler_bf16(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+                          long long timeout_cycles) {
+  return launch_typed<__nv_bfloat16, float>(P, S, prm, outer, eta, timeout_cycles);
+}
+
+}  // namespace cs
