@@ -309,7 +309,7 @@ def main():
     flops_per_launch = 2.0 * w["N"] * (w["N"] - 1) * T * w["n_steps"]
     achieved = flops_per_launch / per_launch_s / 1e12
     peak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2405_00366_gb300", "csrc", "euler.cu"))
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2405_00366_gb300", "csrc", "euler_impl.cuh"))
     ms_sorted = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": args.steps,
@@ -321,7 +321,9 @@ def main():
                        "p99": ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]},
         "quality": {"rmse": oracle.rmse(x_hat, inst.x0), "hamming": oracle.hamming_loss(sigma_hat, inst.xi),
                     "energy": energy, "support": int(stats[1])},
-        "roofline": {"kernel": "euler_kernel<float, float, MR, false> (FP32 G_off resident on chip)", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true> "
+                               "(FP32 G_off resident on chip, packed FMAs)",
+                     "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": (f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                      f"(max SM clock, {peak_kind})"),
