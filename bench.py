@@ -11,6 +11,16 @@ already in HBM (CUDA events on the library's stream, L2 flushed between steps);
 `e2e` is the same metric through the C ABI from pinned host buffers, host<->device
 copies included.  `--impl reference` times the FP64 CPU oracle on a bounded
 sample of the same workload instead.
+
+Two further workloads print their own line (not the default):
+  --workload batch_uneven_bf16   one step = one batched solve (cs_solve_batch) of
+      152 uneven instances (N in [256, 1024], alpha in {0.3, 0.5, 0.7}, a in
+      {0.05, 0.1, 0.2}, 16 trials, 30 x 2000 steps, BF16 storage of G_off),
+      against plain FP32 solves of the same instances one at a time (cs_solve);
+  --workload serve_mix           a Poisson stream (200 requests/s) of 40 requests
+      mixing the single FP64 N=200 shape, the 64-trial N=2000 shape and the
+      uneven BF16 shape 60/30/10, through the continuous-batching server, against
+      the same requests as plain FP32 solves one at a time; p50/p99 latency.
 """
 from __future__ import annotations
 
@@ -186,8 +196,201 @@ def config_of(w, world):
     return {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "nnz": w["nnz"], "noise": w["nu"], "lambda": w["lam"],
             "trials": w["trials"], "n_outer": w["n_outer"], "n_steps": w["n_steps"], "dt": w["dt"],
             "field": w["field"], "precision": w["precision"], "refit": w["refit"],
-            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "parallelism": f"replicas{world}" if world > 1 else "single", "work_split": "autotuned",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
+
+
+# ------------------------------------------------------------------ batched and served workloads
+BATCH = dict(n_inst=152, n_min=256, n_max=1024, alphas=[0.3, 0.5, 0.7], sparsities=[0.05, 0.1, 0.2],
+             nu=0.01, lam=0.03, trials=16, n_plain=16, seed=17)
+
+
+def _run_params(cs, precision, **over):
+    """Run parameters of the 64-trial workload (30 x 2000 steps) in another precision."""
+    w = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], precision=precision)
+    w.update(over)
+    return cs.params_from_workload(w)
+
+
+def run_batch(args):
+    """Batched BF16 solves of uneven instances vs plain FP32 solves one at a time."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2405_00366_gb300 import build, cs
+
+    if not os.path.exists(cs.LIB_PATH):
+        build.build()
+    b = BATCH
+    insts = cs_inputs.uneven_batch(b["n_inst"], b["n_min"], b["n_max"], b["alphas"], b["sparsities"], b["nu"],
+                                   b["lam"], seed=b["seed"])
+    T = b["trials"]
+    stream = torch.cuda.Stream()
+    dev = [(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda()) for i in insts]
+    torch.cuda.synchronize()
+    prm_b = _run_params(cs, "bf16", max_ctas=0)
+    prm_p = _run_params(cs, "fp32")
+
+    def batched():
+        hs = [cs.cs_problem_create(A, y, i.lam, stream=stream) for (A, y), i in zip(dev, insts)]
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        cs.cs_solve_batch(hs, prm_b, T)
+        ev1.record(stream)
+        res = [cs.cs_result(h) for h in hs]
+        for h in hs:
+            cs.cs_problem_destroy(h)
+        return ev0.elapsed_time(ev1) / 1e3, res
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+    times, res = [], None
+    with ClockSampler(_env_int("LOCAL_RANK", 0)) as clocks:
+        for _ in range(max(1, args.steps)):
+            t, res = batched()
+            times.append(t)
+        # plain FP32 solves, one instance at a time, on the first n_plain instances
+        plain_s, plain_rmse = 0.0, []
+        for k in range(b["n_plain"]):
+            (A, y), inst = dev[k], insts[k]
+            h = cs.cs_problem_create(A, y, inst.lam, stream=stream)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            cs.cs_solve(h, prm_p, T)
+            ev1.record(stream)
+            x, sgm, E, st, _ = cs.cs_result(h)
+            cs.cs_problem_destroy(h)
+            plain_s += ev0.elapsed_time(ev1) / 1e3
+            plain_rmse.append(oracle.rmse(x, inst.x0))
+    t_b = statistics.median(times)
+    rmse_b = [oracle.rmse(r[0], i.x0) for r, i in zip(res, insts)]
+    v_b = len(insts) / t_b
+    v_p = b["n_plain"] / plain_s
+    Ns = [i.N for i in insts]
+    line = {
+        "metric": METRIC, "value": v_b, "unit": "reconstructions/s", "n_gpus": 1, "steps": len(times),
+        "warmup": args.warmup, "ms_per_step": t_b * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
+        "config": {"workload": "batch_uneven_bf16", "instances": len(insts), "N_range": [min(Ns), max(Ns)],
+                   "alphas": b["alphas"], "sparsities": b["sparsities"], "trials": T, "n_outer": 30,
+                   "n_steps": 2000, "precision": "bf16", "note": "N range scaled down from [256, 4096]: "
+                   "the batched kernel runs each problem on one CTA"},
+        "spin_steps_per_s": sum(Ns) * T * 30 * 2000 / t_b,
+        "quality": {"rmse_mean": float(np.mean(rmse_b)),
+                    "rmse_mean_first_plain": float(np.mean(rmse_b[:b["n_plain"]])),
+                    "plain_fp32_rmse_mean": float(np.mean(plain_rmse))},
+        "plain_fp32": {"value": v_p, "unit": "reconstructions/s",
+                       "sample": f"first {b['n_plain']} instances solved one at a time (cs_solve, FP32), "
+                                 f"{plain_s:.1f} s"},
+        "ratio_vs_plain_fp32": v_b / v_p,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _serve_requests(seed=23, n_req=40, rate=200.0):
+    """(arrival_s, instance, workload dict, trials) of a seeded Poisson request mix."""
+    rng = __import__("numpy").random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(n_req):
+        t += float(rng.exponential(1.0 / rate))
+        u = float(rng.random())
+        if u < 0.6:
+            w = dict(cs_inputs.WORKLOADS["single_n200_fp64"])
+            inst = cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=1000 + i)
+        elif u < 0.9:
+            w = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"])
+            inst = cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=1000 + i)
+        else:
+            w = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], precision="bf16", trials=16)
+            inst = cs_inputs.uneven_batch(1, 256, 1024, [0.3, 0.5, 0.7], [0.05, 0.1, 0.2], 0.01, 0.03,
+                                          seed=1000 + i)[0]
+        out.append((t, inst, w, w["trials"]))
+    return out
+
+
+def run_serve(args):
+    """Poisson request mix through the server vs plain FP32 solves one at a time."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2405_00366_gb300 import build, cs
+
+    if not os.path.exists(cs.LIB_PATH):
+        build.build()
+    reqs = _serve_requests()
+    torch.cuda.init()
+    # warm-up: one request of each shape through the server
+    sv = cs.cs_server_create(150 << 30, 16)
+    try:
+        seen = {}
+        for _, inst, w, T in reqs:
+            seen.setdefault((inst.N, w["precision"]), (inst, w, T))
+        for inst, w, T in seen.values():
+            tk = cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
+            cs.cs_server_wait(sv, tk)
+            cs.cs_server_result(sv, tk, inst.N)
+    finally:
+        cs.cs_server_destroy(sv)
+
+    with ClockSampler(_env_int("LOCAL_RANK", 0)) as clocks:
+        sv = cs.cs_server_create(150 << 30, 16)
+        try:
+            t0 = time.perf_counter()
+            tickets = []
+            for arr, inst, w, T in reqs:
+                while time.perf_counter() - t0 < arr:
+                    time.sleep(min(0.001, arr - (time.perf_counter() - t0)))
+                tickets.append((time.perf_counter(),
+                                cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)))
+            lat, rmse = [], []
+            for (ts, tk), (arr, inst, w, T) in zip(tickets, reqs):
+                cs.cs_server_wait(sv, tk)
+                x, s, E, st, tm, _ = cs.cs_server_result(sv, tk, inst.N)
+                lat.append(tm[2] - tm[0])
+                rmse.append(oracle.rmse(x, inst.x0))
+            makespan = time.perf_counter() - t0  # first arrival clock to the last result
+        finally:
+            cs.cs_server_destroy(sv)
+        # plain FP32 solves of the same requests one at a time, arrival order, same arrival clock
+        t0 = time.perf_counter()
+        free_at, plat, prmse = 0.0, [], []
+        for arr, inst, w, T in reqs:
+            while time.perf_counter() - t0 < arr:
+                time.sleep(min(0.001, arr - (time.perf_counter() - t0)))
+            h = cs.cs_problem_create(inst.A, inst.y, inst.lam)
+            cs.cs_solve(h, cs.params_from_workload(dict(w, precision="fp32")), T)
+            x, s, E, st, _ = cs.cs_result(h)
+            cs.cs_problem_destroy(h)
+            plat.append(time.perf_counter() - t0 - arr)
+            prmse.append(oracle.rmse(x, inst.x0))
+        pmakespan = time.perf_counter() - t0
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+    line = {
+        "metric": METRIC, "value": len(reqs) / makespan, "unit": "reconstructions/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "per request (f64 / f32 / bf16 storage)", "data": "synthetic",
+        "config": {"workload": "serve_mix", "requests": len(reqs), "rate_per_s": 200.0, "mix": "60/30/10",
+                   "slots": 16, "hbm_budget_gb": 150},
+        "latency_ms": {"p50": pct(lat, 0.5) * 1e3, "p99": pct(lat, 0.99) * 1e3},
+        "quality": {"rmse_mean": float(np.mean(rmse)), "plain_fp32_rmse_mean": float(np.mean(prmse))},
+        "plain_fp32": {"value": len(reqs) / pmakespan, "unit": "reconstructions/s",
+                       "latency_ms": {"p50": pct(plat, 0.5) * 1e3, "p99": pct(plat, 0.99) * 1e3},
+                       "sample": "the same requests as plain FP32 solves one at a time, arrival order"},
+        "ratio_vs_plain_fp32": (len(reqs) / makespan) / (len(reqs) / pmakespan),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -203,6 +406,7 @@ def main():
                     help="override the workload's outer iterations (short runs for profiling only)")
     ap.add_argument("--n-steps", type=int, default=None,
                     help="override the workload's Euler steps per run (short runs for profiling only)")
+    ap.add_argument("--workload", choices=[WORKLOAD, "batch_uneven_bf16", "serve_mix"], default=WORKLOAD)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 does not meet the timing rules", file=sys.stderr)
@@ -212,6 +416,10 @@ def main():
     local = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch_uneven_bf16":
+        return run_batch(args)
+    if args.workload == "serve_mix":
+        return run_serve(args)
 
     import numpy as np
     import torch
@@ -233,7 +441,7 @@ def main():
     if args.n_steps:
         w["n_steps"] = args.n_steps
     inst = cs_inputs.workload_instance(w)
-    prm = cs.params_from_workload(w)
+    prm = cs.params_from_workload(w, autotune=1)  # work split timed on this GPU during the warm-up
     T = w["trials"]
     stream = torch.cuda.Stream()
     A_dev = torch.from_numpy(inst.A).cuda()

@@ -85,6 +85,10 @@ typedef struct {
                            on different streams share the GPU */
   int32_t stream_g;     /* 0: keep G_off on chip when it fits, else stream its tiles from memory
                            every step; 1: always stream (FP32/BF16/FP16/FP8 only) */
+  int32_t autotune;     /* 0: the planner's cost model picks the Euler work split (deterministic);
+                           1: the first solve of a shape in this process times the cost model's
+                           four cheapest splits on this GPU (48 steps each, synchronising the
+                           problem's stream) and keeps the fastest for later solves */
 } cs_params;
 
 typedef struct cs_problem cs_problem;
@@ -116,9 +120,10 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
  * of all problems is one persistent launch in which every CTA takes whole
  * problems from a device work queue (largest N first) and streams that
  * problem's G_off tiles from memory, then one refit launch covers every
- * (problem, trial).  Problem i draws its initial amplitudes with instance
- * number i.  All problems must have been created on the same device and
- * stream.  Results are read per problem with cs_result / cs_result_trials.
+ * (problem, trial).  All outer iterations and the objective are captured
+ * into one CUDA graph, submitted to the problems' stream as a single launch.
+ * Problem i draws its initial amplitudes with instance number i.  All problems
+ * must have been created on the same device and stream.  Results are read per problem with cs_result / cs_result_trials.
  * Errors: CS_EINVAL (parameters, trials > 64, record_steps != 0, mixed
  * streams), CS_ENOMEM, CS_ECUDA. */
 cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials);
@@ -191,14 +196,18 @@ void cs_problem_destroy(cs_problem* p);
 
 /* ---- Serving: a continuous-batching request loop over the solver.
  * A server owns `max_slots` CUDA streams on the current device and a worker
- * thread.  Submitted requests wait in arrival order; one is admitted when a
- * slot is free and its device-memory estimate fits what is left of
- * `hbm_budget_bytes`.  An admitted request forms its problem (Gram on the GPU)
- * and queues its solve on its slot's stream with at most
- * max(1, SMs / max_slots) CTAs per Euler launch (unless params.max_ctas is
- * set) and cooperative launches, so the solves of several requests overlap on
- * the GPU.  When a solve finishes, the worker copies its result to host memory
- * and releases its device memory and slot at once.  A result is the same
+ * thread.  Each request gets an Euler grid sized to its work (unless
+ * params.max_ctas is set): one CTA per 26e6 coupling FMAs per step (N^2 x
+ * trials) and per 150 KB of G_off in its storage precision, at least 2; a request that would take more than half the SMs takes
+ * all but SMs / 16 of them, which stay for small requests.  Submitted requests
+ * are scanned in arrival order; each is admitted when a slot is free, its
+ * device-memory estimate fits what is left of `hbm_budget_bytes` and its grid
+ * fits the SMs not held by running requests (a request that does not fit yet
+ * does not hold back smaller ones behind it).  An admitted request forms its
+ * problem (Gram on the GPU) and queues its solve on its slot's stream with
+ * cooperative launches, so the solves of several requests overlap on the GPU.
+ * When a solve finishes, the worker copies its result to host memory and
+ * releases its device memory, SMs and slot at once.  A result is the same
  * whether the request ran alone or among others (same work split, fixed
  * summation order). */
 typedef struct cs_server cs_server;
@@ -208,7 +217,7 @@ cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server
 
 /* Queue one reconstruction: A (M x N row-major) and y (M) are HOST pointers,
  * copied before the call returns; params and trials as for cs_solve (the
- * server sets cluster_size = 1 and, if 0, max_ctas).  *ticket names the
+ * server sets cluster_size = 1 and, if 0, max_ctas as above).  *ticket names the
  * request.  Errors: CS_EINVAL, CS_ENOMEM if the request can never fit the
  * budget. */
 cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,

@@ -48,7 +48,7 @@ class cs_params(ctypes.Structure):
         ("jacobi_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
         ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-        ("stream_g", ctypes.c_int32),
+        ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32),
     ]
 
 

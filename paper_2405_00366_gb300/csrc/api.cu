@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -161,6 +162,7 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->max_ctas < 0) return fail(CS_EINVAL, "max_ctas must be >= 0");
   if (p->stream_g != 0 && p->stream_g != 1) return fail(CS_EINVAL, "stream_g must be 0 or 1");
   if (p->stream_g == 1 && p->precision == CS_P_FP64) return fail(CS_EINVAL, "FP64 G_off is never streamed");
+  if (p->autotune != 0 && p->autotune != 1) return fail(CS_EINVAL, "autotune must be 0 or 1");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -224,6 +226,32 @@ RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) 
 }  // namespace cs
 
 using namespace cs;
+
+// Executable batch graphs stay alive until their stream has run them; finished
+// ones are destroyed at the next batched solve (and at unload).
+namespace {
+std::mutex g_graph_mu;
+std::vector<std::pair<cudaStream_t, cudaGraphExec_t>> g_graphs;
+
+void reap_batch_graphs() {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size();) {
+    if (cudaStreamQuery(g_graphs[i].first) != cudaErrorNotReady) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(g_graphs[i].second);
+      g_graphs[i] = g_graphs.back();
+      g_graphs.pop_back();
+    } else {
+      ++i;
+    }
+  }
+}
+
+void keep_batch_graph(cudaStream_t st, cudaGraphExec_t exec) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  g_graphs.emplace_back(st, exec);
+}
+}  // namespace
 
 extern "C" {
 
@@ -391,7 +419,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   const size_t stride = (size_t)nmax * nmax + 2 * (size_t)nmax;
   int pool_blocks = std::min(n * trials, P0.num_sms);
   while (pool_blocks > 1 && (double)pool_blocks * stride * 8.0 > 16e9) --pool_blocks;
-  CS_CUDA(dev_alloc(&d_insts, ib * n, stream), "cudaMalloc batch descriptors");
+  CS_CUDA(dev_alloc(&d_insts, ib * n * (size_t)prm->n_outer, stream), "cudaMalloc batch descriptors");
   CS_CUDA(alloc(&d_order, n), "cudaMalloc batch order");
   CS_CUDA(alloc(&d_queue, 1), "cudaMalloc batch queue");
   CS_CUDA(alloc(&d_err, 1), "cudaMalloc batch error word");
@@ -412,16 +440,35 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P0.device), "clock rate");
   const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
   CS_CUDA(launch_init_R(d_jobs, n, trials, P0.num_sms, stream), "init R");
-  std::vector<unsigned char> hinst(ib * n);
-  for (int it = 0; it < prm->n_outer; ++it) {
+  // the descriptors of every outer iteration (eta changes), staged in one copy
+  std::vector<unsigned char> hinst(ib * n * (size_t)prm->n_outer);
+  for (int it = 0; it < prm->n_outer; ++it)
     for (int i = 0; i < n; ++i) {
       const double eta = eta_at(it, *prm, ps[i]->P.lambda);
-      fill_batch_inst(hinst.data() + ib * i, ps[i]->P, ps[i]->S, prm->precision, std::sqrt(prm->tau) * eta * eta / 4.0,
-                      i);
+      fill_batch_inst(hinst.data() + ib * ((size_t)it * n + i), ps[i]->P, ps[i]->S, prm->precision,
+                      std::sqrt(prm->tau) * eta * eta / 4.0, i);
     }
-    CS_CUDA(cudaMemcpyAsync(d_insts, hinst.data(), ib * n, cudaMemcpyHostToDevice, stream), "copy descriptors");
+  CS_CUDA(cudaMemcpyAsync(d_insts, hinst.data(), hinst.size(), cudaMemcpyHostToDevice, stream), "copy descriptors");
+  // Every outer iteration (batched Euler launch + refit) and the objective are
+  // captured into one CUDA graph and submitted as a single launch.
+  // (captured on a private stream: the problems' stream may be the legacy
+  // default stream, which cannot be captured; the graph then runs on theirs)
+  reap_batch_graphs();
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  CS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create the capture stream");
+  {
+    const cudaError_t eb = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (eb != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      CS_CUDA(eb, "begin graph capture");
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  const char* where = "";
+  for (int it = 0; it < prm->n_outer && e == cudaSuccess; ++it) {
     BatchLaunch L;
-    L.insts = d_insts;
+    L.insts = static_cast<unsigned char*>(d_insts) + ib * (size_t)n * it;
     L.order = d_order;
     L.n = n;
     L.T = trials;
@@ -431,12 +478,34 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
     L.err = d_err;
     L.timeout_cycles = timeout_cycles;
     L.ctas = prm->max_ctas > 0 ? std::min(prm->max_ctas, P0.num_sms) : P0.num_sms;
-    cudaError_t e = launch_euler_batch(L, stream);
-    if (e == cudaErrorInvalidConfiguration) return fail(CS_EINVAL, "batched Euler kernel does not fit shared memory");
-    CS_CUDA(e, "batched euler launch");
-    CS_CUDA(launch_refit(d_jobs, n, trials, pool, stride, pool_blocks, it, stream), "batched refit launch");
+    e = launch_euler_batch(L, cap);
+    where = "batched euler launch";
+    if (e == cudaSuccess) {
+      e = launch_refit(d_jobs, n, trials, pool, stride, pool_blocks, it, cap);
+      where = "batched refit launch";
+    }
   }
-  CS_CUDA(launch_finish(d_jobs, n, trials, P0.num_sms, stream), "batched finish launch");
+  if (e == cudaSuccess) {
+    e = launch_finish(d_jobs, n, trials, P0.num_sms, cap);
+    where = "batched finish launch";
+  }
+  const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (e == cudaErrorInvalidConfiguration) return fail(CS_EINVAL, "batched Euler kernel does not fit shared memory");
+    return fail(CS_ECUDA, std::string(e != cudaSuccess ? where : "end graph capture") + ": " +
+                              cudaGetErrorString(e != cudaSuccess ? e : ec));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CS_CUDA(e, "instantiate the batch graph");
+  e = cudaGraphLaunch(exec, stream);
+  if (e != cudaSuccess) cudaGraphExecDestroy(exec);
+  CS_CUDA(e, "launch the batch graph");
+  keep_batch_graph(stream, exec);
   dev_free(d_insts, stream);
   dev_free(d_order, stream);
   dev_free(d_queue, stream);

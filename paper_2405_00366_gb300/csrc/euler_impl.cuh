@@ -32,7 +32,12 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -688,7 +693,8 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide) {
 // its time rather than overlapping the product) and a fixed cost per cluster
 // rank for the reduction through distributed shared memory.
 template <typename GT, typename CT>
-cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out) {
+cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out,
+                      std::vector<std::pair<double, Plan>>* cands = nullptr) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
   const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
   const int twmax = round4(std::min(T, kTChunk));
@@ -707,11 +713,11 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
-  const int cands[] = {1, 2, 4, 8};
+  const int csizes[] = {1, 2, 4, 8};
   for (int pass = force_stream ? 1 : 0; pass < 2 && !found; ++pass) {
     const bool stream = pass == 1;
     if (stream && !streamable<GT>::value) break;
-    for (int C : cands) {
+    for (int C : csizes) {
       if (hint > 0 && C != hint) continue;
       if (C > nq || sms < C) continue;
       // variants: wide with WK = 1, 2, 4, 8 k-warps, then narrow (WK = 0)
@@ -807,6 +813,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             cost = std::max(fma / 128.0 / 0.45, gbytes / 22.0) + xbytes / 44.0;
           }
           cost += 300.0 * C;
+          if (cands) cands->emplace_back(cost, pl);
           if (!found || cost < best_cost) {
             best_cost = cost;
             bp = pl;
@@ -819,6 +826,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   }
   if (!found) { g_where = "make_plan: no work split fits"; return cudaErrorInvalidConfiguration; }
   *out = bp;
+  if (cands) std::stable_sort(cands->begin(), cands->end(), [](const std::pair<double, Plan>& x,
+                                                                const std::pair<double, Plan>& y) {
+    return x.first < y.first;
+  });
   return cudaSuccess;
 }
 
@@ -847,22 +858,11 @@ cudaError_t ensure_cluster_tiles(ProblemDev& P, int precision, const Plan& pl) {
   return cudaSuccess;
 }
 
+// One Euler launch of plan `pl` on the problem's stream: n_steps steps
+// (prm.n_steps for a real run, fewer for a tuning run) of outer iteration `outer`.
 template <typename GT, typename CT>
-cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                         long long timeout_cycles) {
-  // plans depend only on (N, T, hint) for a given device and precision
-  static thread_local struct { int64_t N; int T, hint, cap, strm, dev; Plan pl; bool valid; } cache = {
-      0, 0, 0, 0, 0, -1, {}, false};
-  Plan pl;
-  if (cache.valid && cache.N == P.N && cache.T == S.trials && cache.hint == prm.cluster_size &&
-      cache.cap == prm.max_ctas && cache.strm == prm.stream_g && cache.dev == P.device) {
-    pl = cache.pl;
-  } else {
-    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl);
-    if (e != cudaSuccess) return e;
-    cache.N = P.N; cache.T = S.trials; cache.hint = prm.cluster_size; cache.cap = prm.max_ctas;
-    cache.strm = prm.stream_g; cache.dev = P.device; cache.pl = pl; cache.valid = true;
-  }
+cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+                        long long timeout_cycles, const Plan& pl, int n_steps, bool record) {
   EulerArgs<CT> a;
   a.N = (int)P.N; a.Npad = (int)P.Npad; a.T = S.trials;
   a.C = pl.C; a.RPC = pl.RPC; a.ORW = pl.ORW; a.kq = pl.kq; a.kch = pl.kch; a.slots = pl.slots; a.RW = pl.RW;
@@ -882,9 +882,9 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   a.Gs = P.Gs; a.gscale = P.gscale; a.R = S.R; a.hz = P.hz;
   a.X0 = (CT*)S.X0; a.X1 = (CT*)S.X1;
   a.sigma = S.sigma;
-  a.record_steps = (outer == 0) ? std::min(S.record_steps, prm.n_steps) : 0;
+  a.record_steps = (record && outer == 0) ? std::min(S.record_steps, n_steps) : 0;
   a.rec_c = S.rec_c; a.rec_e = S.rec_e;
-  a.n_steps = prm.n_steps; a.dt = prm.dt;
+  a.n_steps = n_steps; a.dt = prm.dt;
   a.pump_kind = prm.pump_kind; a.p0 = prm.p0; a.p1 = prm.p1; a.p_thr = prm.p_thr; a.d = prm.d;
   a.t0 = prm.t0; a.width = prm.width;
   a.beta = prm.beta; a.tau = prm.tau; a.Kj = prm.K * prm.j;
@@ -924,6 +924,78 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+// Autotuner: time the kTuneCands cheapest candidate splits of the cost model
+// on this GPU (kTuneSteps Euler steps each, twice, CUDA events on the
+// problem's stream; the second run counts) and return the fastest.  The runs
+// only write the solve's scratch (X, sigma), which the real run rewrites.
+constexpr int kTuneCands = 4;
+constexpr int kTuneSteps = 48;
+
+template <typename GT, typename CT>
+cudaError_t autotune_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+                          long long timeout_cycles, const std::vector<std::pair<double, Plan>>& cands, Plan* out) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  const int steps = std::min(prm.n_steps, kTuneSteps);
+  for (size_t c = 0; c < cands.size() && (int)c < kTuneCands && e == cudaSuccess; ++c) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, P.stream);
+      if (e == cudaSuccess) e = launch_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands[c].second, steps,
+                                                    false);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, P.stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e == cudaSuccess && (c == 0 || ms < best)) {
+      best = ms;
+      *out = cands[c].second;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) g_where = "autotuning run";
+  return e;
+}
+
+template <typename GT, typename CT>
+cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
+                         long long timeout_cycles) {
+  // plans depend only on the shape, the caller's limits and the device; one
+  // cache per process (so every thread and every solve of a shape agrees)
+  struct Key {
+    int64_t N;
+    int T, hint, cap, strm, dev, tune;
+    bool operator<(const Key& o) const {
+      return std::tie(N, T, hint, cap, strm, dev, tune) < std::tie(o.N, o.T, o.hint, o.cap, o.strm, o.dev, o.tune);
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, Plan> cache;
+  const Key key{P.N, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g, P.device, prm.autotune};
+  Plan pl;
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) { pl = it->second; hit = true; }
+  }
+  if (!hit) {
+    std::vector<std::pair<double, Plan>> cands;
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl, &cands);
+    if (e != cudaSuccess) return e;
+    if (prm.autotune && cands.size() > 1) {
+      e = autotune_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands, &pl);
+      if (e != cudaSuccess) return e;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = pl;
+  }
+  return launch_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, pl, prm.n_steps, true);
 }
 
 }  // namespace

@@ -1,13 +1,20 @@
 // Continuous-batching request loop (host code; the GPU work is the solver's own
-// kernels).  Requests are admitted in arrival order whenever a slot (a CUDA
-// stream of the server) is free and the request's device-memory estimate fits
-// the remaining HBM budget; each admitted request forms its problem (G stays on
-// the device for its solve) and queues its solve on its slot's stream with a
-// bounded grid, so the work of several requests overlaps on the GPU.  A worker
-// thread harvests finished requests by event query, copies their results to
-// host memory and frees their device memory and slot at once, which is what
-// lets the next request in the queue in.
+// kernels).  Each request gets a grid sized to its work (Euler CTAs, each a
+// whole SM: about one per 26 million coupling FMAs per step and per 150 KB of
+// G_off, at least 2; a request that would take more than half the GPU takes all
+// SMs but a small reserve, so that small requests keep running beside it).
+// Requests are admitted whenever a slot (a CUDA stream of the server) is free,
+// the request's device-memory estimate fits the remaining HBM budget and its
+// grid fits the SMs not held by running requests; the queue is scanned in
+// arrival order and a request that does not fit yet does not hold back smaller
+// ones behind it.  Each admitted request forms its problem (G stays on the
+// device for its solve) and queues its solve on its slot's stream as a
+// cooperative launch, so the work of several requests overlaps on the GPU.  A
+// worker thread harvests finished requests by event query, copies their results
+// to host memory and frees their device memory, SMs and slot at once, which is
+// what lets the next requests in.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -62,11 +69,24 @@ size_t request_bytes(int64_t M, int64_t N, int trials, int precision) {
   return b + (1u << 20);
 }
 
+// Euler CTAs for a request: one per 26e6 coupling FMAs per step (N^2 T), and
+// enough that each holds at most about 150 KB of G_off on chip, at least 2;
+// more than half the GPU becomes all SMs but a reserve of num_sms / 16 for
+// small requests.
+int server_grid(int num_sms, int64_t N, int trials, int precision) {
+  const double work = (double)N * (double)N * (double)trials;
+  const double gbytes = (double)N * (double)N * (double)cs::storage_bytes(precision);
+  int d = (int)std::max(std::ceil(work / 26.0e6), std::ceil(gbytes / 150.0e3));
+  d = std::max(2, std::min(d, num_sms));
+  if (d > num_sms / 2) d = num_sms - std::max(2, num_sms / 16);
+  return d;
+}
+
 }  // namespace
 
 struct cs_server {
   size_t budget = 0, in_use = 0;
-  int max_slots = 0, device = 0, num_sms = 0;
+  int max_slots = 0, device = 0, num_sms = 0, sms_in_use = 0;
   std::vector<cudaStream_t> streams;
   std::vector<char> slot_busy;
   std::deque<Request*> queue;
@@ -89,6 +109,7 @@ struct cs_server {
     r->t_done = now_s();
     slot_busy[r->slot] = 0;
     in_use -= r->bytes;
+    sms_in_use -= r->prm.max_ctas;
     r->A.clear();
     r->A.shrink_to_fit();
     r->y.clear();
@@ -100,6 +121,7 @@ struct cs_server {
     r->slot = s;
     slot_busy[s] = 1;
     in_use += r->bytes;
+    sms_in_use += r->prm.max_ctas;
     r->t_start = now_s();
     r->x_hat.resize((size_t)r->N);
     r->sigma_hat.resize((size_t)r->N);
@@ -118,6 +140,7 @@ struct cs_server {
       r->t_done = now_s();
       slot_busy[s] = 0;
       in_use -= r->bytes;
+      sms_in_use -= r->prm.max_ctas;
       return;
     }
     r->state = RQ_RUNNING;
@@ -139,13 +162,17 @@ struct cs_server {
           ++i;
         }
       }
-      while (!queue.empty()) {
-        Request* r = queue.front();
+      for (auto it = queue.begin(); it != queue.end();) {
+        Request* r = *it;
         int s = -1;
         for (int i = 0; i < max_slots; ++i)
           if (!slot_busy[i]) { s = i; break; }
-        if (s < 0 || in_use + r->bytes > budget) break;
-        queue.pop_front();
+        if (s < 0) break;
+        if (in_use + r->bytes > budget || sms_in_use + r->prm.max_ctas > num_sms) {
+          ++it;
+          continue;
+        }
+        it = queue.erase(it);
         start(r, s);
         progressed = true;
       }
@@ -212,8 +239,10 @@ cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int6
   r->N = N;
   r->lambda = lambda;
   r->prm = *prm;
-  // solves of a server share the GPU: a bounded grid and cooperative launches
-  if (r->prm.max_ctas <= 0) r->prm.max_ctas = std::max(1, sv->num_sms / sv->max_slots);
+  // solves of a server share the GPU: a grid sized to the work and cooperative
+  // launches (which keep every CTA of a grid resident while grids share SMs)
+  if (r->prm.max_ctas <= 0) r->prm.max_ctas = server_grid(sv->num_sms, N, trials, prm->precision);
+  r->prm.max_ctas = std::min(r->prm.max_ctas, sv->num_sms);
   r->prm.cluster_size = 1;
   r->trials = trials;
   r->bytes = request_bytes(M, N, trials, prm->precision);

@@ -213,11 +213,24 @@ def test_large_support_takes_fp64_factorisation():
     np.testing.assert_allclose(g["R"], r["R"], rtol=0, atol=1e-8)
 
 
+def test_autotuned_split_matches_oracle():
+    """autotune = 1 times the cheapest candidate work splits on the GPU and keeps the
+    fastest; whichever it keeps, the solve matches the oracle (FP32 tolerances)."""
+    inst = cs_inputs.random_instance(600, 360, 60, 0.01, 0.03, seed=12)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp32", seed=5,
+             autotune=1)
+    g = gpu_solve(inst, w, 8)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=8)
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_allclose(g["x_hat"], r["x_hat"], rtol=0, atol=1e-5)
+
+
 def test_trials64_full_size_properties():
     """The N = 2000, 64-trial workload at full size (30 x 2000 steps), in the launch
-    configuration the benchmark times.  The oracle runs trials 0 and 1 for the first two
-    outer iterations; the rest is checked by properties that hold at any size."""
-    w = cs_inputs.workload("trials64_n2000_fp32")
+    configuration the benchmark times (autotuned work split).  The oracle runs trials 0
+    and 1 for the first two outer iterations; the rest is checked by properties that hold
+    at any size."""
+    w = cs_inputs.workload("trials64_n2000_fp32", autotune=1)
     inst = cs_inputs.workload_instance(w)
     g = gpu_solve(inst, w, 64)
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(dict(w, n_outer=2)), trials=2)

@@ -89,3 +89,26 @@ def test_server_argument_checks_need_no_gpu():
     assert cs.lib().cs_server_create(1 << 30, 0, ctypes.byref(h)) == cs.CS_EINVAL
     d = ctypes.c_int32()
     assert cs.lib().cs_server_poll(None, 1, ctypes.byref(d)) == cs.CS_EINVAL
+
+
+@pytest.mark.gpu
+def test_small_requests_backfill_beside_a_large_one():
+    """A large request takes all SMs but a reserve; small requests submitted after
+    it start while it runs, and a second large request waits for the SMs."""
+    base = cs_inputs.WORKLOADS["single_n200_fp64"]
+    big = (cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=5),
+           dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], n_outer=2, n_steps=1500), 64)
+    small = (cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=6), dict(base, n_outer=2, n_steps=300), 1)
+    sv = cs.cs_server_create(8 << 30, 8)
+    try:
+        order = [big, small, small, big]
+        tickets = [cs.cs_server_submit(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in order]
+        times = []
+        for (inst, w, T), t in zip(order, tickets):
+            cs.cs_server_wait(sv, t)
+            times.append(cs.cs_server_result(sv, t, inst.N)[4])
+    finally:
+        cs.cs_server_destroy(sv)
+    b1, s1, s2, b2 = times
+    assert s1[1] < b1[2] and s2[1] < b1[2]  # the small ones started before the first large one finished
+    assert b2[1] >= b1[2] - 1e-3            # the second large one waited for the SMs
