@@ -65,9 +65,20 @@ def fp32_simt_peak_tflops(sm_mhz, num_sms=152):
     return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def recorded_traffic(kernel_src):
+KERNEL_SOURCES = ["euler_kernel.cuh", "kernels_common.cuh", "tma.cuh", "common.cuh"]
+
+
+def kernel_source_sha256():
+    """sha256 over the device sources of the Euler kernel (in KERNEL_SOURCES order)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2405_00366_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
     """DRAM bytes per Euler launch from the committed ncu summary, if it was taken on
-    the current kernel source (its sha256 is recorded beside the figure)."""
+    the current kernel sources (their sha256 is recorded beside the figure)."""
     path = os.path.join(ROOT, "profiles", "euler_kernel_trials64_n2000.md")
     if not os.path.exists(path):
         return None
@@ -76,8 +87,7 @@ def recorded_traffic(kernel_src):
     h = re.search(r"euler_source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m.group(1)) if sha == h.group(1) else None
+    return float(m.group(1)) if kernel_source_sha256() == h.group(1) else None
 
 
 class ClockSampler:
@@ -525,7 +535,7 @@ def main():
     flops_per_launch = 2.0 * w["N"] * (w["N"] - 1) * T * w["n_steps"]
     achieved = flops_per_launch / per_launch_s / 1e12
     peak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2405_00366_gb300", "csrc", "euler_impl.cuh"))
+    traffic = recorded_traffic()
     ms_sorted = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": args.steps,

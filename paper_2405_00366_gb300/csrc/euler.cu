@@ -1,4 +1,5 @@
-// Dispatch of one CIM run (the persistent Euler kernel of euler_impl.cuh) to
+// Dispatch of one CIM run (the persistent Euler kernel of euler_kernel.cuh,
+// planned and launched by euler_impl.cuh) to
 // the translation unit built for the storage precision of G_off.
 #include "internal.h"
 

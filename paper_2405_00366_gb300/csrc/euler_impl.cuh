@@ -1,635 +1,19 @@
-// One CIM run of Algorithm 1 as a single persistent, cooperative kernel:
-// initial amplitudes, the constant part of the injection, every explicit Euler
-// step of Eq. mfeq1 / Eq. GMFZEC5 and the sign readout sigma = H(c).
-//
-// Per step the cost is the coupling product U = G_off X with X = R o c
-// (continuous field, Eq. localfieldMFZ) or X = R o H(c) (binarised field,
-// Eq. localfieldMFZBN), for all T trials at once (an N x N x T product).  The
-// rest of the local field is constant within a run because R is fixed there,
-// so it is folded into one vector per trial computed before the first step:
-//   cn: R_r h_r - theta = -1/4 R_r U_r + b_r,
-//       b_r = R_r (-(sqrt tau / 4) (G_off R)_r + (sqrt tau / 2) (A^T y)_r) - theta
-//   bn: R_r h_r - theta = -(sqrt tau / 2) R_r U_r + q_r,
-//       q_r = (sqrt tau / 2) R_r (A^T y)_r - theta
-// with theta = sqrt(tau) eta^2 / 4 (Eq. MFZlocalfieldmain).
-//
-// Work split (2-D, over thread-block clusters of C CTAs):
-//  * cluster c owns rows [c*RPC, (c+1)*RPC) of G_off; CTA rank j of the cluster
-//    owns the j-th 1/C of the k range, so its block of G_off (RPC x N/C) stays
-//    in shared memory for the whole run;
-//  * each step, a producer warp streams this CTA's k rows of X (N/C x T) from
-//    L2 into a shared-memory ring with bulk copies (mbarrier full/empty
-//    handshake), while eight consumer warps form RPC x T partial products;
-//  * the C partials of a row are summed through distributed shared memory:
-//    CTA j reduces and updates rows [j*RPC/C, (j+1)*RPC/C) of its cluster,
-//    whose c, e, b stay in its shared memory, and writes their next X;
-//  * all CTAs then meet at a bounded grid barrier; X is double-buffered in
-//    global memory, so one barrier per step suffices.
-// Versus every CTA reading all of X, the cluster cuts the L2 -> SM traffic of
-// X by C.  C = 1 is the plain row-block split.
+// Host side of one CIM run: the planner that picks the work split of the
+// persistent Euler kernel (euler_kernel.cuh) for N, T and this GPU, the
+// optional autotuner, and the launcher.
 #pragma once
-
-#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
-#include <type_traits>
 #include <utility>
 #include <vector>
 
-#include "common.cuh"
-#include "internal.h"
-#include "kernels_common.cuh"
-#include "tma.cuh"
-
-namespace cg = cooperative_groups;
+#include "euler_kernel.cuh"
 
 namespace cs {
-
-// The last CUDA call attempted by an Euler launcher on this thread.
-extern thread_local const char* g_where;
-
 namespace {
-
-constexpr int kConsumerWarps = 8;
-constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
-constexpr int kTChunk = 64;                          // trials per block of X
-constexpr int kMaxRowsPerLane = 8;                   // accumulator rows per lane
-
-// Consumer warps per column block of trials (one: every warp takes all trials of
-// a block; measured faster on GB300 than splitting the trials between warps).
-__host__ __device__ __forceinline__ int col_warps(int) { return 1; }
-
-template <typename CT>
-struct EulerArgs {
-  int N, Npad, T;
-  int C;        // CTAs per cluster
-  int RPC;      // rows of G_off per cluster
-  int ORW;      // rows reduced and updated per CTA (RPC / C rounded up)
-  int kq;       // k-quads per CTA (the last rank may have fewer)
-  int kch;      // k rows per bulk copy (multiple of 4)
-  int slots;    // ring slots
-  int RW;       // rows per consumer warp (RG * MR; RPC_pad = 8 RW rows are staged)
-  size_t slot_bytes;  // bytes of one ring slot
-  size_t xoff;        // offset of the X chunk inside a slot (after the G tile when streaming)
-  const void* Gt2;    // streamed G_off tiles [cluster][k tile][RPC_pad][32] (streaming plans)
-  int nkct;           // k tiles of 32 columns (Npad / 32)
-  int RG;       // row groups of a warp
-  int RPC_pad;  // staged rows per CTA (multiple of 8 RW >= RPC; padding rows are zero)
-  int WK;       // wide split: k-warps per row-warp (1 for the narrow split)
-  int ldg;      // row stride of the resident G block, in elements
-  const void* Gs;  // Npad x Npad storage-precision G_off
-  const float* gscale;  // row scales of G_off (FP8 storage only)
-  const double* R;
-  const double* hz;
-  CT* X0;
-  CT* X1;
-  uint8_t* sigma;
-  double* rec_c;
-  double* rec_e;
-  int record_steps;
-  int n_steps;
-  double dt;
-  int pump_kind;
-  double p0, p1, p_thr, d, t0, width;
-  double beta, tau, Kj, theta;
-  int field;
-  int init_kind;
-  double init_scale;
-  uint64_t seed;
-  int instance, outer;
-  unsigned* bar;
-  int* err;
-  long long timeout_cycles;
-  unsigned phantom;
-};
-
-// X is stored in blocks of kTChunk trials: block t0 (t0 a multiple of 64) holds
-// trials [t0, t0 + tw) as an Npad x twp matrix (twp = tw rounded up to 4,
-// padding columns zero), row-major or, for the wide split, k-pair interleaved
-// (see xoff), so any run of k rows of a block is contiguous and moves with one
-// bulk copy.
-__host__ __device__ __forceinline__ size_t xblock(int t0, int Npad) { return (size_t)t0 * Npad; }
-__host__ __device__ __forceinline__ int xwidth(int t0, int T) {
-  return round4(T - t0 < kTChunk ? T - t0 : kTChunk);
-}
-
-// Shared-memory layout of one CTA (byte offsets): resident G block (absent when
-// streaming), ring, partials (prows rows), owned state, mbarriers.
-struct Smem {
-  size_t g, ring, part, st, bars, total;
-};
-__host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t slot_bytes, int slots, int prows,
-                                                     int twmax, int ORW, int T, size_t cbytes) {
-  Smem s;
-  s.g = 0;
-  s.ring = align128(gbytes_block);
-  s.part = s.ring + align128((size_t)slots * slot_bytes);
-  s.st = s.part + align128((size_t)prows * twmax * cbytes);
-  s.bars = s.st + align128((size_t)4 * ORW * T * cbytes);
-  s.total = s.bars + 2 * (size_t)slots * sizeof(uint64_t);
-  return s;
-}
-
-// Streamed G_off tiles of a cluster plan: tile (cluster c, k tile kc) holds rows
-// [c RPC, c RPC + RPC_pad) (zero past the cluster's rows and past N) and
-// columns [32 kc, 32 kc + 32), contiguous, with the quad q of row r at
-// q ^ (r & 7) so that the row groups of a warp read distinct banks.
-constexpr int kStreamK = 32;
-
-template <typename GT>
-__global__ void store_cluster_tiles_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int RPC,
-                                           int RPC_pad, int NC, int nkct, const float* __restrict__ gscale) {
-  const size_t total = (size_t)NC * nkct * RPC_pad * kStreamK;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t tile = idx / ((size_t)RPC_pad * kStreamK);
-    const int within = (int)(idx % ((size_t)RPC_pad * kStreamK));
-    const int r = within / kStreamK, kp = within % kStreamK;
-    const int c = (int)(tile / nkct), kc = (int)(tile % nkct);
-    const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
-    const int row = c * RPC + r, col = kc * kStreamK + k;
-    double v = (r < RPC && row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
-    if constexpr (row_scaled<GT>::value) v = (r < RPC && row < N) ? v / gscale[row] : 0.0;
-    Gt[idx] = to_storage<GT>(v);
-  }
-}
-
-// Producer side of one block of trials (lane 0 of warp 8): stream this CTA's
-// k rows of X (and, when streaming, the G_off tiles) through the ring.  `gctr`
-// counts ring uses across calls so the mbarrier phases stay consistent.
-template <typename GT, typename CT, bool STREAM>
-__device__ __forceinline__ void produce_chunks(const EulerArgs<CT>& a, const CT* __restrict__ Xblk, int twp, int k0,
-                                               int klen, int cl, unsigned char* ring, uint64_t* full,
-                                               uint64_t* empty, unsigned gctr) {
-  const int nch = (klen + a.kch - 1) / a.kch;
-  if ((threadIdx.x & 31) == 0) {
-    // earlier generic accesses of X and of the ring come before the copies
-    fence_proxy_async_global();
-    fence_proxy_async_shared();
-    for (int ci = 0; ci < nch; ++ci) {
-      const unsigned g = gctr + ci;
-      const int s = (int)(g % a.slots);
-      const unsigned u = g / a.slots;
-      if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
-        set_error(a.err, DEV_TIMEOUT);
-        break;
-      }
-      const int kr = min(a.kch, klen - ci * a.kch);
-      const unsigned bytes = (unsigned)((size_t)kr * twp * sizeof(CT));
-      unsigned char* slot = ring + (size_t)s * a.slot_bytes;
-      if constexpr (STREAM) {
-        const unsigned gtb = (unsigned)((size_t)a.RPC_pad * kStreamK * sizeof(GT));
-        const size_t kc = (size_t)(k0 + ci * a.kch) / kStreamK;
-        const GT* src = reinterpret_cast<const GT*>(a.Gt2) + ((size_t)cl * a.nkct + kc) * a.RPC_pad * kStreamK;
-        mbar_arrive_expect_tx(full + s, gtb + bytes);
-        bulk_copy_g2s(slot, src, gtb, full + s);
-      } else {
-        mbar_arrive_expect_tx(full + s, bytes);
-      }
-      bulk_copy_g2s(slot + a.xoff, Xblk + (size_t)(k0 + ci * a.kch) * twp, bytes, full + s);
-    }
-  }
-}
-
-// Partial products of this CTA's block for one block of trials:
-//   P[r][tt] = sum_{k in this CTA's range} G_off[row0 + r][k] X[k][tt].
-// Warp 8 (lane 0) streams the k rows of X through the ring; warps 0-7 compute.
-// `gctr` counts ring uses across calls so the mbarrier phases stay consistent.
-// Consumer lanes: CG = twp/4 (rounded up to a power of two) column groups of
-// four trials, RG row groups and KG = 32/(CG RG) k groups; a lane accumulates
-// MR rows x 4 trials (its warp's RW = RG * MR rows are interleaved over the row
-// groups) over every KG-th k-quad of each chunk, and the k groups are summed
-// with shuffles at the end.  The inner loop loads four k-rows of X and MR x 4
-// entries of G, then issues 16 MR independent FMAs.
-template <typename GT, typename CT, int MR, bool STREAM>
-__device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
-                                                 const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
-                                                 int cl, unsigned char* ring, CT* P, uint64_t* full,
-                                                 uint64_t* empty, unsigned& gctr) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int nch = (klen + a.kch - 1) / a.kch;
-  const int ldg = a.ldg;
-  if (w == kConsumerWarps) {
-    produce_chunks<GT, CT, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
-    gctr += nch;
-    return;
-  }
-  // warp grid: WR row-warps x WC column-warps; a column-warp owns tcw trials
-  const int WC = col_warps(twp), WR = kConsumerWarps / WC;
-  const int wr = w % WR, wc = w / WR;
-  const int tcw = twp / WC;
-  int CG = 1;
-  while (CG * 4 < tcw) CG <<= 1;
-  const int RG = a.RG;             // row groups (power of two, CG * RG <= 32)
-  const int KG = 32 / (CG * RG);   // k groups: lanes that split the k rows of a chunk
-  const int cgi = l % CG, rg = (l / CG) % RG, kg = l / (CG * RG);
-  const bool colok = cgi * 4 < tcw;
-  const int col = wc * tcw + cgi * 4;  // first of this lane's four trials
-  const int rbase = wr * a.RW + rg;    // this lane's rows: rbase + RG * i, i < MR
-  CT acc[MR][4];
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = CT(0);
-  bool ok = true;
-  for (int ci = 0; ci < nch; ++ci) {
-    const unsigned g = gctr + ci;
-    const int s = (int)(g % a.slots);
-    const unsigned u = g / a.slots;
-    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
-      ok = false;
-      if (l == 0) set_error(a.err, DEV_TIMEOUT);
-    }
-    if (ok && colok) {
-      const CT* xs = reinterpret_cast<const CT*>(ring + (size_t)s * a.slot_bytes + a.xoff) + col;
-      const int kr = min(a.kch, klen - ci * a.kch);
-      const GT* gk = STREAM ? reinterpret_cast<const GT*>(ring + (size_t)s * a.slot_bytes) + (size_t)rbase * kStreamK
-                            : Gsm + (size_t)rbase * ldg + ci * a.kch;
-#pragma unroll 2
-      for (int kk = 4 * kg; kk < kr; kk += 4 * KG) {
-        CT xv[4][4], gv[MR][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(kk + j) * twp, xv[j]);
-#pragma unroll
-        for (int i = 0; i < MR; ++i) {
-          if constexpr (STREAM) {
-            const int r = rbase + RG * i;
-            load4<CT, GT>(gk + (size_t)(RG * i) * kStreamK + 4 * ((kk >> 2) ^ (r & 7)), gv[i]);
-          } else {
-            load4<CT, GT>(gk + (size_t)(RG * i) * ldg + kk, gv[i]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int i = 0; i < MR; ++i)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][q] = fma(gv[i][j], xv[j][q], acc[i][q]);
-      }
-    }
-    __syncwarp();
-    if (l == 0) mbar_arrive(empty + s);
-  }
-  gctr += nch;
-  // sum over the k groups of the warp
-  for (int o = CG * RG; o < 32; o <<= 1) {
-#pragma unroll
-    for (int i = 0; i < MR; ++i)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][q] += __shfl_xor_sync(0xffffffffu, acc[i][q], o);
-  }
-  if (colok && kg == 0) {
-#pragma unroll
-    for (int i = 0; i < MR; ++i) {
-      const int r = rbase + RG * i;
-      if (r < nrows) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) P[(size_t)r * twp + col + q] = acc[i][q];
-      }
-    }
-  }
-}
-
-// Two FP32 values in one 64-bit register, and the packed FMA of sm_100 and
-// later (fma.rn.f32x2: two independent round-to-nearest FMAs, each exactly
-// fmaf), which issues two FMAs per instruction.
-__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 unpack2(uint64_t v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-
-// G_off quad (four consecutive k of one row) as two k-pairs.
-template <typename GT>
-__device__ __forceinline__ ulonglong2 load_gpairs(const GT* p) {
-  float v[4];
-  load4<float, GT>(p, v);
-  return make_ulonglong2(pack2(v[0], v[1]), pack2(v[2], v[3]));
-}
-template <>
-__device__ __forceinline__ ulonglong2 load_gpairs<float>(const float* p) {
-  return *reinterpret_cast<const ulonglong2*>(p);
-}
-
-// Offset of X[k][t] in a block of twp trials: k-pair interleaved for the wide
-// split ([k/2][t][k%2], so that (X[k][t], X[k+1][t]) is one 64-bit operand of
-// the packed FMA), plain row-major [k][t] otherwise.  Any run of an even number
-// of k rows starting at an even k is contiguous in both.
-template <bool PAIR>
-__device__ __forceinline__ size_t xoff(int k, int t, int twp) {
-  return PAIR ? ((size_t)(k >> 1) * twp + t) * 2 + (k & 1) : (size_t)k * twp + t;
-}
-
-// Partial products of the wide split (FP32 compute; a block of twp trials,
-// twp in {8, 16, 32, 64}; X k-pair interleaved).  Lane (cg, rg) accumulates MR
-// rows (rbase + RG i) x 4 trials (4 cg .. 4 cg + 3) with CG = twp / 4 and
-// RG = 32 / CG; a quarter-warp covers 8 / cq rows x cq column groups
-// (cq = min(CG, 4)), so that each shared-memory load of a half-warp is one
-// wavefront.  The sums over even and odd k are kept apart in the two halves of
-// each 64-bit accumulator (packed FMAs with a G pair and an X pair, no operand
-// shuffling) and added at the end.  The consumer warps form WR row-warps x WK
-// k-warps; k-warp kw takes every WK-th k-quad of each chunk.  The k-warps'
-// partials are left in the ring (idle once every chunk of the block has been
-// consumed) as [kw][RPC_pad][twp], for sum_k_warps.
-template <typename GT, int MR, bool STREAM>
-__device__ __forceinline__ void wide_partials(const EulerArgs<float>& a, const GT* __restrict__ Gsm,
-                                              const float* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
-                                              int cl, unsigned char* ring, float* P, uint64_t* full,
-                                              uint64_t* empty, unsigned& gctr) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int nch = (klen + a.kch - 1) / a.kch;
-  if (w == kConsumerWarps) {
-    produce_chunks<GT, float, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
-    gctr += nch;
-    return;
-  }
-  const int WK = a.WK, WR = kConsumerWarps / WK;
-  const int wr = w % WR, kw = w / WR;
-  const int CG = twp >> 2, RG = 32 / CG;
-  const int cq = CG < 4 ? CG : 4, qd = l >> 3, li = l & 7;
-  const int cg = (qd % (CG / cq)) * cq + li % cq, rg = (qd / (CG / cq)) * (8 / cq) + li / cq;
-  const int rbase = wr * a.RW + rg;
-  const int c = 4 * cg;
-  uint64_t acc[MR][4];
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
-  bool ok = true;
-  for (int ci = 0; ci < nch; ++ci) {
-    const unsigned g = gctr + ci;
-    const int s = (int)(g % a.slots);
-    const unsigned u = g / a.slots;
-    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
-      ok = false;
-      if (l == 0) set_error(a.err, DEV_TIMEOUT);
-    }
-    if (ok) {
-      const unsigned char* slot = ring + (size_t)s * a.slot_bytes;
-      const float* xs = reinterpret_cast<const float*>(slot + a.xoff) + 2 * c;
-      const int nqc = min(a.kch, klen - ci * a.kch) >> 2;
-      const GT* gk = STREAM ? reinterpret_cast<const GT*>(slot) + (size_t)rbase * kStreamK
-                            : Gsm + (size_t)rbase * a.ldg + ci * a.kch;
-#pragma unroll 1
-      for (int q = kw; q < nqc; q += WK) {
-        ulonglong2 gp[MR];
-#pragma unroll
-        for (int i = 0; i < MR; ++i) {
-          if constexpr (STREAM) {
-            gp[i] = load_gpairs<GT>(gk + (size_t)(RG * i) * kStreamK + 4 * (q ^ ((rbase + RG * i) & 7)));
-          } else {
-            gp[i] = load_gpairs<GT>(gk + (size_t)(RG * i) * a.ldg + 4 * q);
-          }
-        }
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          // k-pair 2q + pp: (X[k][t], X[k+1][t]) for the lane's four trials
-          const float* xp = xs + (size_t)(2 * q + pp) * twp * 2;
-          const ulonglong2 x01 = *reinterpret_cast<const ulonglong2*>(xp);
-          const ulonglong2 x23 = *reinterpret_cast<const ulonglong2*>(xp + 4);
-#pragma unroll
-          for (int i = 0; i < MR; ++i) {
-            const uint64_t gg = pp ? gp[i].y : gp[i].x;
-            fma2(acc[i][0], gg, x01.x);
-            fma2(acc[i][1], gg, x01.y);
-            fma2(acc[i][2], gg, x23.x);
-            fma2(acc[i][3], gg, x23.y);
-          }
-        }
-      }
-    }
-    __syncwarp();
-    if (l == 0) mbar_arrive(empty + s);
-  }
-  gctr += nch;
-  // every consumer warp is done with the ring before it holds partials
-  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
-  float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
-#pragma unroll
-  for (int i = 0; i < MR; ++i) {
-    const int r = rbase + RG * i;
-    {
-      float v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 h = unpack2(acc[i][q]);
-        v[q] = h.x + h.y;
-      }
-      *reinterpret_cast<float4*>(dst + (size_t)r * twp + c) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-  }
-}
-
-// P = the sum of the WK k-warp partials left in the ring (fixed order), for the
-// first nrows rows; then the ring may be refilled by bulk copies.  (Measured on
-// GB300: cheaper than letting the cluster read all C x WK planes remotely.)
-__device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const unsigned char* ring, float* P,
-                                            int twp, int nrows) {
-  __syncthreads();
-  const float* Pw = reinterpret_cast<const float*>(ring);
-  const size_t plane = (size_t)a.RPC_pad * twp;
-  for (int idx = threadIdx.x; idx < nrows * twp; idx += kThreads) {
-    float v = Pw[idx];
-    for (int kw = 1; kw < a.WK; ++kw) v += Pw[kw * plane + idx];
-    P[idx] = v;
-  }
-  fence_proxy_async_shared();
-}
-
-// One block of trials: this CTA's partial products in P (rows < nrows).
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE>
-__device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
-                                               const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
-                                               int cl, unsigned char* ring, CT* P, uint64_t* full, uint64_t* empty,
-                                               unsigned& gctr) {
-  if constexpr (WIDE) {
-    wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
-    sum_k_warps(a, ring, P, twp, nrows);
-  } else {
-    cluster_partials<GT, CT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
-  }
-}
-
-// Sum of the C cluster partials at offset `off`, in the fixed order rank 0, 1,
-// ...  (A plain loop over the C ranks: measured on GB300 about 2 us per Euler
-// step faster than predicated loads from all eight possible ranks.)
-template <typename CT>
-__device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, size_t off, int C) {
-  CT s = CT(0);
-  for (int jj = 0; jj < C; ++jj) s += cluster.map_shared_rank(P, jj)[off];
-  return s;
-}
-
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE>
-__global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = a.C;
-  const int j = (int)cluster.block_rank();
-  const int cl = blockIdx.x / C;
-  const int N = a.N, T = a.T, Npad = a.Npad;
-  const int row0 = cl * a.RPC;                     // first row of this cluster
-  const int nrows = max(0, min(a.RPC, N - row0));  // rows of this cluster
-  const int nq = Npad >> 2;
-  const int q0 = j * a.kq;
-  const int nqj = max(0, min(a.kq, nq - q0));      // k-quads of this CTA
-  const int k0 = q0 * 4, klen = nqj * 4;
-  const int own0 = j * a.ORW;                      // first owned row (cluster-local)
-  const int nown = max(0, min(a.ORW, nrows - own0));
-  const int twmax = round4(min(T, kTChunk));
-  const Smem L = smem_layout(STREAM ? 0 : (size_t)a.RPC_pad * a.ldg * sizeof(GT), a.slot_bytes, a.slots,
-                             a.RPC_pad, twmax, a.ORW, T, sizeof(CT));
-  GT* Gsm = reinterpret_cast<GT*>(smem_raw + L.g);
-  unsigned char* ring = smem_raw + L.ring;
-  CT* P = reinterpret_cast<CT*>(smem_raw + L.part);
-  CT* c_s = reinterpret_cast<CT*>(smem_raw + L.st);
-  CT* e_s = c_s + (size_t)a.ORW * T;
-  CT* b_s = e_s + (size_t)a.ORW * T;
-  CT* R_s = b_s + (size_t)a.ORW * T;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
-  uint64_t* empty = full + a.slots;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < a.slots; ++i) {
-      mbar_init(full + i, 1);
-      mbar_init(empty + i, kConsumerWarps);
-    }
-    fence_mbar_init();
-  }
-  // Stage this CTA's block of G_off: rows [row0, row0 + nrows), k in [k0, k0 + klen).
-  if (!STREAM) {
-    const GT* src = reinterpret_cast<const GT*>(a.Gs);
-    const int ldg = a.ldg;
-    const int total = a.RPC_pad * nqj;
-    for (int v = threadIdx.x; v < total; v += kThreads) {
-      const int r = v / nqj, q = v % nqj;
-      GT* d4 = Gsm + (size_t)r * ldg + 4 * q;
-      if (r < nrows) {
-        const GT* s4 = src + (size_t)(row0 + r) * Npad + k0 + 4 * q;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) d4[e] = s4[e];
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) d4[e] = GT(0.0f);
-      }
-    }
-  }
-  // owned R
-  for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
-    const int r = idx / T, t = idx % T;
-    R_s[idx] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
-  }
-  __syncthreads();
-  unsigned gctr = 0;
-  const double st = sqrt(a.tau);
-  const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
-  unsigned bar_k = 0;
-
-  // ---- prologue: b (or q), initial c and e, first X.
-  if (a.field == CS_FIELD_CN) {
-    for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
-      const int r = idx / T, t = idx % T;
-      const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-      a.X0[xblock(t0, Npad) + xoff<WIDE>(row0 + own0 + r, t - t0, twp)] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
-    }
-    fence_proxy_async_global();
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
-    for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                full, empty, gctr);
-      cluster.sync();
-      for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
-        const int r = idx / tw, tt = idx % tw;
-        const int gr = row0 + own0 + r;
-        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr);
-        const double Rr = a.R[(size_t)gr * T + t0 + tt];
-        b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
-      }
-      cluster.sync();
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
-      const int r = idx / T, t = idx % T;
-      const int gr = row0 + own0 + r;
-      b_s[idx] = CT((st / 2.0) * a.R[(size_t)gr * T + t] * a.hz[gr] - a.theta);
-    }
-  }
-  for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
-    const int r = idx / T, t = idx % T;
-    const int gr = row0 + own0 + r;
-    const uint64_t key = run_key(a.seed, (uint64_t)a.instance, (uint64_t)t, (uint64_t)a.outer);
-    const CT c0 = CT(initial_amplitude(key, (uint64_t)gr, a.init_kind, a.init_scale));
-    c_s[idx] = c0;
-    e_s[idx] = CT(1);
-    const CT Rr = R_s[idx];
-    const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-    a.X1[xblock(t0, Npad) + xoff<WIDE>(gr, t - t0, twp)] =
-        (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
-  }
-  fence_proxy_async_global();
-  if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
-
-  // ---- Euler steps
-  const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
-  CT* Xc = a.X1;
-  CT* Xn = a.X0;
-  for (int n = 0; n < a.n_steps; ++n) {
-    const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
-    const bool last = (n + 1 == a.n_steps);
-    const bool rec = n < a.record_steps;
-    for (int t0 = 0; t0 < T; t0 += kTChunk) {
-      const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                full, empty, gctr);
-      cluster.sync();
-      CT* Xnb = Xn + xblock(t0, Npad);
-      for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
-        const int r = idx / tw, tt = idx % tw;
-        const int gr = row0 + own0 + r;
-        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr);
-        const size_t so = (size_t)r * T + t0 + tt;
-        const CT Rr = R_s[so];
-        const CT f = wcoef * Rr * U + b_s[so];
-        const CT cc = c_s[so], ee = e_s[so];
-        const CT c2 = cc * cc;
-        const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
-        const CT en = ee + dt * (-beta * (c2 - tau) * ee);
-        c_s[so] = cn;
-        e_s[so] = en;
-        Xnb[xoff<WIDE>(gr, tt, twp)] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
-        const size_t o = (size_t)gr * T + t0 + tt;
-        if (rec) {
-          const size_t ro = (size_t)n * N * T + o;
-          a.rec_c[ro] = (double)cn;
-          a.rec_e[ro] = (double)en;
-        }
-        if (last) a.sigma[o] = cn > CT(0) ? 1 : 0;
-      }
-      // every CTA of the cluster has read this CTA's partials before they are rewritten
-      if (t0 + kTChunk < T) cluster.sync();
-    }
-    if (last) break;
-    // the next X is read by bulk copies (async proxy) of every CTA after the barrier
-    fence_proxy_async_global();
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) break;
-    CT* tmp = Xc; Xc = Xn; Xn = tmp;
-  }
-  cluster.sync();  // peers may still read this CTA's partials
-}
-
-
 struct Plan {
   int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, RG, MR, WK, ldg;
   bool stream, wide;
