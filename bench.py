@@ -239,8 +239,9 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     dev = [(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda()) for i in insts]
     torch.cuda.synchronize()
-    prm_b = _run_params(cs, "bf16", max_ctas=0)
-    prm_p = _run_params(cs, "fp32")
+    over = {k: v for k, v in (("n_outer", args.n_outer), ("n_steps", args.n_steps)) if v}
+    prm_b = _run_params(cs, "bf16", **over)
+    prm_p = _run_params(cs, "fp32", **over)
 
     def batched():
         hs = [cs.cs_problem_create(A, y, i.lam, stream=stream) for (A, y), i in zip(dev, insts)]
@@ -285,10 +286,10 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": t_b * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
         "config": {"workload": "batch_uneven_bf16", "instances": len(insts), "N_range": [min(Ns), max(Ns)],
-                   "alphas": b["alphas"], "sparsities": b["sparsities"], "trials": T, "n_outer": 30,
-                   "n_steps": 2000, "precision": "bf16", "note": "N range scaled down from [256, 4096]: "
+                   "alphas": b["alphas"], "sparsities": b["sparsities"], "trials": T, "n_outer": prm_b.n_outer,
+                   "n_steps": prm_b.n_steps, "precision": "bf16", "note": "N range scaled down from [256, 4096]: "
                    "the batched kernel runs each problem on one CTA"},
-        "spin_steps_per_s": sum(Ns) * T * 30 * 2000 / t_b,
+        "spin_steps_per_s": sum(Ns) * T * prm_b.n_outer * prm_b.n_steps / t_b,
         "quality": {"rmse_mean": float(np.mean(rmse_b)),
                     "rmse_mean_first_plain": float(np.mean(rmse_b[:b["n_plain"]])),
                     "plain_fp32_rmse_mean": float(np.mean(plain_rmse))},

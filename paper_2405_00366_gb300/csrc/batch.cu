@@ -19,6 +19,7 @@
 // those rows of c and e (kept in global memory, L2-resident) and write their
 // next X.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -91,6 +92,12 @@ struct BArgs {
 
 __host__ __device__ __forceinline__ size_t b_slot_bytes(int twp, size_t gbytes, size_t cbytes) {
   return align128((size_t)kRT * kKC * gbytes + (size_t)kKC * twp * cbytes);
+}
+
+// Partials of one row tile: kRT x twp, or for the wide form WK = 64 / twp
+// planes of it (64 kRT values either way).
+__host__ __device__ __forceinline__ size_t b_part_bytes(int twp, size_t cbytes, bool pair) {
+  return align128((size_t)kRT * (pair ? 64 : twp) * cbytes);
 }
 
 // Partial-free product of one row tile: U[r][tt] = sum_k G_off[rt*kRT + r][k] X[k][tt]
@@ -190,8 +197,142 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
   return ok;
 }
 
+// Wide form of tile_product for FP32 compute and twp in {8, 16, 32, 64}, with X
+// k-pair interleaved (see xoff): lane (cg, rg) holds 8 rows (rbase + RG i) x 4
+// trials (4 cg ..) as 64-bit accumulators of the even-k and odd-k sums, fed by
+// packed FMAs of a G_off pair and an X pair; CG = twp / 4, RG = 32 / CG, a
+// quarter-warp covers 8 / cq rows x cq column groups (cq = min(CG, 4)).  The
+// consumer warps form WR = 16 / RG row-warps (RG x 8 rows each, 128 in all) x
+// WK = RG / 2 k-warps; k-warp kw takes every WK-th quad of each 32-column tile
+// and writes its partials to plane kw of P ([WK][kRT][twp]); the caller sums
+// the planes.
+template <typename GT>
+__device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const BInst<float>& I,
+                                                  const float* __restrict__ X, int rt, unsigned char* ring,
+                                                  size_t slot, float* P, uint64_t* full, uint64_t* empty,
+                                                  unsigned& gctr, unsigned* issued) {
+  constexpr int MR = 8;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int twp = a.twp, nkc = I.nkc;
+  const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
+  const unsigned xbytes = (unsigned)(kKC * twp * sizeof(float));
+  bool ok = true;
+  if (w == kBWarps) {
+    if (l == 0) {
+      fence_proxy_async_global();
+      const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const unsigned g = gctr + kc;
+        const int s = (int)(g % a.slots);
+        const unsigned u = g / a.slots;
+        if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
+          set_error(a.err, DEV_TIMEOUT);
+          break;
+        }
+        unsigned char* dst = ring + (size_t)s * slot;
+        issued[s] = g + 1;
+        mbar_arrive_expect_tx(full + s, (unsigned)gtile + xbytes);
+        bulk_copy_g2s(dst, gsrc + (size_t)kc * kRT * kKC, (unsigned)gtile, full + s);
+        bulk_copy_g2s(dst + gtile, X + (size_t)kc * kKC * twp, xbytes, full + s);
+      }
+    }
+    gctr += nkc;
+    return true;
+  }
+  const int CG = twp >> 2, RG = 32 / CG;
+  const int WR = 16 / RG, WK = kBWarps / WR;
+  const int wr = w % WR, kw = w / WR;
+  const int cq = CG < 4 ? CG : 4, qd = l >> 3, li = l & 7;
+  const int cg = (qd % (CG / cq)) * cq + li % cq, rg = (qd / (CG / cq)) * (8 / cq) + li / cq;
+  const int rbase = wr * RG * MR + rg;
+  const int c = 4 * cg;
+  uint64_t acc[MR][4];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
+  for (int kc = 0; kc < nkc; ++kc) {
+    const unsigned g = gctr + kc;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok) {
+      const GT* gt = reinterpret_cast<const GT*>(ring + (size_t)s * slot);
+      const float* xs = reinterpret_cast<const float*>(ring + (size_t)s * slot + gtile) + 2 * c;
+#pragma unroll 1
+      for (int q = kw; q < kKC / 4; q += WK) {
+        ulonglong2 gp[MR];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int r = rbase + RG * i;
+          gp[i] = load_gpairs<GT>(gt + (size_t)r * kKC + 4 * (q ^ (r & 7)));
+        }
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          const float* xp = xs + (size_t)(2 * q + pp) * twp * 2;
+          const ulonglong2 x01 = *reinterpret_cast<const ulonglong2*>(xp);
+          const ulonglong2 x23 = *reinterpret_cast<const ulonglong2*>(xp + 4);
+#pragma unroll
+          for (int i = 0; i < MR; ++i) {
+            const uint64_t gg = pp ? gp[i].y : gp[i].x;
+            fma2(acc[i][0], gg, x01.x);
+            fma2(acc[i][1], gg, x01.y);
+            fma2(acc[i][2], gg, x23.x);
+            fma2(acc[i][3], gg, x23.y);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (l == 0) mbar_arrive(empty + s);
+  }
+  gctr += nkc;
+  float* dst = P + (size_t)kw * kRT * twp;
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    const int r = rbase + RG * i;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 h = unpack2(acc[i][q]);
+      v[q] = h.x + h.y;
+    }
+    *reinterpret_cast<float4*>(dst + (size_t)r * twp + c) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  return ok;
+}
+
+// U of row rl (tile-local) and trial t: the partials of the row tile, summed
+// over the k-warp planes of the wide form (one plane otherwise).
+template <typename CT, bool PAIR>
+__device__ __forceinline__ CT tile_sum(const CT* P, int rl, int t, int twp) {
+  if constexpr (PAIR) {
+    const int WK = (32 / (twp >> 2)) / 2;
+    CT v = P[(size_t)rl * twp + t];
+    for (int kw = 1; kw < WK; ++kw) v += P[(size_t)kw * kRT * twp + (size_t)rl * twp + t];
+    return v;
+  } else {
+    return P[(size_t)rl * twp + t];
+  }
+}
+
+// Product of one row tile in the form the launch was built for.
+template <typename GT, typename CT, int MR, bool PAIR>
+__device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
+                                                 int rt, unsigned char* ring, size_t slot, CT* P, uint64_t* full,
+                                                 uint64_t* empty, unsigned& gctr, unsigned* issued) {
+  if constexpr (PAIR) {
+    return tile_product_pair<GT>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
+  } else {
+    return tile_product<GT, CT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
+  }
+}
+
 // One CIM run of problem I.  Returns false (in every thread) if a wait timed out.
-template <typename GT, typename CT, int MR>
+template <typename GT, typename CT, int MR, bool PAIR>
 __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned char* ring, size_t slot, CT* P,
                              uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued) {
   const int T = a.T, twp = a.twp, N = I.N;
@@ -206,16 +347,17 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   if (a.field == CS_FIELD_CN) {
     for (size_t idx = threadIdx.x; idx < NT; idx += kBThreads) {
       const int r = (int)(idx / T), t = (int)(idx % T);
-      I.X0[(size_t)r * twp + t] = CT(I.R[idx]);
+      I.X0[xoff<PAIR>(r, t, twp)] = CT(I.R[idx]);
     }
     fence_proxy_async_global();
     __syncthreads();
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
-      ok = __syncthreads_and(tile_product<GT, CT, MR>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued));
+      ok = __syncthreads_and(
+          row_tile_product<GT, CT, MR, PAIR>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int r = rt * kRT + idx / T, t = idx % T;
         if (r >= N) continue;
-        const double v = (double)(P[(size_t)(idx / T) * twp + t] * row_scale<GT, CT>(I.gscale, r));
+        const double v = (double)(tile_sum<CT, PAIR>(P, idx / T, t, twp) * row_scale<GT, CT>(I.gscale, r));
         const size_t o = (size_t)r * T + t;
         b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta);
       }
@@ -234,7 +376,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     c[o] = c0;
     e[o] = CT(1);
     const CT Rr = CT(I.R[o]);
-    I.X1[(size_t)r * twp + t] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+    I.X1[xoff<PAIR>(r, t, twp)] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
   }
   fence_proxy_async_global();
   __syncthreads();
@@ -246,12 +388,13 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
     const bool last = (n + 1 == a.n_steps);
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
-      ok = __syncthreads_and(tile_product<GT, CT, MR>(a, I, Xc, rt, ring, slot, P, full, empty, gctr, issued));
+      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
+                                                                issued));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int rl = idx / T, t = idx % T, r = rt * kRT + rl;
         if (r >= N) continue;
         const size_t o = (size_t)r * T + t;
-        const CT U = P[(size_t)rl * twp + t] * row_scale<GT, CT>(I.gscale, r);
+        const CT U = tile_sum<CT, PAIR>(P, rl, t, twp) * row_scale<GT, CT>(I.gscale, r);
         const CT Rr = CT(I.R[o]);
         const CT f = wcoef * Rr * U + b[o];
         const CT cc = c[o], ee = e[o];
@@ -260,7 +403,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
         c[o] = cn;
         e[o] = en;
-        Xn[(size_t)r * twp + t] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        Xn[xoff<PAIR>(r, t, twp)] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
         if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
       }
       __syncthreads();
@@ -272,13 +415,13 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   return ok;
 }
 
-template <typename GT, typename CT, int MR>
+template <typename GT, typename CT, int MR, bool PAIR>
 __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT));
   unsigned char* ring = smem_raw;
   CT* P = reinterpret_cast<CT*>(smem_raw + (size_t)a.slots * slot);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + align128((size_t)kRT * a.twp * sizeof(CT)));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + b_part_bytes(a.twp, sizeof(CT), PAIR));
   uint64_t* empty = full + a.slots;
   __shared__ int s_next;
   if (threadIdx.x == 0) {
@@ -299,7 +442,7 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
     __syncthreads();
     if (qi >= a.n) break;
     const BInst<CT> I = a.insts[a.order[qi]];
-    ok = run_instance<GT, CT, MR>(a, I, ring, slot, P, full, empty, gctr, issued);
+    ok = run_instance<GT, CT, MR, PAIR>(a, I, ring, slot, P, full, empty, gctr, issued);
   }
   // After a timeout, let any copy still in flight land before the CTA exits.
   if (!ok && threadIdx.x == kBWarps * 32) {
@@ -308,11 +451,11 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
   }
 }
 
-template <typename GT, typename CT, int MR>
+template <typename GT, typename CT, int MR, bool PAIR>
 cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
   const size_t slot = b_slot_bytes(twp, sizeof(GT), sizeof(CT));
-  auto fn = euler_batch_kernel<GT, CT, MR>;
+  auto fn = euler_batch_kernel<GT, CT, MR, PAIR>;
   int optin = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -321,7 +464,7 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, fn);
   if (e != cudaSuccess) return e;
-  const size_t fixed = align128((size_t)kRT * twp * sizeof(CT));
+  const size_t fixed = b_part_bytes(twp, sizeof(CT), PAIR);
   const size_t cap = (size_t)optin - fa.sharedSizeBytes;
   int slots = 8;
   while (slots > 2 && (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t) > cap) --slots;
@@ -350,20 +493,25 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.timeout_cycles = L.timeout_cycles;
   e = cudaMemsetAsync(L.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  euler_batch_kernel<GT, CT, MR><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
+  euler_batch_kernel<GT, CT, MR, PAIR><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename GT, typename CT>
 cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
+  const int twp = round4(L.T);
+  if constexpr (std::is_same<CT, float>::value) {
+    // the wide form (packed FMAs) for trial blocks of 8, 16, 32 or 64
+    if (twp == 8 || twp == 16 || twp == 32 || twp == 64) return launch_batch_typed<GT, CT, 8, true>(L, st);
+  }
   int CG = 1;
-  while (CG * 4 < round4(L.T)) CG <<= 1;
+  while (CG * 4 < twp) CG <<= 1;
   const int RG = std::min(16, 32 / CG);
   switch (16 / RG) {
-    case 1: return launch_batch_typed<GT, CT, 1>(L, st);
-    case 2: return launch_batch_typed<GT, CT, 2>(L, st);
-    case 4: return launch_batch_typed<GT, CT, 4>(L, st);
-    default: return launch_batch_typed<GT, CT, 8>(L, st);
+    case 1: return launch_batch_typed<GT, CT, 1, false>(L, st);
+    case 2: return launch_batch_typed<GT, CT, 2, false>(L, st);
+    case 4: return launch_batch_typed<GT, CT, 4, false>(L, st);
+    default: return launch_batch_typed<GT, CT, 8, false>(L, st);
   }
 }
 

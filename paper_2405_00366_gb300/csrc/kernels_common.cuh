@@ -78,4 +78,42 @@ __device__ __forceinline__ CT row_scale(const float* gscale, int r) {
   return CT(1);
 }
 
+// Two FP32 values in one 64-bit register, and the packed FMA of sm_100 and
+// later (fma.rn.f32x2: two independent round-to-nearest FMAs, each exactly
+// fmaf), which issues two FMAs per instruction.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// G_off quad (four consecutive k of one row) as two k-pairs.
+template <typename GT>
+__device__ __forceinline__ ulonglong2 load_gpairs(const GT* p) {
+  float v[4];
+  load4<float, GT>(p, v);
+  return make_ulonglong2(pack2(v[0], v[1]), pack2(v[2], v[3]));
+}
+template <>
+__device__ __forceinline__ ulonglong2 load_gpairs<float>(const float* p) {
+  return *reinterpret_cast<const ulonglong2*>(p);
+}
+
+// Offset of X[k][t] in a block of twp trials: k-pair interleaved for the wide
+// split ([k/2][t][k%2], so that (X[k][t], X[k+1][t]) is one 64-bit operand of
+// the packed FMA), plain row-major [k][t] otherwise.  Any run of an even number
+// of k rows starting at an even k is contiguous in both.
+template <bool PAIR>
+__device__ __forceinline__ size_t xoff(int k, int t, int twp) {
+  return PAIR ? ((size_t)(k >> 1) * twp + t) * 2 + (k & 1) : (size_t)k * twp + t;
+}
+
 }  // namespace cs

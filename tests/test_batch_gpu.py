@@ -62,6 +62,19 @@ def test_batch_matches_oracle(precision):
         assert int(g[i]["stats"][0]) == r["best_trial"]
 
 
+@pytest.mark.parametrize("T", [8, 16, 64])
+def test_batch_wide_form_matches_oracle(T):
+    """FP32 batches of 8, 16 or 64 trials take the wide form of the batched kernel
+    (packed FMAs over k-pairs, k-warps): supports identical to the oracle's, x_hat to 1e-5."""
+    insts = uneven([40, 150, 333, 130, 257], seed=8)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp32", seed=6)
+    g = run_batch(insts, w, T)
+    for i, inst in enumerate(insts):
+        r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)
+        np.testing.assert_array_equal(g[i]["sigmas"], r["sigmas"])
+        np.testing.assert_allclose(g[i]["x_hat"], r["x_hat"], rtol=0, atol=1e-5)
+
+
 def test_batch_equals_individual_solves():
     """A problem gives the same support and signal alone (cs_solve, instance i) and in a batch."""
     insts = uneven([64, 200, 96], seed=11)
