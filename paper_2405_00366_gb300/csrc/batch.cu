@@ -76,6 +76,7 @@ struct BArgs {
   const int* order;  // processing order (largest first)
   int n;
   int T, twp, slots;
+  int tps;          // column tiles per ring slot (1, 2 or 4)
   int* queue;
   int n_steps;
   double dt;
@@ -90,8 +91,10 @@ struct BArgs {
   long long timeout_cycles;
 };
 
-__host__ __device__ __forceinline__ size_t b_slot_bytes(int twp, size_t gbytes, size_t cbytes) {
-  return align128((size_t)kRT * kKC * gbytes + (size_t)kKC * twp * cbytes);
+// One ring slot: tps consecutive column tiles of G_off, then their tps x kKC
+// rows of X.
+__host__ __device__ __forceinline__ size_t b_slot_bytes(int twp, size_t gbytes, size_t cbytes, int tps) {
+  return align128((size_t)tps * kRT * kKC * gbytes + (size_t)tps * kKC * twp * cbytes);
 }
 
 // Partials of one row tile: kRT x twp, or for the wide form WK = 64 / twp
@@ -111,27 +114,29 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
   const unsigned xbytes = (unsigned)(kKC * twp * sizeof(CT));
+  const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
     if (l == 0) {
       fence_proxy_async_global();
       const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
-      for (int kc = 0; kc < nkc; ++kc) {
-        const unsigned g = gctr + kc;
+      for (int ci = 0; ci < nch; ++ci) {
+        const unsigned g = gctr + ci;
         const int s = (int)(g % a.slots);
         const unsigned u = g / a.slots;
         if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
           set_error(a.err, DEV_TIMEOUT);
           break;
         }
+        const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
         unsigned char* dst = ring + (size_t)s * slot;
         issued[s] = g + 1;
-        mbar_arrive_expect_tx(full + s, (unsigned)gtile + xbytes);
-        bulk_copy_g2s(dst, gsrc + (size_t)kc * kRT * kKC, (unsigned)gtile, full + s);
-        bulk_copy_g2s(dst + gtile, X + (size_t)kc * kKC * twp, xbytes, full + s);
+        mbar_arrive_expect_tx(full + s, (unsigned)(nt * (gtile + xbytes)));
+        bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
+        bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
       }
     }
-    gctr += nkc;
+    gctr += nch;
     return true;
   }
   int CG = 1;
@@ -147,8 +152,8 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
   for (int i = 0; i < MR; ++i)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[i][q] = CT(0);
-  for (int kc = 0; kc < nkc; ++kc) {
-    const unsigned g = gctr + kc;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
     const int s = (int)(g % a.slots);
     const unsigned u = g / a.slots;
     if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
@@ -157,16 +162,18 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
     }
     if (ok && colok) {
       const GT* gt = reinterpret_cast<const GT*>(ring + (size_t)s * slot);
-      const CT* xs = reinterpret_cast<const CT*>(ring + (size_t)s * slot + gtile) + col;
+      const CT* xs = reinterpret_cast<const CT*>(ring + (size_t)s * slot + a.tps * gtile) + col;
+      const int nq = min(a.tps, nkc - ci * a.tps) * (kKC / 4);
 #pragma unroll 2
-      for (int q = kg; q < kKC / 4; q += KG) {
+      for (int q = kg; q < nq; q += KG) {
         CT xv[4][4], gv[MR][4];
+        const GT* gq = gt + (size_t)(q >> 3) * kRT * kKC;  // tile of quad q
 #pragma unroll
         for (int j = 0; j < 4; ++j) load4<CT, CT>(xs + (size_t)(4 * q + j) * twp, xv[j]);
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
           const int r = rbase + RG * i;
-          load4<CT, GT>(gt + (size_t)r * kKC + 4 * (q ^ (r & 7)), gv[i]);
+          load4<CT, GT>(gq + (size_t)r * kKC + 4 * ((q & 7) ^ (r & 7)), gv[i]);
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -179,7 +186,7 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
     __syncwarp();
     if (l == 0) mbar_arrive(empty + s);
   }
-  gctr += nkc;
+  gctr += nch;
   for (int o = CG * RG; o < 32; o <<= 1) {
 #pragma unroll
     for (int i = 0; i < MR; ++i)
@@ -216,27 +223,29 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
   const unsigned xbytes = (unsigned)(kKC * twp * sizeof(float));
+  const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
     if (l == 0) {
       fence_proxy_async_global();
       const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
-      for (int kc = 0; kc < nkc; ++kc) {
-        const unsigned g = gctr + kc;
+      for (int ci = 0; ci < nch; ++ci) {
+        const unsigned g = gctr + ci;
         const int s = (int)(g % a.slots);
         const unsigned u = g / a.slots;
         if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
           set_error(a.err, DEV_TIMEOUT);
           break;
         }
+        const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
         unsigned char* dst = ring + (size_t)s * slot;
         issued[s] = g + 1;
-        mbar_arrive_expect_tx(full + s, (unsigned)gtile + xbytes);
-        bulk_copy_g2s(dst, gsrc + (size_t)kc * kRT * kKC, (unsigned)gtile, full + s);
-        bulk_copy_g2s(dst + gtile, X + (size_t)kc * kKC * twp, xbytes, full + s);
+        mbar_arrive_expect_tx(full + s, (unsigned)(nt * (gtile + xbytes)));
+        bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
+        bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
       }
     }
-    gctr += nkc;
+    gctr += nch;
     return true;
   }
   const int CG = twp >> 2, RG = 32 / CG;
@@ -251,8 +260,8 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
   for (int i = 0; i < MR; ++i)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
-  for (int kc = 0; kc < nkc; ++kc) {
-    const unsigned g = gctr + kc;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
     const int s = (int)(g % a.slots);
     const unsigned u = g / a.slots;
     if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
@@ -261,14 +270,16 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
     }
     if (ok) {
       const GT* gt = reinterpret_cast<const GT*>(ring + (size_t)s * slot);
-      const float* xs = reinterpret_cast<const float*>(ring + (size_t)s * slot + gtile) + 2 * c;
+      const float* xs = reinterpret_cast<const float*>(ring + (size_t)s * slot + a.tps * gtile) + 2 * c;
+      const int nq = min(a.tps, nkc - ci * a.tps) * (kKC / 4);
 #pragma unroll 1
-      for (int q = kw; q < kKC / 4; q += WK) {
+      for (int q = kw; q < nq; q += WK) {
         ulonglong2 gp[MR];
+        const GT* gq = gt + (size_t)(q >> 3) * kRT * kKC;  // tile of quad q
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
           const int r = rbase + RG * i;
-          gp[i] = load_gpairs<GT>(gt + (size_t)r * kKC + 4 * (q ^ (r & 7)));
+          gp[i] = load_gpairs<GT>(gq + (size_t)r * kKC + 4 * ((q & 7) ^ (r & 7)));
         }
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp) {
@@ -289,7 +300,7 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
     __syncwarp();
     if (l == 0) mbar_arrive(empty + s);
   }
-  gctr += nkc;
+  gctr += nch;
   float* dst = P + (size_t)kw * kRT * twp;
 #pragma unroll
   for (int i = 0; i < MR; ++i) {
@@ -418,7 +429,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
 template <typename GT, typename CT, int MR, bool PAIR>
 __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT));
+  const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT), a.tps);
   unsigned char* ring = smem_raw;
   CT* P = reinterpret_cast<CT*>(smem_raw + (size_t)a.slots * slot);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + b_part_bytes(a.twp, sizeof(CT), PAIR));
@@ -454,7 +465,6 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
 template <typename GT, typename CT, int MR, bool PAIR>
 cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
-  const size_t slot = b_slot_bytes(twp, sizeof(GT), sizeof(CT));
   auto fn = euler_batch_kernel<GT, CT, MR, PAIR>;
   int optin = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -466,8 +476,16 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const size_t fixed = b_part_bytes(twp, sizeof(CT), PAIR);
   const size_t cap = (size_t)optin - fa.sharedSizeBytes;
-  int slots = 8;
-  while (slots > 2 && (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t) > cap) --slots;
+  // column tiles per slot: the most (4, 2, 1) that still leave 3 slots (measured:
+  // one 32-column tile per slot leaves too little work between ring handoffs)
+  int tps = 4, slots = 0;
+  size_t slot = 0;
+  for (; tps >= 1; tps >>= 1) {
+    slot = b_slot_bytes(twp, sizeof(GT), sizeof(CT), tps);
+    slots = 8;
+    while (slots > 2 && (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t) > cap) --slots;
+    if (slots >= 3 || tps == 1) break;
+  }
   const size_t smem = (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t);
   if (smem > cap) return cudaErrorInvalidConfiguration;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -479,6 +497,7 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.T = L.T;
   a.twp = twp;
   a.slots = slots;
+  a.tps = tps;
   a.queue = L.queue;
   a.n_steps = L.prm->n_steps;
   a.dt = L.prm->dt;
