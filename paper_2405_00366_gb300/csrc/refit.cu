@@ -35,6 +35,8 @@ __device__ bool same_support(const uint8_t* __restrict__ sigma, int N, int T, in
   return __syncthreads_or(diff) == 0;
 }
 
+constexpr size_t kBlockedSmem = (32 * 33 + 2 * 64 * 33) * sizeof(float);  // solve_mixed_blocked's tiles
+
 __device__ __forceinline__ size_t packed_off(int k, int n) { return (size_t)k * n - (size_t)k * (k - 1) / 2; }
 
 __device__ __forceinline__ double block_max(double v, double* scratch) {
@@ -138,6 +140,190 @@ __device__ bool solve_mixed(const RefitJob& J, const int* idx, int n, float* Lp,
   return prev <= 1e-12 * rn0;
 }
 
+// Blocked form of solve_mixed for supports whose packed factor does not fit in
+// shared memory: the FP32 copy of G_SS lives in this block's global workspace
+// (column-major, lower triangle), factorised right-looking in panels of 32
+// columns (the diagonal block by one warp in shared memory, the panel below it
+// by one thread per row, the trailing update in 64 x 64 tiles staged through
+// shared memory), then FP32 triangular solves by blocks of 32 and the same FP64
+// refinement and acceptance as solve_mixed.  W holds x and r (FP64, n each),
+// then L (n x n FP32) and d (n FP32); `sm` needs 21 KB.
+__device__ bool solve_mixed_blocked(const RefitJob& J, const int* idx, int n, double* W, float* sm) {
+  constexpr int NB = 32, TB = 64, LD = NB + 1;
+  constexpr int nw = kRefitThreads / 32;
+  const int N = J.N, tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  double* x = W;
+  double* r = W + n;
+  float* L = reinterpret_cast<float*>(W + 2 * (size_t)n);
+  float* d = L + (size_t)n * n;
+  float* D = sm;                // NB x LD: diagonal block
+  float* Ti = sm + NB * LD;     // TB x LD: rows of the panel for one tile row
+  float* Tk = Ti + TB * LD;     // TB x LD: rows of the panel for one tile column
+  __shared__ int ok_s;
+  __shared__ double red_s[kRefitThreads / 32];
+  for (int k = w; k < n; k += nw) {
+    const double* Gk = J.G + (size_t)idx[k] * N;
+    for (int i = k + l; i < n; i += 32) L[i + (size_t)k * n] = (float)Gk[idx[i]];
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int b = min(NB, n - j0);
+    for (int e = tid; e < b * b; e += kRefitThreads) {
+      const int c = e / b, i = e % b;
+      if (i >= c) D[i * LD + c] = L[(j0 + i) + (size_t)(j0 + c) * n];
+    }
+    __syncthreads();
+    if (w == 0) {  // unblocked Cholesky of the diagonal block, lane = row
+      int ok = 1;
+      for (int c = 0; c < b && ok; ++c) {
+        const float dc = D[c * LD + c];
+        ok = (dc > 1e-5f * (float)J.g[idx[j0 + c]] && isfinite(dc)) ? 1 : 0;
+        if (!ok) break;
+        const float sc = sqrtf(dc);
+        __syncwarp();
+        if (l == c) D[c * LD + c] = sc;
+        if (l > c && l < b) D[l * LD + c] /= sc;
+        __syncwarp();
+        for (int c2 = c + 1; c2 < b; ++c2)
+          if (l >= c2 && l < b) D[l * LD + c2] = fmaf(-D[l * LD + c], D[c2 * LD + c], D[l * LD + c2]);
+        __syncwarp();
+      }
+      if (l == 0) ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) return false;
+    for (int e = tid; e < b * b; e += kRefitThreads) {
+      const int c = e / b, i = e % b;
+      if (i >= c) L[(j0 + i) + (size_t)(j0 + c) * n] = D[i * LD + c];
+    }
+    // panel below the diagonal block: row i solves v L11^T = A[i, j0 : j0 + b]
+    for (int i = j0 + b + tid; i < n; i += kRefitThreads) {
+      float v[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) v[c] = c < b ? L[i + (size_t)(j0 + c) * n] : 0.f;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < b) {
+          float s = v[c];
+#pragma unroll
+          for (int c2 = 0; c2 < c; ++c2) s = fmaf(-v[c2], D[c * LD + c2], s);
+          v[c] = s / D[c * LD + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < b) L[i + (size_t)(j0 + c) * n] = v[c];
+    }
+    __syncthreads();
+    // trailing update A22 -= L21 L21^T (lower tiles), rows and columns from j1
+    const int j1 = j0 + b, m = n - j1, nt = (m + TB - 1) / TB;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    for (int ti = 0; ti < nt; ++ti) {
+      for (int tk = 0; tk <= ti; ++tk) {
+        const int ri0 = j1 + ti * TB, rk0 = j1 + tk * TB;
+        for (int e = tid; e < TB * NB; e += kRefitThreads) {
+          const int c = e / TB, rr = e % TB;
+          Ti[rr * LD + c] = (c < b && ri0 + rr < n) ? L[(ri0 + rr) + (size_t)(j0 + c) * n] : 0.f;
+          Tk[rr * LD + c] = (c < b && rk0 + rr < n) ? L[(rk0 + rr) + (size_t)(j0 + c) * n] : 0.f;
+        }
+        __syncthreads();
+        float acc[4][4] = {};
+        for (int c = 0; c < b; ++c) {
+          float a4[4], b4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a4[q] = Ti[(tr + q) * LD + c];
+            b4[q] = Tk[(tc + q) * LD + c];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) acc[q][q2] = fmaf(a4[q], b4[q2], acc[q][q2]);
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int col = rk0 + tc + q2;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int row = ri0 + tr + q;
+            if (row < n && col < n && row >= col) L[row + (size_t)col * n] -= acc[q][q2];
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // FP64 refinement with FP32 solves L L^T d = r
+  for (int i = tid; i < n; i += kRefitThreads) {
+    x[i] = 0.0;
+    r[i] = J.hz[idx[i]];
+  }
+  double rn0 = 0.0;
+  for (int i = tid; i < n; i += kRefitThreads) rn0 = fmax(rn0, fabs(J.hz[idx[i]]));
+  rn0 = block_max(rn0, red_s);
+  if (rn0 == 0.0) return true;
+  double prev = rn0;
+  for (int it = 0; it < 8; ++it) {
+    for (int i = tid; i < n; i += kRefitThreads) d[i] = (float)r[i];
+    __syncthreads();
+    for (int j0 = 0; j0 < n; j0 += NB) {  // L z = d
+      const int b = min(NB, n - j0);
+      if (w == 0) {
+        float zi = l < b ? d[j0 + l] : 0.f;
+        for (int c = 0; c < b; ++c) {
+          const float zc = __shfl_sync(0xffffffffu, zi, c) / L[(j0 + c) + (size_t)(j0 + c) * n];
+          if (l == c) zi = zc;
+          if (l > c && l < b) zi = fmaf(-L[(j0 + l) + (size_t)(j0 + c) * n], zc, zi);
+        }
+        if (l < b) d[j0 + l] = zi;
+      }
+      __syncthreads();
+      for (int i = j0 + b + tid; i < n; i += kRefitThreads) {
+        float s = d[i];
+        for (int c = 0; c < b; ++c) s = fmaf(-L[i + (size_t)(j0 + c) * n], d[j0 + c], s);
+        d[i] = s;
+      }
+      __syncthreads();
+    }
+    for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {  // L^T d = z
+      const int b = min(NB, n - j0);
+      if (w == 0) {
+        float xi = l < b ? d[j0 + l] : 0.f;
+        for (int c = b - 1; c >= 0; --c) {
+          const float xc = __shfl_sync(0xffffffffu, xi, c) / L[(j0 + c) + (size_t)(j0 + c) * n];
+          if (l == c) xi = xc;
+          if (l < c) xi = fmaf(-L[(j0 + c) + (size_t)(j0 + l) * n], xc, xi);
+        }
+        if (l < b) d[j0 + l] = xi;
+      }
+      __syncthreads();
+      for (int i = tid; i < j0; i += kRefitThreads) {
+        float s = d[i];
+        const float* Li = L + (size_t)i * n + j0;  // row block j0 of column i
+        for (int c = 0; c < b; ++c) s = fmaf(-Li[c], d[j0 + c], s);
+        d[i] = s;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < n; i += kRefitThreads) x[i] += (double)d[i];
+    __syncthreads();
+    for (int i = w; i < n; i += nw) {
+      const double* Gi = J.G + (size_t)idx[i] * N;
+      double s = 0.0;
+      for (int k = l; k < n; k += 32) s = fma(Gi[idx[k]], x[k], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) r[i] = J.hz[idx[i]] - s;
+    }
+    __syncthreads();
+    double rm = 0.0;
+    for (int i = tid; i < n; i += kRefitThreads) rm = fmax(rm, fabs(r[i]));
+    rm = block_max(rm, red_s);
+    if (rm <= 1e-14 * rn0 || (it >= 1 && rm > 0.5 * prev)) return rm <= 1e-12 * rn0;
+    prev = rm;
+  }
+  return prev <= 1e-12 * rn0;
+}
+
 // Refit of trial t of job J.  W is this block's global workspace (n^2 + 2n
 // doubles); `smem` (smem_bytes) holds the FP32 factor of the mixed-precision
 // path, taken when it fits and succeeds; otherwise the FP64 factorisation.
@@ -154,6 +340,9 @@ __device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, doubl
   if ((packed + (size_t)n) * sizeof(float) <= smem_bytes) {
     x = W;
     done = solve_mixed(J, idx, n, smem, smem + packed, W, W + n);
+  } else if (smem_bytes >= kBlockedSmem) {
+    x = W;
+    done = solve_mixed_blocked(J, idx, n, W, smem);
   }
   if (!done) {
     x = W + (size_t)n * n;

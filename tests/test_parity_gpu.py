@@ -201,9 +201,10 @@ def test_jacobi_refit_matches_oracle(precision, trials):
     np.testing.assert_allclose(g["energies"], r["energies"], rtol=1e-9 if precision == "fp64" else 1e-6)
 
 
-def test_large_support_takes_fp64_factorisation():
-    """Supports of more than about 310 entries do not fit the FP32 factor in shared memory
-    and take the FP64 Cholesky; against the oracle: identical supports, R to 1e-8."""
+def test_large_support_blocked_factor_matches_oracle():
+    """Supports of more than about 310 entries do not fit the packed FP32 factor in shared
+    memory and take the blocked FP32 factor in global memory with FP64 refinement (FP64
+    Cholesky if that does not converge); against the oracle: identical supports, R to 1e-8."""
     inst = cs_inputs.random_instance(900, 760, 420, 0.0, 0.005, seed=4)
     w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=500, precision="fp64")
     g = gpu_solve(inst, w, 2)
