@@ -62,12 +62,13 @@ def test_batch_matches_oracle(precision):
         assert int(g[i]["stats"][0]) == r["best_trial"]
 
 
-@pytest.mark.parametrize("T", [8, 16, 64])
-def test_batch_wide_form_matches_oracle(T):
+@pytest.mark.parametrize("T,field", [(8, "cn"), (16, "cn"), (64, "cn"), (16, "bn")])
+def test_batch_wide_form_matches_oracle(T, field):
     """FP32 batches of 8, 16 or 64 trials take the wide form of the batched kernel
-    (packed FMAs over k-pairs, k-warps): supports identical to the oracle's, x_hat to 1e-5."""
+    (packed FMAs over k-pairs, k-warps), with the continuous or the binarised field:
+    supports identical to the oracle's, x_hat to 1e-5."""
     insts = uneven([40, 150, 333, 130, 257], seed=8)
-    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp32", seed=6)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp32", seed=6, field=field)
     g = run_batch(insts, w, T)
     for i, inst in enumerate(insts):
         r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)

@@ -226,6 +226,18 @@ def test_autotuned_split_matches_oracle():
     np.testing.assert_allclose(g["x_hat"], r["x_hat"], rtol=0, atol=1e-5)
 
 
+def test_two_trial_blocks_match_oracle():
+    """128 trials: two blocks of 64 in one launch (wide split, per-block reductions);
+    supports identical to the oracle's, x_hat to 1e-5."""
+    inst = cs_inputs.random_instance(300, 180, 30, 0.01, 0.03, seed=21)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300, precision="fp32", seed=9)
+    g = gpu_solve(inst, w, 128)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=128)
+    np.testing.assert_array_equal(g["support_sizes"], r["support_sizes"])
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_allclose(g["x_hat"], r["x_hat"], rtol=0, atol=1e-5)
+
+
 def test_trials64_full_size_properties():
     """The N = 2000, 64-trial workload at full size (30 x 2000 steps), in the launch
     configuration the benchmark times (autotuned work split).  The oracle runs trials 0

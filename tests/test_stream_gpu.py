@@ -66,3 +66,14 @@ def test_mri_shaped_small(precision):
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=4)
     assert oracle.hamming_loss(g["sigma"], r["sigma"]) <= 0.01
     assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+
+
+def test_streamed_bf16_autotuned_matches_resident():
+    """Streamed G_off with the autotuner choosing among streamed splits: the same
+    supports as the resident default on a BF16 problem."""
+    w = cs_inputs.workload("trials64_n2000_fp32", N=800, M=480, nnz=80, n_outer=2, n_steps=500, precision="bf16")
+    inst = cs_inputs.workload_instance(w)
+    a = solve(inst, w, 64)
+    b = solve(inst, w, 64, stream_g=1, autotune=1)
+    np.testing.assert_array_equal(a["sigmas"], b["sigmas"])
+    np.testing.assert_allclose(a["x_hat"], b["x_hat"], rtol=0, atol=1e-6)
