@@ -14,7 +14,7 @@ sample of the same workload instead.
 
 Two further workloads print their own line (not the default):
   --workload batch_uneven_bf16   one step = one batched solve (cs_solve_batch) of
-      152 uneven instances (N in [256, 1024], alpha in {0.3, 0.5, 0.7}, a in
+      512 uneven instances (N in [256, 1024], alpha in {0.3, 0.5, 0.7}, a in
       {0.05, 0.1, 0.2}, 16 trials, 30 x 2000 steps, BF16 storage of G_off),
       against plain FP32 solves of the same instances one at a time (cs_solve);
   --workload serve_mix           a Poisson stream (200 requests/s) of 40 requests
@@ -211,7 +211,7 @@ def config_of(w, world):
 
 
 # ------------------------------------------------------------------ batched and served workloads
-BATCH = dict(n_inst=152, n_min=256, n_max=1024, alphas=[0.3, 0.5, 0.7], sparsities=[0.05, 0.1, 0.2],
+BATCH = dict(n_inst=512, n_min=256, n_max=1024, alphas=[0.3, 0.5, 0.7], sparsities=[0.05, 0.1, 0.2],
              nu=0.01, lam=0.03, trials=16, n_plain=16, seed=17)
 
 
