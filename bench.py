@@ -202,6 +202,29 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+def replica_workload(rank):
+    """The benchmark workload of one replica: the instance seed is offset by the rank,
+    so the N replicas solve N independent problems (no data exchange between ranks)."""
+    return cs_inputs.workload(WORKLOAD, seed=cs_inputs.WORKLOADS[WORKLOAD]["seed"] + rank)
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values of x (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, total_s):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / total_s
+
+
 def config_of(w, world):
     return {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "nnz": w["nnz"], "noise": w["nu"], "lambda": w["lam"],
             "trials": w["trials"], "n_outer": w["n_outer"], "n_steps": w["n_steps"], "dt": w["dt"],
@@ -446,7 +469,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = cs_inputs.workload(WORKLOAD, seed=cs_inputs.WORKLOADS[WORKLOAD]["seed"] + rank)
+    w = replica_workload(rank)
     if args.n_outer:
         w["n_outer"] = args.n_outer
     if args.n_steps:
@@ -499,12 +522,8 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+    value = job_value(world, args.steps, total_s)
 
     # end to end through the C ABI from pinned host buffers
     A_pin = torch.from_numpy(inst.A).pin_memory()
@@ -518,11 +537,7 @@ def main():
         x_e2e, s_e2e, E_e2e, st_e2e, _ = cs.cs_result(h)
         cs.cs_problem_destroy(h)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_s), dist, "cuda")
 
     if rank != 0:
         dist.destroy_process_group()
@@ -556,7 +571,7 @@ def main():
                                      f"(max SM clock, {peak_kind})"),
                      "launch_ms": per_launch_s * 1e3,
                      "flops_per_launch": flops_per_launch},
-        "e2e": {"value": world * len(e2e_s) / e2e_total, "unit": "reconstructions/s",
+        "e2e": {"value": job_value(world, len(e2e_s), e2e_total), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": (inst.A.size + inst.y.size) * 8,
                 "d2h_bytes_per_step": inst.N * 8 + inst.N + 8 + cs.CS_STATS_LEN * 8},
         "gpu_launches": launches,
