@@ -42,6 +42,11 @@ import cs_inputs  # noqa: E402
 
 METRIC = "solved reconstructions/s and Euler spin-steps/s at oracle RMSE; p50/p99 latency; %roofline"
 WORKLOAD = "trials64_n2000_fp32"
+# single-problem workloads the main path also measures (--workload): the FP64
+# N = 200 single trial (latency-bound) and the MRI-shaped N = 16384 FP16 one
+# (G_off streamed from HBM every step)
+SINGLE_WORKLOADS = [WORKLOAD, "single_n200_fp64", "mri_n16384_fp16"]
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -203,10 +208,10 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
-def replica_workload(rank):
+def replica_workload(rank, name=WORKLOAD):
     """The benchmark workload of one replica: the instance seed is offset by the rank,
     so the N replicas solve N independent problems (no data exchange between ranks)."""
-    return cs_inputs.workload(WORKLOAD, seed=cs_inputs.WORKLOADS[WORKLOAD]["seed"] + rank)
+    return cs_inputs.workload(name, seed=cs_inputs.WORKLOADS[name]["seed"] + rank)
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -225,11 +230,12 @@ def job_value(world, units_per_rank, total_s):
     return world * units_per_rank / total_s
 
 
-def config_of(w, world):
-    return {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "nnz": w["nnz"], "noise": w["nu"], "lambda": w["lam"],
+def config_of(w, world, name=WORKLOAD):
+    return {"workload": name, "N": w["N"], "M": w["M"], "nnz": w["nnz"], "noise": w["nu"], "lambda": w["lam"],
             "trials": w["trials"], "n_outer": w["n_outer"], "n_steps": w["n_steps"], "dt": w["dt"],
             "field": w["field"], "precision": w["precision"], "refit": w["refit"],
-            "parallelism": f"replicas{world}" if world > 1 else "single", "work_split": "autotuned",
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "work_split": "cost model" if name == "mri_n16384_fp16" else "autotuned",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
 
 
@@ -440,7 +446,7 @@ def main():
                     help="override the workload's outer iterations (short runs for profiling only)")
     ap.add_argument("--n-steps", type=int, default=None,
                     help="override the workload's Euler steps per run (short runs for profiling only)")
-    ap.add_argument("--workload", choices=[WORKLOAD, "batch_uneven_bf16", "serve_mix"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=SINGLE_WORKLOADS + ["batch_uneven_bf16", "serve_mix"], default=WORKLOAD)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 does not meet the timing rules", file=sys.stderr)
@@ -469,13 +475,16 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = replica_workload(rank)
+    name = args.workload
+    w = replica_workload(rank, name)
     if args.n_outer:
         w["n_outer"] = args.n_outer
     if args.n_steps:
         w["n_steps"] = args.n_steps
     inst = cs_inputs.workload_instance(w)
-    prm = cs.params_from_workload(w, autotune=1)  # work split timed on this GPU during the warm-up
+    # work split timed on this GPU during the warm-up (the MRI-shaped problem keeps
+    # the cost model's streamed split: its tuning runs would take seconds)
+    prm = cs.params_from_workload(w, autotune=0 if name == "mri_n16384_fp16" else 1)
     T = w["trials"]
     stream = torch.cuda.Stream()
     A_dev = torch.from_numpy(inst.A).cuda()
@@ -549,28 +558,47 @@ def main():
     n_launch_euler = args.steps * w["n_outer"]
     per_launch_s = euler_ms / 1e3 / n_launch_euler
     flops_per_launch = 2.0 * w["N"] * (w["N"] - 1) * T * w["n_steps"]
-    achieved = flops_per_launch / per_launch_s / 1e12
-    peak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    traffic = recorded_traffic()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if name == "mri_n16384_fp16":
+        # every step streams the stored G_off (Npad x Npad FP16) from HBM
+        npad = (w["N"] + 31) // 32 * 32
+        bytes_per_launch = float(npad) * npad * 2 * w["n_steps"]
+        roof = {"kernel": "euler_kernel<__half, float, MR, STREAM=true, WIDE=true> (FP16 G_off streamed)",
+                "bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9,
+                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                "peak_source": f"HBM copy bandwidth ({peak_kind})", "bytes_per_launch": bytes_per_launch,
+                "bytes_note": "full stored matrix; the symmetric minimum is N(N-1)/2 x 2 B per step",
+                "traffic": None}
+    elif name == "single_n200_fp64":
+        roof = {"kernel": "euler_kernel<double, double, MR, STREAM=false, WIDE=false> (FP64, latency-bound)",
+                "bound": "alu", "achieved": flops_per_launch / per_launch_s / 1e12,
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "GB300 FP64 nominal; a 1000-step dependent chain of 200 x 200 products: "
+                               "the step latency is the figure of merit",
+                "us_per_step": per_launch_s * 1e6 / w["n_steps"], "flops_per_launch": flops_per_launch,
+                "traffic": None}
+    else:
+        roof = {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true> "
+                          "(FP32 G_off resident on chip, packed FMAs)",
+                "bound": "alu", "achieved": flops_per_launch / per_launch_s / 1e12,
+                "peak": fp32_simt_peak_tflops(sm_mhz), "unit": "TFLOP/s",
+                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz} MHz (max SM clock, {peak_kind})",
+                "flops_per_launch": flops_per_launch, "traffic": recorded_traffic()}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["launch_ms"] = per_launch_s * 1e3
     ms_sorted = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(w, world),
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"single_n200_fp64": "f64", "mri_n16384_fp16": "f16 storage, f32 compute"}.get(name, "f32"),
+        "data": "synthetic", "config": config_of(w, world, name),
         "spin_steps_per_s": world * w["N"] * T * w["n_outer"] * w["n_steps"] / (total_s / args.steps),
         "latency_ms": {"p50": ms_sorted[len(ms_sorted) // 2],
                        "p99": ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]},
         "quality": {"rmse": oracle.rmse(x_hat, inst.x0), "hamming": oracle.hamming_loss(sigma_hat, inst.xi),
                     "energy": energy, "support": int(stats[1])},
-        "roofline": {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true> "
-                               "(FP32 G_off resident on chip, packed FMAs)",
-                     "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": (f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                     f"(max SM clock, {peak_kind})"),
-                     "launch_ms": per_launch_s * 1e3,
-                     "flops_per_launch": flops_per_launch},
+        "roofline": roof,
         "e2e": {"value": job_value(world, len(e2e_s), e2e_total), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": (inst.A.size + inst.y.size) * 8,
                 "d2h_bytes_per_step": inst.N * 8 + inst.N + 8 + cs.CS_STATS_LEN * 8},

@@ -74,11 +74,18 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide) {
 //  * narrow split (every other case; measured at about 45% of FFMA issue):
 //    FMAs at 128 per clock / 0.45, or streamed G bytes;
 // each plus X bytes at 44 per clock (measured: the X traffic of a step adds to
-// its time rather than overlapping the product) and a fixed cost per cluster
-// rank for the reduction through distributed shared memory.
+// its time rather than overlapping the product), a fixed cost per cluster rank
+// for the reduction through distributed shared memory, and the step barrier: a
+// grid barrier (about 1.8 us measured) or, for a single cluster, the hardware
+// cluster barrier.  FP64 FMAs count at 1/64 of the FP32 rate (GB300 issues
+// about 2 FP64 FMAs per clock per SM, measured).  For the autotuner, besides
+// the largest number of clusters that fits, a single cluster is offered too:
+// for small problems it is sometimes the fastest split (N = 200 FP32, one
+// trial: 2.8 us per step against 3.4) and sometimes far from it (16 trials:
+// 5.9 against 3.6), beyond what this model resolves.
 template <typename GT, typename CT>
 cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out,
-                      std::vector<std::pair<double, Plan>>* cands = nullptr) {
+                      std::vector<std::pair<double, Plan>>* cands = nullptr, bool single_cluster = false) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
   const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
   const int twmax = round4(std::min(T, kTChunk));
@@ -126,7 +133,11 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         pl.ldg = (wide && pl.kq % 2 == 0) ? (pl.kq + 1) * 4 : pl.kq * 4;
         const int WR = wide ? kConsumerWarps / WK : WRn;
         const int CGw = twmax / 4, RGw = wide ? 32 / CGw : 1;
+        // the largest number of clusters that fits, and a single cluster (whose
+        // steps need only the hardware cluster barrier) when that differs
+        bool took_largest = false;
         for (int NC = std::min(sms / C, N); NC >= 1; --NC) {
+          if (took_largest && NC != 1) continue;
           pl.RPC = (N + NC - 1) / NC;
           pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
           if (pl.NC != NC && NC != std::min(sms / C, N)) continue;
@@ -162,7 +173,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
             if (pl.smem <= cap) { pl.slots = slots; break; }
           }
-          if (pl.slots == 0) break;
+          if (pl.slots == 0) break;  // fewer clusters only need more shared memory
           e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
           if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"; return e; }
           e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -184,7 +195,9 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             maxc = 0;
           }
           if (pl.NC > maxc) continue;
-          const double fma = (double)pl.RPC_pad * pl.kq * 4 * T;
+          // FP64 FMAs issue at a small fraction of the FP32 rate on this GPU
+          const double frate = std::is_same<CT, double>::value ? 2.0 : 128.0;
+          const double fma = (double)pl.RPC_pad * pl.kq * 4 * T * (128.0 / frate);
           const double xbytes = (double)pl.kq * 4 * twmax * sizeof(CT) * nblk;
           const double gbytes = stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) : 0.0;
           double cost;
@@ -197,13 +210,17 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             cost = std::max(fma / 128.0 / 0.45, gbytes / 22.0) + xbytes / 44.0;
           }
           cost += 300.0 * C;
+          // per-step barrier: a grid barrier (about 1.8 us measured), or the
+          // hardware cluster barrier when the grid is one cluster
+          cost += pl.NC > 1 ? 3700.0 : 600.0;
           if (cands) cands->emplace_back(cost, pl);
           if (!found || cost < best_cost) {
             best_cost = cost;
             bp = pl;
             found = true;
           }
-          break;
+          if (took_largest || pl.NC == 1 || !single_cluster) break;
+          took_largest = true;
         }
       }
     }
@@ -370,7 +387,8 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   }
   if (!hit) {
     std::vector<std::pair<double, Plan>> cands;
-    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl, &cands);
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl, &cands,
+                                      prm.autotune != 0);
     if (e != cudaSuccess) return e;
     if (prm.autotune && cands.size() > 1) {
       e = autotune_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands, &pl);
