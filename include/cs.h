@@ -112,6 +112,11 @@ cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t
 /* Queue one full solve (Algorithm 1, every outer iteration) of `trials`
  * independent trials on the problem's stream; returns without waiting.
  * Trial t draws its initial amplitudes from key (seed, instance, t, outer).
+ * The exact refit returns the FP64 least-squares solution on the support: an
+ * FP32 Cholesky factor (in shared memory, or blocked in global memory for
+ * large supports) with FP64 iterative refinement, else an FP64 Cholesky, with
+ * the ridge for numerically singular G_SS (CS_ESINGULAR).  With autotune = 1
+ * the first solve of a shape synchronises the stream while it times splits.
  * Errors: CS_EINVAL for bad parameters or trials < 1; CS_ENOMEM; CS_ECUDA. */
 cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
 
@@ -123,7 +128,8 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
  * (problem, trial).  All outer iterations and the objective are captured
  * into one CUDA graph, submitted to the problems' stream as a single launch.
  * Problem i draws its initial amplitudes with instance number i.  All problems
- * must have been created on the same device and stream.  Results are read per problem with cs_result / cs_result_trials.
+ * must have been created on the same device and stream.  Results are read per
+ * problem with cs_result / cs_result_trials.
  * Errors: CS_EINVAL (parameters, trials > 64, record_steps != 0, mixed
  * streams), CS_ENOMEM, CS_ECUDA. */
 cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials);
@@ -198,8 +204,9 @@ void cs_problem_destroy(cs_problem* p);
  * A server owns `max_slots` CUDA streams on the current device and a worker
  * thread.  Each request gets an Euler grid sized to its work (unless
  * params.max_ctas is set): one CTA per 26e6 coupling FMAs per step (N^2 x
- * trials) and per 150 KB of G_off in its storage precision, at least 2; a request that would take more than half the SMs takes
- * all but SMs / 16 of them, which stay for small requests.  Submitted requests
+ * trials) and per 150 KB of G_off in its storage precision, at least 2; a
+ * request that would take more than half the SMs takes all but SMs / 16 of
+ * them, which stay for small requests.  Submitted requests
  * are scanned in arrival order; each is admitted when a slot is free, its
  * device-memory estimate fits what is left of `hbm_budget_bytes` and its grid
  * fits the SMs not held by running requests (a request that does not fit yet

@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
   const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT), a.tps);
   unsigned char* ring = smem_raw;
   CT* P = reinterpret_cast<CT*>(smem_raw + (size_t)a.slots * slot);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + b_part_bytes(a.twp, sizeof(CT), PAIR));
+  uint64_t* full =
+      reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + b_part_bytes(a.twp, sizeof(CT), PAIR));
   uint64_t* empty = full + a.slots;
   __shared__ int s_next;
   if (threadIdx.x == 0) {
@@ -536,7 +537,9 @@ cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-size_t batch_inst_bytes() { return sizeof(BInst<double>) > sizeof(BInst<float>) ? sizeof(BInst<double>) : sizeof(BInst<float>); }
+size_t batch_inst_bytes() {
+  return sizeof(BInst<double>) > sizeof(BInst<float>) ? sizeof(BInst<double>) : sizeof(BInst<float>);
+}
 
 int64_t tiled_elems(int64_t N, int64_t Npad) {
   const int64_t nrt = (N + kRT - 1) / kRT;
