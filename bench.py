@@ -183,6 +183,23 @@ def oracle_sample(w, target_s=12.0, min_steps=10):
             "spin_steps_per_s": w["N"] * w["trials"] / per_step, "seconds": t}
 
 
+def oracle_sample_single_thread(name, target_s=6.0):
+    """oracle_sample on one host core: a child process with every BLAS thread pool
+    limited to one thread (the pools are sized when NumPy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_sample(bench.replica_workload(0, %r), target_s=%r); r.pop('seconds', None); "
+            "print(json.dumps(r))" % (ROOT, name, target_s))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        r["cores"] = 1
+        r["sample"] = r["sample"].replace("BLAS on all host cores", "BLAS on one core")
+        return r
+    except Exception as exc:  # reported, never fatal to the GPU measurement
+        return {"unavailable": str(exc)[:200]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -609,6 +626,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(w)
         cb.pop("seconds", None)
+        cb["single_thread"] = oracle_sample_single_thread(name)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if dist:
