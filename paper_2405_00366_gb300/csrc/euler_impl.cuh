@@ -76,13 +76,12 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide) {
 // each plus X bytes at 44 per clock (measured: the X traffic of a step adds to
 // its time rather than overlapping the product), a fixed cost per cluster rank
 // for the reduction through distributed shared memory, and the step barrier: a
-// grid barrier (about 1.8 us measured) or, for a single cluster, the hardware
-// cluster barrier.  FP64 FMAs count at 1/64 of the FP32 rate (GB300 issues
-// about 2 FP64 FMAs per clock per SM, measured).  For the autotuner, besides
-// the largest number of clusters that fits, a single cluster is offered too:
-// for small problems it is sometimes the fastest split (N = 200 FP32, one
-// trial: 2.8 us per step against 3.4) and sometimes far from it (16 trials:
-// 5.9 against 3.6), beyond what this model resolves.
+// grid barrier (about 1.8 us measured; cheaper when the grid is a single
+// cluster).  FP64 FMAs count at 1/64 of the FP32 rate (GB300 issues about 2
+// FP64 FMAs per clock per SM, measured).  For the autotuner, besides the
+// largest number of clusters that fits, a single cluster is offered too: for
+// small problems it can be the fastest split and can be far from it, beyond
+// what this model resolves.
 template <typename GT, typename CT>
 cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out,
                       std::vector<std::pair<double, Plan>>* cands = nullptr, bool single_cluster = false) {
@@ -210,9 +209,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             cost = std::max(fma / 128.0 / 0.45, gbytes / 22.0) + xbytes / 44.0;
           }
           cost += 300.0 * C;
-          // per-step barrier: a grid barrier (about 1.8 us measured), or the
-          // hardware cluster barrier when the grid is one cluster
-          cost += pl.NC > 1 ? 3700.0 : 600.0;
+          // per-step grid barrier (about 1.8 us measured; less for one cluster)
+          cost += pl.NC > 1 ? 3700.0 : 1200.0;
           if (cands) cands->emplace_back(cost, pl);
           if (!found || cost < best_cost) {
             best_cost = cost;

@@ -404,19 +404,6 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
   fence_proxy_async_shared();
 }
 
-// Barrier between Euler steps: the grid barrier, or, when the whole grid is one
-// cluster, the hardware cluster barrier (release/acquire at cluster scope; the
-// writers' proxy fence before it orders their X for the bulk copies that
-// follow).  The test hook of phantom CTAs always takes the grid barrier.
-__device__ __forceinline__ bool step_barrier(cg::cluster_group& cluster, unsigned* bar, unsigned k, int* err,
-                                             long long timeout_cycles, unsigned phantom, int C) {
-  if (phantom == 0 && (int)gridDim.x == C) {
-    cluster.sync();
-    return ld_volatile(err) == 0;
-  }
-  return grid_barrier(bar, k, err, timeout_cycles, phantom);
-}
-
 // One block of trials: this CTA's partial products in P (rows < nrows).
 template <typename GT, typename CT, int MR, bool STREAM, bool WIDE>
 __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
@@ -514,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       a.X0[xblock(t0, Npad) + xoff<WIDE>(row0 + own0 + r, t - t0, twp)] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
     }
     fence_proxy_async_global();
-    if (!step_barrier(cluster, a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom, C)) { cluster.sync(); return; }
+    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
       block_partials<GT, CT, MR, STREAM, WIDE>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
@@ -549,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
   }
   fence_proxy_async_global();
-  if (!step_barrier(cluster, a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom, C)) { cluster.sync(); return; }
+  if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
 
   // ---- Euler steps
   const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
@@ -593,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     if (last) break;
     // the next X is read by bulk copies (async proxy) of every CTA after the barrier
     fence_proxy_async_global();
-    if (!step_barrier(cluster, a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom, C)) break;
+    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) break;
     CT* tmp = Xc; Xc = Xn; Xn = tmp;
   }
   cluster.sync();  // peers may still read this CTA's partials
