@@ -324,6 +324,23 @@ def run_batch(args):
             plain_rmse.append(oracle.rmse(x, inst.x0))
     t_b = statistics.median(times)
     rmse_b = [oracle.rmse(r[0], i.x0) for r, i in zip(res, insts)]
+    # roofline of the whole batched solve (Euler steps dominate): FP32 FMAs of the
+    # coupling products against the FP32 FMA peak, and the G_off bytes streamed
+    # (stored tiles, BF16, every step of every instance) against the HBM copy rate
+    peaks, peak_kind = measured_peaks()
+    steps_all = prm_b.n_outer * prm_b.n_steps
+    flops = sum(2.0 * i.N * (i.N - 1) * T for i in insts) * steps_all
+    gbytes = sum(((i.N + 127) // 128 * 128) * ((i.N + 31) // 32 * 32) * 2.0 for i in insts) * steps_all
+    tflops = flops / t_b / 1e12
+    gbs = gbytes / t_b / 1e9
+    fpeak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    hpeak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = gbs / hpeak > tflops / fpeak
+    roof = {"kernel": "euler_batch_kernel<__nv_bfloat16, float, 8, PAIR=true>", "bound": "hbm" if hbm else "alu",
+            "achieved": gbs if hbm else tflops, "peak": hpeak if hbm else fpeak,
+            "unit": "GB/s" if hbm else "TFLOP/s", "frac": max(gbs / hpeak, tflops / fpeak),
+            "alu_frac": tflops / fpeak, "hbm_frac": gbs / hpeak, "traffic": None,
+            "peak_source": f"FP32 FMA peak and HBM copy bandwidth ({peak_kind})"}
     v_b = len(insts) / t_b
     v_p = b["n_plain"] / plain_s
     Ns = [i.N for i in insts]
@@ -343,6 +360,7 @@ def run_batch(args):
                        "sample": f"first {b['n_plain']} instances solved one at a time (cs_solve, FP32), "
                                  f"{plain_s:.1f} s"},
         "ratio_vs_plain_fp32": v_b / v_p,
+        "roofline": roof,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
