@@ -43,9 +43,14 @@ Readings where the paper is silent (each one is listed in the design doc):
 
 Pins: tests/test_oracle_pins.py checks this module against the brute-force
 minimum over all supports, exact noise-free recovery, the separable case
-A orthogonal (hard threshold), a hand-computed three-spin Euler step, the
-symmetry and zero diagonal of J, the published SplitMix64 outputs, the
-recomputed objective and the zero gradient of the refit.
+A orthogonal (hard threshold, both fields), a hand-computed three-spin Euler
+step, the symmetry and zero diagonal of J, the published SplitMix64 outputs,
+the moments of the initial-amplitude distributions, the pump and eta
+schedules at closed-form points, the Gram matrix by brute force, the
+recomputed objective, the zero gradient of the exact refit, the ridge on a
+singular support, and the damped Jacobi refit converging to the exact one;
+tests/test_oracle_mutations.py plants mistakes in it and checks that a pin
+fails for each.
 """
 from __future__ import annotations
 
