@@ -278,7 +278,7 @@ def run_batch(args):
 
     if not os.path.exists(cs.LIB_PATH):
         build.build()
-    b = BATCH
+    b = dict(BATCH, n_inst=args.batch_instances or BATCH["n_inst"])
     insts = cs_inputs.uneven_batch(b["n_inst"], b["n_min"], b["n_max"], b["alphas"], b["sparsities"], b["nu"],
                                    b["lam"], seed=b["seed"])
     T = b["trials"]
@@ -482,6 +482,8 @@ def main():
     ap.add_argument("--n-steps", type=int, default=None,
                     help="override the workload's Euler steps per run (short runs for profiling only)")
     ap.add_argument("--workload", choices=SINGLE_WORKLOADS + ["batch_uneven_bf16", "serve_mix"], default=WORKLOAD)
+    ap.add_argument("--batch-instances", type=int, default=None,
+                    help="instances of the batched workload (smaller batches for profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 does not meet the timing rules", file=sys.stderr)

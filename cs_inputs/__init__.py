@@ -117,7 +117,7 @@ WORKLOADS = {
     # 128 x 128 Haar-sparse image through a subsampled 2-D DCT (N=16384, M=4915),
     # 8 trials, FP16 storage; K = 0.1 as in the paper's MRI runs
     "mri_n16384_fp16": dict(
-        mri_side=128, N=16384, M=4915, nnz=1638, nu=0.0, lam=0.01, seed=0, trials=8,
+        mri_side=128, N=16384, M=4915, nnz=1638, nu=0.0, lam=0.1, seed=0, trials=8,
         n_outer=40, n_steps=3000, precision="fp16", **dict(_COMMON, K=0.1)),
 }
 

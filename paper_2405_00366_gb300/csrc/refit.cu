@@ -337,10 +337,11 @@ __device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, doubl
   double* x;
   const size_t packed = (size_t)n * (n + 1) / 2;
   bool done = false;
-  if ((packed + (size_t)n) * sizeof(float) <= smem_bytes) {
+  // a support larger than M makes G_SS singular: straight to the FP64 ridge path
+  if (n <= J.M && (packed + (size_t)n) * sizeof(float) <= smem_bytes) {
     x = W;
     done = solve_mixed(J, idx, n, smem, smem + packed, W, W + n);
-  } else if (smem_bytes >= kBlockedSmem) {
+  } else if (n <= J.M && smem_bytes >= kBlockedSmem) {
     x = W;
     done = solve_mixed_blocked(J, idx, n, W, smem);
   }
