@@ -121,7 +121,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         pl.WK = wide ? WK : 1;
         if (stream) {
           pl.kq = ((nq + C - 1) / C + 7) / 8 * 8;  // whole 32-column tiles per rank
-          pl.kch = kStreamK;
+          pl.kch = kStreamK;  // per slot; widened below to as many tiles as the ring allows
         } else {
           pl.kq = (nq + C - 1) / C;
           // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
@@ -162,15 +162,22 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
           const size_t cap = (size_t)optin - fa.sharedSizeBytes;
           const size_t gblock = stream ? 0 : (size_t)pl.RPC_pad * pl.ldg * sizeof(GT);
-          const size_t gtile = stream ? (size_t)pl.RPC_pad * kStreamK * sizeof(GT) : 0;
           const size_t kpart = wide ? (size_t)WK * pl.RPC_pad * twmax * sizeof(float) : 0;
-          pl.xoff = align128(gtile);
-          pl.slot_bytes = align128(pl.xoff + (size_t)pl.kch * twmax * sizeof(CT));
+          // streamed plans: the most G_off tiles per slot (4, 2, 1) that leave 3
+          // slots (measured: one tile per slot keeps too few bytes in flight)
           pl.slots = 0;
-          for (int slots = 8; slots >= (stream ? 2 : 3); --slots) {
-            if ((size_t)slots * pl.slot_bytes < kpart) break;  // the ring holds the k-warp partials
-            pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
-            if (pl.smem <= cap) { pl.slots = slots; break; }
+          for (int tps = stream ? 4 : 1; tps >= 1 && pl.slots == 0; tps >>= 1) {
+            if (stream && (size_t)tps * kStreamK > (size_t)pl.kq * 4) continue;
+            if (stream) pl.kch = kStreamK * tps;
+            const size_t gtile = stream ? (size_t)tps * pl.RPC_pad * kStreamK * sizeof(GT) : 0;
+            pl.xoff = align128(gtile);
+            pl.slot_bytes = align128(pl.xoff + (size_t)pl.kch * twmax * sizeof(CT));
+            const int min_slots = (stream && tps > 1) ? 3 : (stream ? 2 : 3);
+            for (int slots = 8; slots >= min_slots; --slots) {
+              if ((size_t)slots * pl.slot_bytes < kpart) break;  // the ring holds the k-warp partials
+              pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
+              if (pl.smem <= cap) { pl.slots = slots; break; }
+            }
           }
           if (pl.slots == 0) break;  // fewer clusters only need more shared memory
           e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
@@ -198,7 +205,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           const double frate = std::is_same<CT, double>::value ? 2.0 : 128.0;
           const double fma = (double)pl.RPC_pad * pl.kq * 4 * T * (128.0 / frate);
           const double xbytes = (double)pl.kq * 4 * twmax * sizeof(CT) * nblk;
-          const double gbytes = stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) : 0.0;
+          // streamed G_off bytes, weighted up when a slot carries fewer than 4 tiles
+          // (fewer bytes in flight per SM)
+          const double gbytes =
+              stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) * std::max(1.0, 128.0 / pl.kch) : 0.0;
           double cost;
           if (wide) {
             const double ffma2 = fma / 64.0;  // packed FMA warp instructions

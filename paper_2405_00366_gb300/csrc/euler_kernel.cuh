@@ -131,7 +131,8 @@ __host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t
 // Streamed G_off tiles of a cluster plan: tile (cluster c, k tile kc) holds rows
 // [c RPC, c RPC + RPC_pad) (zero past the cluster's rows and past N) and
 // columns [32 kc, 32 kc + 32), contiguous, with the quad q of row r at
-// q ^ (r & 7) so that the row groups of a warp read distinct banks.
+// q ^ (r & 7) so that the row groups of a warp read distinct banks.  A ring
+// slot carries kch / 32 consecutive tiles of one cluster (one bulk copy).
 constexpr int kStreamK = 32;
 
 template <typename GT>
@@ -176,7 +177,8 @@ __device__ __forceinline__ void produce_chunks(const EulerArgs<CT>& a, const CT*
       const unsigned bytes = (unsigned)((size_t)kr * twp * sizeof(CT));
       unsigned char* slot = ring + (size_t)s * a.slot_bytes;
       if constexpr (STREAM) {
-        const unsigned gtb = (unsigned)((size_t)a.RPC_pad * kStreamK * sizeof(GT));
+        // kr / 32 consecutive tiles of this cluster's G_off (contiguous in memory)
+        const unsigned gtb = (unsigned)((size_t)(kr / kStreamK) * a.RPC_pad * kStreamK * sizeof(GT));
         const size_t kc = (size_t)(k0 + ci * a.kch) / kStreamK;
         const GT* src = reinterpret_cast<const GT*>(a.Gt2) + ((size_t)cl * a.nkct + kc) * a.RPC_pad * kStreamK;
         mbar_arrive_expect_tx(full + s, gtb + bytes);
@@ -251,8 +253,10 @@ __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const G
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
           if constexpr (STREAM) {
-            const int r = rbase + RG * i;
-            load4<CT, GT>(gk + (size_t)(RG * i) * kStreamK + 4 * ((kk >> 2) ^ (r & 7)), gv[i]);
+            const int r = rbase + RG * i, q = kk >> 2;  // tile q / 8 of the chunk, quad q % 8 of the tile
+            load4<CT, GT>(gk + (size_t)(q >> 3) * a.RPC_pad * kStreamK + (size_t)(RG * i) * kStreamK +
+                              4 * ((q & 7) ^ (r & 7)),
+                          gv[i]);
           } else {
             load4<CT, GT>(gk + (size_t)(RG * i) * ldg + kk, gv[i]);
           }
@@ -343,8 +347,9 @@ __device__ __forceinline__ void wide_partials(const EulerArgs<float>& a, const G
         ulonglong2 gp[MR];
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
-          if constexpr (STREAM) {
-            gp[i] = load_gpairs<GT>(gk + (size_t)(RG * i) * kStreamK + 4 * (q ^ ((rbase + RG * i) & 7)));
+          if constexpr (STREAM) {  // tile q / 8 of the chunk, quad q % 8 of the tile
+            gp[i] = load_gpairs<GT>(gk + (size_t)(q >> 3) * a.RPC_pad * kStreamK + (size_t)(RG * i) * kStreamK +
+                                    4 * ((q & 7) ^ ((rbase + RG * i) & 7)));
           } else {
             gp[i] = load_gpairs<GT>(gk + (size_t)(RG * i) * a.ldg + 4 * q);
           }
