@@ -25,7 +25,7 @@ CS_REFIT_EXACT, CS_REFIT_JACOBI = 0, 1
 CS_PUMP_LINEAR, CS_PUMP_SIGMOID = 0, 1
 CS_INIT_UNIFORM, CS_INIT_NORMAL = 0, 1
 CS_P_FP64, CS_P_FP32, CS_P_BF16, CS_P_FP16, CS_P_FP8 = 0, 1, 2, 3, 4
-CS_STATS_LEN = 10
+CS_STATS_LEN = 11
 
 PRECISIONS = {"fp64": CS_P_FP64, "fp32": CS_P_FP32, "bf16": CS_P_BF16, "fp16": CS_P_FP16, "fp8": CS_P_FP8}
 FIELDS = {"cn": CS_FIELD_CN, "bn": CS_FIELD_BN}
@@ -48,7 +48,7 @@ class cs_params(ctypes.Structure):
         ("jacobi_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
         ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-        ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32), ("tensor_form", ctypes.c_int32),
     ]
 
 

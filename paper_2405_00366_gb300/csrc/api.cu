@@ -163,6 +163,7 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->stream_g != 0 && p->stream_g != 1) return fail(CS_EINVAL, "stream_g must be 0 or 1");
   if (p->stream_g == 1 && p->precision == CS_P_FP64) return fail(CS_EINVAL, "FP64 G_off is never streamed");
   if (p->autotune != 0 && p->autotune != 1) return fail(CS_EINVAL, "autotune must be 0 or 1");
+  if (p->tensor_form < 0 || p->tensor_form > 2) return fail(CS_EINVAL, "tensor_form must be 0, 1 or 2");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -516,6 +517,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
     ps[i]->S.done = true;
     ps[i]->S.plan_cluster = 0;
     ps[i]->S.plan_ctas = std::min(n, P0.num_sms);
+    ps[i]->S.plan_form = 3;
   }
   return CS_OK;
 }
@@ -528,9 +530,13 @@ static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   CS_CUDA(cudaMemcpy(st, p->S.stats, 8 * sizeof(double), cudaMemcpyDeviceToHost), "copy stats");
   st[8] = p->S.plan_cluster;
   st[9] = p->S.plan_ctas;
+  st[10] = p->S.plan_form;
   if (stats_out) std::memcpy(stats_out, st, sizeof(st));
   const int err = (int)st[3];
   if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a grid barrier timed out");
+  if (err == DEV_RANGE)
+    return fail(CS_ECUDA, "device error word 4: an amplitude left the FP16 range of the tensor-core Euler form "
+                          "(set tensor_form = 1)");
   if (err != 0) return fail(CS_ECUDA, "device error word " + std::to_string(err));
   return st[2] != 0.0 ? CS_ESINGULAR : CS_OK;
 }

@@ -16,24 +16,24 @@ namespace cs {
 namespace {
 struct Plan {
   int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, RG, MR, WK, ldg;
-  bool stream, wide;
+  bool stream, wide, tc;
   size_t smem, slot_bytes, xoff;
 };
 
 template <typename CT>
 using EulerFn = void (*)(EulerArgs<CT>);
 
-template <typename GT, typename CT, bool STREAM, bool WIDE>
+template <typename GT, typename CT, bool STREAM, bool WIDE, bool TC = false>
 EulerFn<CT> kernel_for_s(int MR) {
   switch (MR) {
-    case 1: return euler_kernel<GT, CT, 1, STREAM, WIDE>;
-    case 2: return euler_kernel<GT, CT, 2, STREAM, WIDE>;
-    case 3: return euler_kernel<GT, CT, 3, STREAM, WIDE>;
-    case 4: return euler_kernel<GT, CT, 4, STREAM, WIDE>;
-    case 5: return euler_kernel<GT, CT, 5, STREAM, WIDE>;
-    case 6: return euler_kernel<GT, CT, 6, STREAM, WIDE>;
-    case 7: return euler_kernel<GT, CT, 7, STREAM, WIDE>;
-    default: return euler_kernel<GT, CT, 8, STREAM, WIDE>;
+    case 1: return euler_kernel<GT, CT, 1, STREAM, WIDE, TC>;
+    case 2: return euler_kernel<GT, CT, 2, STREAM, WIDE, TC>;
+    case 3: return euler_kernel<GT, CT, 3, STREAM, WIDE, TC>;
+    case 4: return euler_kernel<GT, CT, 4, STREAM, WIDE, TC>;
+    case 5: return euler_kernel<GT, CT, 5, STREAM, WIDE, TC>;
+    case 6: return euler_kernel<GT, CT, 6, STREAM, WIDE, TC>;
+    case 7: return euler_kernel<GT, CT, 7, STREAM, WIDE, TC>;
+    default: return euler_kernel<GT, CT, 8, STREAM, WIDE, TC>;
   }
 }
 
@@ -42,6 +42,10 @@ EulerFn<CT> kernel_for_s(int MR) {
 // for FP32 compute only.
 template <typename GT> struct streamable { static constexpr bool value = !std::is_same<GT, double>::value; };
 template <typename CT> struct widenable { static constexpr bool value = std::is_same<CT, float>::value; };
+// The tensor-core form: streamed FP16 / BF16 G_off with FP32 compute.
+template <typename GT, typename CT> struct tensorable {
+  static constexpr bool value = tc_type<GT>::value && std::is_same<CT, float>::value;
+};
 
 template <typename GT, typename CT, bool WIDE>
 EulerFn<CT> kernel_for_w(int MR, bool stream) {
@@ -52,7 +56,10 @@ EulerFn<CT> kernel_for_w(int MR, bool stream) {
 }
 
 template <typename GT, typename CT>
-EulerFn<CT> kernel_for(int MR, bool stream, bool wide) {
+EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
+  if constexpr (tensorable<GT, CT>::value) {
+    if (tc) return kernel_for_s<GT, CT, true, true, true>(MR);
+  }
   if constexpr (widenable<CT>::value) {
     if (wide) return kernel_for_w<GT, CT, true>(MR, stream);
   }
@@ -83,7 +90,7 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide) {
 // small problems it can be the fastest split and can be far from it, beyond
 // what this model resolves.
 template <typename GT, typename CT>
-cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, Plan* out,
+cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, int tensor_form, Plan* out,
                       std::vector<std::pair<double, Plan>>* cands = nullptr, bool single_cluster = false) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
   const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
@@ -100,6 +107,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   // power of two (lane column groups)
   const bool wide_ok = widenable<CT>::value && (twmax == 8 || twmax == 16 || twmax == 32 || twmax == 64) &&
                        (T <= kTChunk || T % kTChunk == 0);
+  // the tensor-core form: one block of exactly eight trials
+  const bool tc_ok = tensorable<GT, CT>::value && tensor_form != 1 && T == 8;
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -110,14 +119,20 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
     for (int C : csizes) {
       if (hint > 0 && C != hint) continue;
       if (C > nq || sms < C) continue;
-      // variants: wide with WK = 1, 2, 4, 8 k-warps, then narrow (WK = 0)
-      for (int WK : {1, 2, 4, 8, 0}) {
+      // variants: wide with WK = 1, 2, 4, 8 k-warps, narrow (WK = 0), and
+      // (streamed) the tensor-core form with WK = 1, 2, 4, 8 (v >= 5)
+      for (int v = 0; v < 9; ++v) {
+        const bool tc = v >= 5;
+        const int WK = tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0);
         const bool wide = WK > 0;
         if (wide && !wide_ok) continue;
+        if (tc && !(stream && tc_ok)) continue;
+        if (!tc && tensor_form == 2) continue;
         Plan pl{};
         pl.C = C;
         pl.stream = stream;
         pl.wide = wide;
+        pl.tc = tc;
         pl.WK = wide ? WK : 1;
         if (stream) {
           pl.kq = ((nq + C - 1) / C + 7) / 8 * 8;  // whole 32-column tiles per rank
@@ -131,7 +146,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         // reads start in different banks
         pl.ldg = (wide && pl.kq % 2 == 0) ? (pl.kq + 1) * 4 : pl.kq * 4;
         const int WR = wide ? kConsumerWarps / WK : WRn;
-        const int CGw = twmax / 4, RGw = wide ? 32 / CGw : 1;
+        // rows per lane group: the wide split's row groups, or 16-row MMA tiles
+        const int CGw = twmax / 4, RGw = tc ? 16 : (wide ? 32 / CGw : 1);
         // the largest number of clusters that fits, and a single cluster (whose
         // steps need only the hardware cluster barrier) when that differs
         bool took_largest = false;
@@ -156,7 +172,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           pl.RW = pl.RG * pl.MR;
           pl.RPC_pad = WR * pl.RW;
           pl.ORW = (pl.RPC + C - 1) / C;
-          EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, stream, wide);
+          EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, stream, wide, tc);
           cudaFuncAttributes fa;
           e = cudaFuncGetAttributes(&fa, fn);
           if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
@@ -210,7 +226,13 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           const double gbytes =
               stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) * std::max(1.0, 128.0 / pl.kch) : 0.0;
           double cost;
-          if (wide) {
+          if (tc) {
+            // MMAs (two per 16 x 16 tile of G_off: the two parts of X), taken at
+            // one per two clocks per SM, overlap the streamed bytes
+            const double mmas = (double)pl.RPC_pad / 16.0 * pl.kq * 4 / 16.0 * 2.0;
+            const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
+            cost = std::max(mmas * 2.0, gbytes / 22.0) + xbytes / 44.0 + red;
+          } else if (wide) {
             const double ffma2 = fma / 64.0;  // packed FMA warp instructions
             const double wf = ffma2 * (8.0 + 2.0 * pl.MR) / (8.0 * pl.MR);
             const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
@@ -245,7 +267,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
 // Streamed G_off tiles for a plan, rebuilt when the precision or split changes.
 template <typename GT>
 cudaError_t ensure_cluster_tiles(ProblemDev& P, int precision, const Plan& pl) {
-  if (P.Gt2 && P.gt2_prec == precision && P.gt2_rpc == pl.RPC && P.gt2_rpcpad == pl.RPC_pad && P.gt2_nc == pl.NC)
+  if (P.Gt2 && P.gt2_prec == precision && P.gt2_rpc == pl.RPC && P.gt2_rpcpad == pl.RPC_pad && P.gt2_nc == pl.NC &&
+      P.gt2_frag == (int)pl.tc)
     return cudaSuccess;
   if (P.Gt2) { dev_free(P.Gt2, P.stream); P.Gt2 = nullptr; P.gt2_prec = -1; }
   if (row_scaled<GT>::value) {
@@ -257,13 +280,14 @@ cudaError_t ensure_cluster_tiles(ProblemDev& P, int precision, const Plan& pl) {
   cudaError_t e = dev_alloc(&P.Gt2, elems * sizeof(GT), P.stream);
   if (e != cudaSuccess) return e;
   store_cluster_tiles_kernel<GT><<<P.num_sms * 4, 256, 0, P.stream>>>(P.G, (GT*)P.Gt2, (int)P.N, pl.RPC, pl.RPC_pad,
-                                                                        pl.NC, nkct, P.gscale);
+                                                                        pl.NC, nkct, P.gscale, (int)pl.tc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   P.gt2_prec = precision;
   P.gt2_rpc = pl.RPC;
   P.gt2_rpcpad = pl.RPC_pad;
   P.gt2_nc = pl.NC;
+  P.gt2_frag = (int)pl.tc;
   return cudaSuccess;
 }
 
@@ -304,8 +328,9 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
   a.phantom = (unsigned)prm.test_phantom_ctas;
   S.plan_cluster = pl.C;
   S.plan_ctas = pl.C * pl.NC;
+  S.plan_form = pl.tc ? 2 : (pl.wide ? 1 : 0);
 
-  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, pl.stream, pl.wide);
+  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, pl.stream, pl.wide, pl.tc);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(launch)"; return e; }
   e = cudaMemsetAsync(S.bar, 0, sizeof(unsigned), P.stream);
@@ -378,14 +403,16 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   // cache per process (so every thread and every solve of a shape agrees)
   struct Key {
     int64_t N;
-    int T, hint, cap, strm, dev, tune;
+    int T, hint, cap, strm, dev, tune, notc;
     bool operator<(const Key& o) const {
-      return std::tie(N, T, hint, cap, strm, dev, tune) < std::tie(o.N, o.T, o.hint, o.cap, o.strm, o.dev, o.tune);
+      return std::tie(N, T, hint, cap, strm, dev, tune, notc) <
+             std::tie(o.N, o.T, o.hint, o.cap, o.strm, o.dev, o.tune, o.notc);
     }
   };
   static std::mutex mu;
   static std::map<Key, Plan> cache;
-  const Key key{P.N, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g, P.device, prm.autotune};
+  const Key key{P.N, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g, P.device, prm.autotune,
+                prm.tensor_form};
   Plan pl;
   bool hit = false;
   {
@@ -395,7 +422,8 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   }
   if (!hit) {
     std::vector<std::pair<double, Plan>> cands;
-    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1, &pl, &cands,
+    cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1,
+                                      prm.tensor_form, &pl, &cands,
                                       prm.autotune != 0);
     if (e != cudaSuccess) return e;
     if (prm.autotune && cands.size() > 1) {

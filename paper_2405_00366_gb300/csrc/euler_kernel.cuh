@@ -130,22 +130,37 @@ __host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t
 
 // Streamed G_off tiles of a cluster plan: tile (cluster c, k tile kc) holds rows
 // [c RPC, c RPC + RPC_pad) (zero past the cluster's rows and past N) and
-// columns [32 kc, 32 kc + 32), contiguous, with the quad q of row r at
-// q ^ (r & 7) so that the row groups of a warp read distinct banks.  A ring
-// slot carries kch / 32 consecutive tiles of one cluster (one bulk copy).
+// columns [32 kc, 32 kc + 32), contiguous.  A ring slot carries kch / 32
+// consecutive tiles of one cluster (one bulk copy).  Inside a tile:
+//  * FMA forms: row-major with the quad q of row r at q ^ (r & 7), so that the
+//    row groups of a warp read distinct banks;
+//  * tensor-core form (frag = 1): [row tile rt][k half h][lane][8], each
+//    16 x 16 sub-tile (rows 16 rt .., columns 16 h ..) stored as the A operands
+//    of one m16n8k16 MMA, lane by lane (see tc_partials).
 constexpr int kStreamK = 32;
 
 template <typename GT>
 __global__ void store_cluster_tiles_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int RPC,
-                                           int RPC_pad, int NC, int nkct, const float* __restrict__ gscale) {
+                                           int RPC_pad, int NC, int nkct, const float* __restrict__ gscale,
+                                           int frag) {
   const size_t total = (size_t)NC * nkct * RPC_pad * kStreamK;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const size_t tile = idx / ((size_t)RPC_pad * kStreamK);
     const int within = (int)(idx % ((size_t)RPC_pad * kStreamK));
-    const int r = within / kStreamK, kp = within % kStreamK;
     const int c = (int)(tile / nkct), kc = (int)(tile % nkct);
-    const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    int r, k;
+    if (frag) {
+      // lane L = 4 g + i holds rows g, g + 8 and columns 4 i .. 4 i + 3 of the
+      // sub-tile, in the register order of the MMA's A operand (tc_partials)
+      const int sub = within >> 8, L = (within >> 3) & 31, e = within & 7;
+      r = (sub >> 1) * 16 + (L >> 2) + 8 * ((e >> 1) & 1);
+      k = 16 * (sub & 1) + 4 * (L & 3) + 2 * (e >> 2) + (e & 1);
+    } else {
+      r = within / kStreamK;
+      const int kp = within % kStreamK;
+      k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    }
     const int row = c * RPC + r, col = kc * kStreamK + k;
     double v = (r < RPC && row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
     if constexpr (row_scaled<GT>::value) v = (r < RPC && row < N) ? v / gscale[row] : 0.0;
@@ -409,13 +424,149 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
   fence_proxy_async_shared();
 }
 
+// Tensor-core form (streamed FP16 or BF16 G_off, one block of eight trials):
+// the product G_off X of each chunk as m16n8k16 MMAs (mma.sync, FP32
+// accumulation; 16 rows x 8 trials x 16 k per instruction).  The 16-bit A
+// operand is the stored G_off itself, as in the FMA forms.  X, whose B operand
+// must have the same 16-bit type, is carried in two parts,
+//   hi = rn(X),  lo = rn((X - hi) 2^s)   (s = kLoShift<GT>),
+// whose products are accumulated apart and added as hi + 2^-s lo, so the
+// product sees X to about 2 (s + 1) significant bits (22 for FP16, 16 for BF16)
+// rather than the 11 or 8 of one part.  Before the first step X is scaled by a
+// power of two that maps the largest |R| below 1 (so FP16 X stays in range
+// while the amplitudes stay below 6e4) and U is scaled back exactly.
+//
+// Contraction order: the MMA sums k = 2i, 2i + 1 (operand register 0) and
+// 2i + 8, 2i + 9 (register 2) in lane group i; both operands here put the
+// consecutive k 4i .. 4i + 3 there instead, which only renames the summation
+// index, so a lane loads its four k of G_off (per row) and of X (per trial)
+// with one access each.
+// Layouts: G_off tiles as in store_cluster_tiles_kernel (frag = 1); X of the
+// block as [k / 16][part][trial][k % 16] (xput), 512 bytes per 16 k; lane
+// L = 4 g + i of a warp reads, for 16 k, 8 bytes of X (trial g, k 4i .. 4i + 3)
+// per part and 16 bytes of G_off per row tile, and holds the MMA results for
+// rows g, g + 8 and trials 2i, 2i + 1.  The consumer warps form WR row-warps
+// (MR row tiles of 16 each) x WK k-warps (every WK-th 16-k block of a chunk);
+// the k-warps' partials go through the ring as in the wide split.
+template <typename GT> struct tc_type { static constexpr bool value = false; };
+template <> struct tc_type<__half> { static constexpr bool value = true; static constexpr int kLoShift = 11; };
+template <> struct tc_type<__nv_bfloat16> { static constexpr bool value = true; static constexpr int kLoShift = 8; };
+
+template <typename GT>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint4& a, const uint2& b) {
+  if constexpr (std::is_same<GT, __half>::value) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  } else {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  }
+}
+
+template <typename GT, int MR>
+__device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const float* __restrict__ Xblk, int twp,
+                                            int k0, int klen, int cl, unsigned char* ring, uint64_t* full,
+                                            uint64_t* empty, unsigned& gctr) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nch = (klen + a.kch - 1) / a.kch;
+  if (w == kConsumerWarps) {
+    produce_chunks<GT, float, true>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    gctr += nch;
+    return;
+  }
+  const int WK = a.WK, WR = kConsumerWarps / WK;
+  const int wr = w % WR, kw = w / WR;
+  const int rt0 = wr * MR;  // first row tile of this warp
+  const size_t tile_u4 = (size_t)a.RPC_pad * kStreamK * sizeof(GT) / 16;  // 16-byte words per 32-column tile
+  float acc[MR][2][4];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][p][q] = 0.f;
+  bool ok = true;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok) {
+      const unsigned char* slot = ring + (size_t)s * a.slot_bytes;
+      const uint4* gt = reinterpret_cast<const uint4*>(slot) + (size_t)rt0 * 64 + l;
+      const uint2* xt = reinterpret_cast<const uint2*>(slot + a.xoff) + l;
+      const int nkb = min(a.kch, klen - ci * a.kch) >> 4;
+#pragma unroll 1
+      for (int kb = kw; kb < nkb; kb += WK) {
+        const uint2 xh = xt[(size_t)kb * 64];
+        const uint2 xl = xt[(size_t)kb * 64 + 32];
+        // tile kb / 2 of the slot, k half kb % 2, row tiles rt0 ..
+        const uint4* gb = gt + (size_t)(kb >> 1) * tile_u4 + (kb & 1) * 32;
+        uint4 av[MR];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) av[i] = gb[(size_t)i * 64];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          mma16816<GT>(acc[i][0], av[i], xh);
+          mma16816<GT>(acc[i][1], av[i], xl);
+        }
+      }
+    }
+    __syncwarp();
+    if (l == 0) mbar_arrive(empty + s);
+  }
+  gctr += nch;
+  // every consumer warp is done with the ring before it holds partials
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+  float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  const float wlo = 1.0f / (float)(1 << tc_type<GT>::kLoShift);
+  const int gq = l >> 2, c = 2 * (l & 3);
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    const int r = (rt0 + i) * 16 + gq;
+    *reinterpret_cast<float2*>(dst + (size_t)r * twp + c) =
+        make_float2(fmaf(wlo, acc[i][1][0], acc[i][0][0]), fmaf(wlo, acc[i][1][1], acc[i][0][1]));
+    *reinterpret_cast<float2*>(dst + (size_t)(r + 8) * twp + c) =
+        make_float2(fmaf(wlo, acc[i][1][2], acc[i][0][2]), fmaf(wlo, acc[i][1][3], acc[i][0][3]));
+  }
+}
+
+// Store X[k][t] = v of a block of twp trials in the layout the kernel form reads:
+// xoff for the FMA forms; for the tensor-core form the hi and lo parts at
+// [k / 16][part][t][k % 16].  An X that overflows FP16 (amplitude beyond the
+// range after the scale) sets DEV_RANGE.
+template <typename GT, typename CT, bool WIDE, bool TC>
+__device__ __forceinline__ void xput(CT* Xb, int k, int t, int twp, CT v, int* err) {
+  if constexpr (TC) {
+    GT* h = reinterpret_cast<GT*>(Xb);
+    const size_t o = ((size_t)(k >> 4) * 2 * twp + t) * 16 + (k & 15);
+    const GT hi = GT(v);
+    const float hf = float(hi);
+    if (isinf(hf) && isfinite(v)) set_error(err, DEV_RANGE);
+    h[o] = hi;
+    h[o + (size_t)twp * 16] = GT((v - hf) * (float)(1 << tc_type<GT>::kLoShift));
+  } else {
+    Xb[xoff<WIDE>(k, t, twp)] = v;
+  }
+}
+
 // One block of trials: this CTA's partial products in P (rows < nrows).
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE>
+template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC>
 __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
                                                int cl, unsigned char* ring, CT* P, uint64_t* full, uint64_t* empty,
                                                unsigned& gctr) {
-  if constexpr (WIDE) {
+  if constexpr (TC) {
+    tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    sum_k_warps(a, ring, P, twp, nrows);
+  } else if constexpr (WIDE) {
     wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
     sum_k_warps(a, ring, P, twp, nrows);
   } else {
@@ -433,7 +584,7 @@ __device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, si
   return s;
 }
 
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE>
+template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC>
 __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -492,6 +643,23 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     const int r = idx / T, t = idx % T;
     R_s[idx] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
   }
+  // scale of X (tensor-core form): 2^-e with max |R| < 2^e; every CTA forms it
+  // from all of R, so all agree without communication
+  CT xsc = CT(1), xsi = CT(1);
+  if constexpr (TC) {
+    double m = 0.0;
+    for (size_t idx = threadIdx.x; idx < (size_t)N * T; idx += kThreads) m = fmax(m, fabs(a.R[idx]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    double* red = reinterpret_cast<double*>(P);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    for (int i = 0; i < kThreads / 32; ++i) m = fmax(m, red[i]);
+    int ex = 0;
+    if (m > 0.0 && m <= 1e30) frexp(m, &ex);
+    ex = max(-100, min(100, ex));
+    xsc = CT(ldexp(1.0, -ex));
+    xsi = CT(ldexp(1.0, ex));
+  }
   __syncthreads();
   unsigned gctr = 0;
   const double st = sqrt(a.tau);
@@ -503,19 +671,20 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
       const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-      a.X0[xblock(t0, Npad) + xoff<WIDE>(row0 + own0 + r, t - t0, twp)] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
+      xput<GT, CT, WIDE, TC>(a.X0 + xblock(t0, Npad), row0 + own0 + r, t - t0, twp,
+                             CT(a.R[(size_t)(row0 + own0 + r) * T + t]) * xsc, a.err);
     }
     fence_proxy_async_global();
     if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                full, empty, gctr);
+      block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring,
+                                                    P, full, empty, gctr);
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         const int gr = row0 + own0 + r;
-        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr);
+        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr) * xsi;
         const double Rr = a.R[(size_t)gr * T + t0 + tt];
         b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
       }
@@ -537,8 +706,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     e_s[idx] = CT(1);
     const CT Rr = R_s[idx];
     const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-    a.X1[xblock(t0, Npad) + xoff<WIDE>(gr, t - t0, twp)] =
-        (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+    xput<GT, CT, WIDE, TC>(a.X1 + xblock(t0, Npad), gr, t - t0, twp,
+                           ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc, a.err);
   }
   fence_proxy_async_global();
   if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
@@ -553,14 +722,14 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     const bool rec = n < a.record_steps;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                full, empty, gctr);
+      block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
+                                                    full, empty, gctr);
       cluster.sync();
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         const int gr = row0 + own0 + r;
-        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr);
+        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr) * xsi;
         const size_t so = (size_t)r * T + t0 + tt;
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
@@ -570,7 +739,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
         c_s[so] = cn;
         e_s[so] = en;
-        Xnb[xoff<WIDE>(gr, tt, twp)] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        xput<GT, CT, WIDE, TC>(Xnb, gr, tt, twp, ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc,
+                               a.err);
         const size_t o = (size_t)gr * T + t0 + tt;
         if (rec) {
           const size_t ro = (size_t)n * N * T + o;

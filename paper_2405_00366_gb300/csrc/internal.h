@@ -43,7 +43,7 @@ struct ProblemDev {
   int gt_prec = -1;
   float* gscale = nullptr; // N row scales of G_off for FP8 storage (largest |G_off[r][k]| / 448)
   void* Gt2 = nullptr;    // G_off tiles of a streaming Euler plan (see euler.cu)
-  int gt2_prec = -1, gt2_rpc = 0, gt2_rpcpad = 0, gt2_nc = 0;
+  int gt2_prec = -1, gt2_rpc = 0, gt2_rpcpad = 0, gt2_nc = 0, gt2_frag = 0;
   int* flag = nullptr;    // device word: nonzero if A or y had a non-finite value
   int64_t launches = 0;   // kernels launched by the last create + solve
 };
@@ -99,7 +99,7 @@ struct SolveDev {
   int* singular = nullptr;      // set when a refit used the ridge
   RefitJob* job = nullptr;      // this problem's refit job (device copy)
   bool done = false;
-  int plan_cluster = 0, plan_ctas = 0;  // work split of the last Euler launch
+  int plan_cluster = 0, plan_ctas = 0, plan_form = 0;  // work split of the last Euler launch
 };
 
 RefitJob make_job(const ProblemDev& P, const SolveDev& S);

@@ -77,3 +77,88 @@ def test_streamed_bf16_autotuned_matches_resident():
     b = solve(inst, w, 64, stream_g=1, autotune=1)
     np.testing.assert_array_equal(a["sigmas"], b["sigmas"])
     np.testing.assert_allclose(a["x_hat"], b["x_hat"], rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------------ tensor-core form
+def round_to_storage(G, precision):
+    """G rounded to nearest, ties to even, in the 16-bit storage type (as the
+    library stores G_off)."""
+    if precision == "fp16":
+        return G.astype(np.float16).astype(np.float64)
+    m, e = np.frexp(G)  # G = m 2^e, 1/2 <= |m| < 1; BF16 keeps 8 significant bits
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def rel_traj_err(c, ref):
+    """Per-step ||c - ref||_inf / max(||ref||_inf, 1e-2)."""
+    num = np.abs(c - ref).reshape(c.shape[0], -1).max(axis=1)
+    den = np.maximum(np.abs(ref).reshape(ref.shape[0], -1).max(axis=1), 1e-2)
+    return num / den
+
+
+def solve_traj(inst, w, T, record_steps, y=None, lam=None, **over):
+    prm = cs.params_from_workload(w, record_steps=record_steps, **over)
+    y = inst.y if y is None else y
+    lam = inst.lam if lam is None else lam
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(y).cuda(), lam)
+    try:
+        cs.cs_solve(h, prm, T)
+        x, s, E, st, status = cs.cs_result(h)
+        R, sig, Es, ss = cs.cs_result_trials(h, T, w["n_outer"])
+        c, e = cs.cs_trajectory(h, record_steps, T)
+    finally:
+        cs.cs_problem_destroy(h)
+    return dict(x_hat=x, sigma=s, energy=E, stats=st, status=status, sigmas=sig, c=c, e=e)
+
+
+@pytest.mark.parametrize("precision,field,cluster", [("fp16", "cn", 0), ("fp16", "bn", 1), ("bf16", "cn", 2)])
+def test_tensor_core_trajectory_matches_rounded_oracle(precision, field, cluster):
+    """Streamed 16-bit G_off with eight trials runs on the tensor cores (stats[10]
+    = 2).  N = 333 (ragged: 21 row tiles of 16, a partial last k tile): the first
+    200 Euler steps of every trial against the oracle's CIM run on the same G_off
+    rounded to the storage type, to the FP32 form's tolerance (1e-4 relative)."""
+    inst = cs_inputs.random_instance(333, 211, 30, 0.01, 0.04, seed=7)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=600, precision=precision, field=field,
+             seed=3)
+    g = solve_traj(inst, w, 8, 200, stream_g=1, cluster_size=cluster, tensor_form=2)
+    assert g["stats"][10] == 2
+    op = oracle_params(w)
+    G, hz, gd = oracle.gram(inst.A, inst.y)
+    Goff = round_to_storage(G - np.diag(gd), precision)
+    R = np.repeat((hz / gd)[:, None], 8, axis=1)
+    _, _, _, rc, re = oracle.cim_run(Goff, hz, R, oracle.eta_at(0, op, inst.lam), op, outer=0, record_steps=200,
+                                     max_steps=200)
+    assert rel_traj_err(g["c"], rc).max() <= 1e-4
+    assert rel_traj_err(g["e"], re).max() <= 1e-4
+
+
+def test_tensor_core_power_of_two_scaling_is_exact():
+    """(y, lambda, K) -> (2^16 y, 2^32 lambda, 2^-32 K) leaves the dynamics exactly
+    unchanged and scales R, x_hat by 2^16 and the energy by 2^32.  With FP16 X the
+    unscaled X would overflow (|X| ~ 2^16 |c|); the form's power-of-two scale of X
+    makes every trajectory bit-identical to the unscaled problem's."""
+    inst = cs_inputs.random_instance(333, 211, 30, 0.01, 0.04, seed=7)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=400, precision="fp16", seed=3)
+    s = 2.0 ** 16
+    a = solve_traj(inst, w, 8, 100, stream_g=1, tensor_form=2)
+    b = solve_traj(inst, dict(w, K=w["K"] / (s * s)), 8, 100, y=inst.y * s, lam=inst.lam * s * s, stream_g=1,
+                   tensor_form=2)
+    assert a["stats"][10] == 2 and b["stats"][10] == 2
+    np.testing.assert_array_equal(a["c"], b["c"])
+    np.testing.assert_array_equal(a["sigmas"], b["sigmas"])
+    np.testing.assert_array_equal(a["x_hat"] * s, b["x_hat"])
+    assert b["energy"] == pytest.approx(a["energy"] * s * s, rel=1e-14)
+
+
+def test_mri_shaped_small_tensor_cores():
+    """32 x 32 MRI-shaped problem, FP16 G_off streamed, eight trials: the tensor-core
+    form (tensor_form = 2) and the FMA forms (tensor_form = 1) each meet the FP16 gate against the
+    FP64 oracle (support within 1%, RMSE within 1e-3)."""
+    w = cs_inputs.workload("mri_n16384_fp16", mri_side=32, N=1024, M=307, nnz=102, n_outer=3, n_steps=800)
+    inst = cs_inputs.workload_instance(w)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=8)
+    for tf in (2, 1):
+        g = solve(inst, w, 8, stream_g=1, tensor_form=tf)
+        assert (g["stats"][10] == 2) == (tf == 2)
+        assert oracle.hamming_loss(g["sigma"], r["sigma"]) <= 0.01
+        assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
