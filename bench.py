@@ -476,6 +476,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-form", type=int, choices=[0, 1, 2], default=0,
+                    help="cs_params.tensor_form: 0 planner, 1 FMA forms only, 2 tensor-core form only")
     ap.add_argument("--reference-step-s", type=float, default=8.0)
     ap.add_argument("--n-outer", type=int, default=None,
                     help="override the workload's outer iterations (short runs for profiling only)")
@@ -521,7 +523,7 @@ def main():
     inst = cs_inputs.workload_instance(w)
     # work split timed on this GPU during the warm-up (the MRI-shaped problem keeps
     # the cost model's streamed split: its tuning runs would take seconds)
-    prm = cs.params_from_workload(w, autotune=0 if name == "mri_n16384_fp16" else 1)
+    prm = cs.params_from_workload(w, autotune=0 if name == "mri_n16384_fp16" else 1, tensor_form=args.tensor_form)
     T = w["trials"]
     stream = torch.cuda.Stream()
     A_dev = torch.from_numpy(inst.A).cuda()

@@ -42,9 +42,13 @@ EulerFn<CT> kernel_for_s(int MR) {
 // for FP32 compute only.
 template <typename GT> struct streamable { static constexpr bool value = !std::is_same<GT, double>::value; };
 template <typename CT> struct widenable { static constexpr bool value = std::is_same<CT, float>::value; };
-// The tensor-core form: streamed FP16 / BF16 G_off with FP32 compute.
+// The tensor-core forms: streamed FP16 / BF16 G_off with FP32 compute, and
+// resident FP32 G_off (3xTF32).
 template <typename GT, typename CT> struct tensorable {
   static constexpr bool value = tc_type<GT>::value && std::is_same<CT, float>::value;
+};
+template <typename GT, typename CT> struct tf32able {
+  static constexpr bool value = std::is_same<GT, float>::value && std::is_same<CT, float>::value;
 };
 
 template <typename GT, typename CT, bool WIDE>
@@ -59,6 +63,9 @@ template <typename GT, typename CT>
 EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
   if constexpr (tensorable<GT, CT>::value) {
     if (tc) return kernel_for_s<GT, CT, true, true, true>(MR);
+  }
+  if constexpr (tf32able<GT, CT>::value) {
+    if (tc) return kernel_for_s<GT, CT, false, true, true>(MR);
   }
   if constexpr (widenable<CT>::value) {
     if (wide) return kernel_for_w<GT, CT, true>(MR, stream);
@@ -107,8 +114,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   // power of two (lane column groups)
   const bool wide_ok = widenable<CT>::value && (twmax == 8 || twmax == 16 || twmax == 32 || twmax == 64) &&
                        (T <= kTChunk || T % kTChunk == 0);
-  // the tensor-core form: one block of exactly eight trials
+  // the 16-bit tensor-core form (streamed): one block of exactly eight trials;
+  // the FP32 one (resident): blocks of one width in {16, 32, 64}
   const bool tc_ok = tensorable<GT, CT>::value && tensor_form != 1 && T == 8;
+  const bool tf32_ok = tf32able<GT, CT>::value && tensor_form != 1 && twmax >= 16 && wide_ok;
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -126,7 +135,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         const int WK = tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0);
         const bool wide = WK > 0;
         if (wide && !wide_ok) continue;
-        if (tc && !(stream && tc_ok)) continue;
+        if (tc && !(stream ? tc_ok : tf32_ok)) continue;
+        if (tc && !stream && WK * (twmax / 16) > kConsumerWarps) continue;
         if (!tc && tensor_form == 2) continue;
         Plan pl{};
         pl.C = C;
@@ -139,13 +149,15 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           pl.kch = kStreamK;  // per slot; widened below to as many tiles as the ring allows
         } else {
           pl.kq = (nq + C - 1) / C;
+          if (tc) pl.kq += pl.kq & 1;  // whole blocks of 8 k per rank
           // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
           pl.kch = std::max(4, std::min(pl.kq * 4, (int)((16384 / (twmax * sizeof(CT))) & ~(size_t)3)));
         }
         // resident G rows: an odd number of quads apart, so the rows a half-warp
         // reads start in different banks
         pl.ldg = (wide && pl.kq % 2 == 0) ? (pl.kq + 1) * 4 : pl.kq * 4;
-        const int WR = wide ? kConsumerWarps / WK : WRn;
+        if (tc && !stream) pl.ldg = (pl.kq * 4 + 23) / 32 * 32 + 8;  // 8 (mod 32) words
+        const int WR = tc && !stream ? kConsumerWarps / (WK * (twmax / 16)) : (wide ? kConsumerWarps / WK : WRn);
         // rows per lane group: the wide split's row groups, or 16-row MMA tiles
         const int CGw = twmax / 4, RGw = tc ? 16 : (wide ? 32 / CGw : 1);
         // the largest number of clusters that fits, and a single cluster (whose
@@ -226,12 +238,18 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           const double gbytes =
               stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) * std::max(1.0, 128.0 / pl.kch) : 0.0;
           double cost;
-          if (tc) {
+          if (tc && stream) {
             // MMAs (two per 16 x 16 tile of G_off: the two parts of X), taken at
-            // one per two clocks per SM, overlap the streamed bytes
+            // one per two clocks per SM (measured on GB300), overlap the streamed bytes
             const double mmas = (double)pl.RPC_pad / 16.0 * pl.kq * 4 / 16.0 * 2.0;
             const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
             cost = std::max(mmas * 2.0, gbytes / 22.0) + xbytes / 44.0 + red;
+          } else if (tc) {
+            // three m16n8k8 MMAs per 16 x 8 x 8 block, at one per two clocks per SM
+            // and an assumed 70% of that
+            const double mmas = (double)pl.RPC_pad / 16.0 * (twmax / 8) * nblk * (pl.kq * 4 / 8) * 3.0;
+            const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
+            cost = mmas * 2.0 / 0.7 + xbytes / 44.0 + red;
           } else if (wide) {
             const double ffma2 = fma / 64.0;  // packed FMA warp instructions
             const double wf = ffma2 * (8.0 + 2.0 * pl.MR) / (8.0 * pl.MR);
@@ -360,10 +378,11 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
   return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
-// Autotuner: time the kTuneCands cheapest candidate splits of the cost model
-// on this GPU (kTuneSteps Euler steps each, twice, CUDA events on the
-// problem's stream; the second run counts) and return the fastest.  The runs
-// only write the solve's scratch (X, sigma), which the real run rewrites.
+// Autotuner: time the kTuneCands cheapest candidate splits of the cost model,
+// plus the cheapest of each kernel form (FMA, tensor cores) not among them, on
+// this GPU (kTuneSteps Euler steps each, twice, CUDA events on the problem's
+// stream; the second run counts) and return the fastest.  The runs only write
+// the solve's scratch (X, sigma), which the real run rewrites.
 constexpr int kTuneCands = 4;
 constexpr int kTuneSteps = 48;
 
@@ -375,7 +394,17 @@ cudaError_t autotune_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int 
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best = 0.f;
   const int steps = std::min(prm.n_steps, kTuneSteps);
-  for (size_t c = 0; c < cands.size() && (int)c < kTuneCands && e == cudaSuccess; ++c) {
+  std::vector<size_t> pick;
+  bool form_seen[2] = {false, false};
+  for (size_t c = 0; c < cands.size(); ++c) {
+    const int f = cands[c].second.tc ? 1 : 0;
+    if ((int)pick.size() < kTuneCands || !form_seen[f]) {
+      pick.push_back(c);
+      form_seen[f] = true;
+    }
+  }
+  for (size_t pi = 0; pi < pick.size() && e == cudaSuccess; ++pi) {
+    const size_t c = pick[pi];
     float ms = 0.f;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       e = cudaEventRecord(e0, P.stream);
@@ -385,7 +414,7 @@ cudaError_t autotune_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int 
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     }
-    if (e == cudaSuccess && (c == 0 || ms < best)) {
+    if (e == cudaSuccess && (pi == 0 || ms < best)) {
       best = ms;
       *out = cands[c].second;
     }

@@ -436,6 +436,10 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
 // power of two that maps the largest |R| below 1 (so FP16 X stays in range
 // while the amplitudes stay below 6e4) and U is scaled back exactly.
 //
+// Accumulation: each MMA starts from zero and its result is added to the FP32
+// sums with round-to-nearest additions; chaining the MMAs of a whole k range in
+// one accumulator would let the tensor cores' truncating accumulation build a
+// bias (measured on GB300: about 1e-5 relative over a few hundred MMAs).
 // Contraction order: the MMA sums k = 2i, 2i + 1 (operand register 0) and
 // 2i + 8, 2i + 9 (register 2) in lane group i; both operands here put the
 // consecutive k 4i .. 4i + 3 there instead, which only renames the summation
@@ -514,8 +518,14 @@ __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const flo
         for (int i = 0; i < MR; ++i) av[i] = gb[(size_t)i * 64];
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
-          mma16816<GT>(acc[i][0], av[i], xh);
-          mma16816<GT>(acc[i][1], av[i], xl);
+          float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+          mma16816<GT>(dh, av[i], xh);
+          mma16816<GT>(dl, av[i], xl);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[i][0][q] += dh[q];
+            acc[i][1][q] += dl[q];
+          }
         }
       }
     }
@@ -538,13 +548,133 @@ __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const flo
   }
 }
 
+// FP32 tensor-core form (G_off resident in shared memory in FP32, trial blocks
+// of 16, 32 or 64): G_off X as m16n8k8 TF32 MMAs with both operands split in
+// registers, v = hi + lo with hi = v truncated to TF32 (10 fraction bits) and
+// lo = v - hi (exact) rounded to the nearest TF32, and three MMAs per tile
+// (lo_G hi_X + hi_G lo_X + hi_G hi_X), dropping only the lo_G lo_X term: each
+// product is kept to about 2^-21 relative, without bias, below the FP32
+// accumulation error of a sum over the k range, so the form stands in for FP32
+// FMAs.  (The split is integer masking and one add: conversion instructions
+// issue at a quarter of the ALU rate and measured slower.)  (TF32 MMAs issue at about four times the FP32 FMA rate on GB300.)  The
+// three MMAs of a block of 8 k chain in one zeroed accumulator whose result is
+// added to the FP32 sums (round to nearest), as in the 16-bit form.
+// Contraction order: lane group i supplies the MMA's k = i and i + 4; here
+// both operands put the consecutive k 2i, 2i + 1 of each block of 8 there, so
+// a lane reads them with one 8-byte access.  X of the block is stored as
+// [k / 8][trial][k % 8] (xput), so the 8-byte X reads of a half-warp hit distinct
+// banks; the rows of the resident G_off block are ldg = 8 (mod 32) words apart,
+// which does the same for G_off.  Warps: WC = twp / 16 column-warps of two
+// n-tiles (16 trials) x WR row-warps (MR row tiles of 16) x WK k-warps (every
+// WK-th 8-k block of a chunk); partials through the ring as in the wide split.
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(v) & 0xffffe000u;                    // truncated: the rest is exact in r
+  const float r = v - __uint_as_float(hi);
+  lo = (__float_as_uint(r) + 0x1000u) & 0xffffe000u;        // r to nearest TF32 (ties away from zero)
+}
+__device__ __forceinline__ void mma1688(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int MR>
+__device__ __forceinline__ void tf32_partials(const EulerArgs<float>& a, const float* __restrict__ Gsm,
+                                              const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
+                                              unsigned char* ring, uint64_t* full, uint64_t* empty, unsigned& gctr) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nch = (klen + a.kch - 1) / a.kch;
+  if (w == kConsumerWarps) {
+    produce_chunks<float, float, false>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    gctr += nch;
+    return;
+  }
+  const int WC = twp >> 4, WK = a.WK, WR = kConsumerWarps / (WC * WK);
+  const int wc = w % WC, wr = (w / WC) % WR, kw = w / (WC * WR);
+  const int rt0 = wr * MR, n0 = wc * 16;
+  const int gq = l >> 2, i4 = l & 3;
+  const int ldg = a.ldg;
+  float acc[MR][2][4];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][nt][q] = 0.f;
+  bool ok = true;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok) {
+      const float* xs = reinterpret_cast<const float*>(ring + (size_t)s * a.slot_bytes) + (n0 + gq) * 8 + 2 * i4;
+      const float* gk = Gsm + (size_t)(rt0 * 16 + gq) * ldg + ci * a.kch + 2 * i4;
+      const int nkb = min(a.kch, klen - ci * a.kch) >> 3;
+#pragma unroll 1
+      for (int kb = kw; kb < nkb; kb += WK) {
+        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const float2 v = *reinterpret_cast<const float2*>(xs + ((size_t)kb * twp + nt * 8) * 8);
+          split_tf32(v.x, bh[nt][0], bl[nt][0]);
+          split_tf32(v.y, bh[nt][1], bl[nt][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const float* gr = gk + (size_t)(i * 16) * ldg + kb * 8;
+          const float2 u0 = *reinterpret_cast<const float2*>(gr);              // row g
+          const float2 u8 = *reinterpret_cast<const float2*>(gr + 8 * ldg);    // row g + 8
+          uint32_t ah[4], al[4];
+          split_tf32(u0.x, ah[0], al[0]);
+          split_tf32(u8.x, ah[1], al[1]);
+          split_tf32(u0.y, ah[2], al[2]);
+          split_tf32(u8.y, ah[3], al[3]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            mma1688(d, al, bh[nt][0], bh[nt][1]);
+            mma1688(d, ah, bl[nt][0], bl[nt][1]);
+            mma1688(d, ah, bh[nt][0], bh[nt][1]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][nt][q] += d[q];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (l == 0) mbar_arrive(empty + s);
+  }
+  gctr += nch;
+  // every consumer warp is done with the ring before it holds partials
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+  float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    const int r = (rt0 + i) * 16 + gq;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int c = n0 + nt * 8 + 2 * i4;
+      *reinterpret_cast<float2*>(dst + (size_t)r * twp + c) = make_float2(acc[i][nt][0], acc[i][nt][1]);
+      *reinterpret_cast<float2*>(dst + (size_t)(r + 8) * twp + c) = make_float2(acc[i][nt][2], acc[i][nt][3]);
+    }
+  }
+}
+
 // Store X[k][t] = v of a block of twp trials in the layout the kernel form reads:
-// xoff for the FMA forms; for the tensor-core form the hi and lo parts at
-// [k / 16][part][t][k % 16].  An X that overflows FP16 (amplitude beyond the
-// range after the scale) sets DEV_RANGE.
+// xoff for the FMA forms; [k / 8][t][k % 8] for the FP32 tensor-core form; for
+// the 16-bit tensor-core form the hi and lo parts at [k / 16][part][t][k % 16].
+// An X that overflows FP16 (amplitude beyond the range after the scale) sets
+// DEV_RANGE.
 template <typename GT, typename CT, bool WIDE, bool TC>
 __device__ __forceinline__ void xput(CT* Xb, int k, int t, int twp, CT v, int* err) {
-  if constexpr (TC) {
+  if constexpr (TC && !tc_type<GT>::value) {
+    Xb[((size_t)(k >> 3) * twp + t) * 8 + (k & 7)] = v;
+  } else if constexpr (TC) {
     GT* h = reinterpret_cast<GT*>(Xb);
     const size_t o = ((size_t)(k >> 4) * 2 * twp + t) * 16 + (k & 15);
     const GT hi = GT(v);
@@ -564,7 +694,11 @@ __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT*
                                                int cl, unsigned char* ring, CT* P, uint64_t* full, uint64_t* empty,
                                                unsigned& gctr) {
   if constexpr (TC) {
-    tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    if constexpr (tc_type<GT>::value) {
+      tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    } else {
+      tf32_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    }
     sum_k_warps(a, ring, P, twp, nrows);
   } else if constexpr (WIDE) {
     wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
@@ -646,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   // scale of X (tensor-core form): 2^-e with max |R| < 2^e; every CTA forms it
   // from all of R, so all agree without communication
   CT xsc = CT(1), xsi = CT(1);
-  if constexpr (TC) {
+  if constexpr (TC && tc_type<GT>::value) {
     double m = 0.0;
     for (size_t idx = threadIdx.x; idx < (size_t)N * T; idx += kThreads) m = fmax(m, fabs(a.R[idx]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
