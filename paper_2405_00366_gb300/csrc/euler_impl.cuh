@@ -43,11 +43,11 @@ EulerFn<CT> kernel_for_s(int MR) {
 template <typename GT> struct streamable { static constexpr bool value = !std::is_same<GT, double>::value; };
 template <typename CT> struct widenable { static constexpr bool value = std::is_same<CT, float>::value; };
 // The tensor-core forms: streamed FP16 / BF16 G_off with FP32 compute, and
-// resident FP32 G_off (3xTF32).
+// resident FP32 G_off (three FP16 MMAs on split operands).
 template <typename GT, typename CT> struct tensorable {
   static constexpr bool value = tc_type<GT>::value && std::is_same<CT, float>::value;
 };
-template <typename GT, typename CT> struct tf32able {
+template <typename GT, typename CT> struct h3able {
   static constexpr bool value = std::is_same<GT, float>::value && std::is_same<CT, float>::value;
 };
 
@@ -64,7 +64,7 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
   if constexpr (tensorable<GT, CT>::value) {
     if (tc) return kernel_for_s<GT, CT, true, true, true>(MR);
   }
-  if constexpr (tf32able<GT, CT>::value) {
+  if constexpr (h3able<GT, CT>::value) {
     if (tc) return kernel_for_s<GT, CT, false, true, true>(MR);
   }
   if constexpr (widenable<CT>::value) {
@@ -117,7 +117,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   // the 16-bit tensor-core form (streamed): one block of exactly eight trials;
   // the FP32 one (resident): blocks of one width in {16, 32, 64}
   const bool tc_ok = tensorable<GT, CT>::value && tensor_form != 1 && T == 8;
-  const bool tf32_ok = tf32able<GT, CT>::value && tensor_form != 1 && twmax >= 16 && wide_ok;
+  const bool h3_ok = h3able<GT, CT>::value && tensor_form != 1 && twmax >= 16 && wide_ok;
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -135,7 +135,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         const int WK = tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0);
         const bool wide = WK > 0;
         if (wide && !wide_ok) continue;
-        if (tc && !(stream ? tc_ok : tf32_ok)) continue;
+        if (tc && !(stream ? tc_ok : h3_ok)) continue;
         if (tc && !stream && WK * (twmax / 16) > kConsumerWarps) continue;
         if (!tc && tensor_form == 2) continue;
         Plan pl{};
@@ -149,14 +149,14 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           pl.kch = kStreamK;  // per slot; widened below to as many tiles as the ring allows
         } else {
           pl.kq = (nq + C - 1) / C;
-          if (tc) pl.kq += pl.kq & 1;  // whole blocks of 8 k per rank
+          if (tc) pl.kq = (pl.kq + 3) / 4 * 4;  // whole blocks of 16 k per rank
           // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
           pl.kch = std::max(4, std::min(pl.kq * 4, (int)((16384 / (twmax * sizeof(CT))) & ~(size_t)3)));
         }
         // resident G rows: an odd number of quads apart, so the rows a half-warp
         // reads start in different banks
         pl.ldg = (wide && pl.kq % 2 == 0) ? (pl.kq + 1) * 4 : pl.kq * 4;
-        if (tc && !stream) pl.ldg = (pl.kq * 4 + 23) / 32 * 32 + 8;  // 8 (mod 32) words
+        if (tc && !stream) pl.ldg = pl.kq * 4;  // the block in A-operand order, no padding
         const int WR = tc && !stream ? kConsumerWarps / (WK * (twmax / 16)) : (wide ? kConsumerWarps / WK : WRn);
         // rows per lane group: the wide split's row groups, or 16-row MMA tiles
         const int CGw = twmax / 4, RGw = tc ? 16 : (wide ? 32 / CGw : 1);
@@ -245,9 +245,9 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
             cost = std::max(mmas * 2.0, gbytes / 22.0) + xbytes / 44.0 + red;
           } else if (tc) {
-            // three m16n8k8 MMAs per 16 x 8 x 8 block, at one per two clocks per SM
-            // and an assumed 70% of that
-            const double mmas = (double)pl.RPC_pad / 16.0 * (twmax / 8) * nblk * (pl.kq * 4 / 8) * 3.0;
+            // three m16n8k16 MMAs per 16 x 8 x 16 block, at one per two clocks per
+            // SM and about 70% of that (measured on GB300 for this loop)
+            const double mmas = (double)pl.RPC_pad / 16.0 * (twmax / 8) * nblk * (pl.kq * 4 / 16) * 3.0;
             const double red = (double)WK * pl.RPC * twmax * nblk / kThreads * 4.0;
             cost = mmas * 2.0 / 0.7 + xbytes / 44.0 + red;
           } else if (wide) {

@@ -455,6 +455,10 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
 template <typename GT> struct tc_type { static constexpr bool value = false; };
 template <> struct tc_type<__half> { static constexpr bool value = true; static constexpr int kLoShift = 11; };
 template <> struct tc_type<__nv_bfloat16> { static constexpr bool value = true; static constexpr int kLoShift = 8; };
+// 16-bit type and lo shift of the two parts of X in a tensor-core form: the
+// storage type's own for 16-bit G_off, FP16 for FP32 G_off
+template <typename GT> struct tc_x { using type = GT; static constexpr int kLoShift = tc_type<GT>::kLoShift; };
+template <> struct tc_x<float> { using type = __half; static constexpr int kLoShift = 11; };
 
 template <typename GT>
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint4& a, const uint2& b) {
@@ -548,41 +552,27 @@ __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const flo
   }
 }
 
-// FP32 tensor-core form (G_off resident in shared memory in FP32, trial blocks
-// of 16, 32 or 64): G_off X as m16n8k8 TF32 MMAs with both operands split in
-// registers, v = hi + lo with hi = v truncated to TF32 (10 fraction bits) and
-// lo = v - hi (exact) rounded to the nearest TF32, and three MMAs per tile
-// (lo_G hi_X + hi_G lo_X + hi_G hi_X), dropping only the lo_G lo_X term: each
-// product is kept to about 2^-21 relative, without bias, below the FP32
+// FP32 tensor-core form (G_off resident in shared memory, FP32 problems, trial
+// blocks of 16, 32 or 64): G_off X as m16n8k16 FP16 MMAs on three-way splits.
+// Each CTA scales its block of G_off by a power of two (max |G| < 1) and keeps
+// it as two FP16 parts, G = hi + 2^-11 lo (hi = rn(G), lo = rn((G - hi) 2^11)),
+// stored once per launch in the MMA's A-operand order (the 16-bit form's tile
+// layout, [row tile][16-k block][part][lane][8]); X comes in the same two FP16
+// parts as in the 16-bit form (xput, power-of-two scale from max |R|).  Per
+// 16 x 8 x 16 tile three MMAs, hi_G hi_X into one zeroed accumulator and
+// hi_G lo_X + lo_G hi_X into another, dropping only the 2^-22 lo_G lo_X term:
+// each product keeps about 22 significant bits, without bias, below the FP32
 // accumulation error of a sum over the k range, so the form stands in for FP32
-// FMAs.  (The split is integer masking and one add: conversion instructions
-// issue at a quarter of the ALU rate and measured slower.)  (TF32 MMAs issue at about four times the FP32 FMA rate on GB300.)  The
-// three MMAs of a block of 8 k chain in one zeroed accumulator whose result is
-// added to the FP32 sums (round to nearest), as in the 16-bit form.
-// Contraction order: lane group i supplies the MMA's k = i and i + 4; here
-// both operands put the consecutive k 2i, 2i + 1 of each block of 8 there, so
-// a lane reads them with one 8-byte access.  X of the block is stored as
-// [k / 8][trial][k % 8] (xput), so the 8-byte X reads of a half-warp hit distinct
-// banks; the rows of the resident G_off block are ldg = 8 (mod 32) words apart,
-// which does the same for G_off.  Warps: WC = twp / 16 column-warps of two
+// FMAs.  (FP16 MMAs issue at twice the TF32 rate per k on GB300, and the
+// split costs no ALU work per use.)  Warps: WC = twp / 16 column-warps of two
 // n-tiles (16 trials) x WR row-warps (MR row tiles of 16) x WK k-warps (every
-// WK-th 8-k block of a chunk); partials through the ring as in the wide split.
-__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
-  hi = __float_as_uint(v) & 0xffffe000u;                    // truncated: the rest is exact in r
-  const float r = v - __uint_as_float(hi);
-  lo = (__float_as_uint(r) + 0x1000u) & 0xffffe000u;        // r to nearest TF32 (ties away from zero)
-}
-__device__ __forceinline__ void mma1688(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
+// WK-th 16-k block of a chunk); partials through the ring as in the wide split,
+// scaled back by the block's power of two.
 template <int MR>
-__device__ __forceinline__ void tf32_partials(const EulerArgs<float>& a, const float* __restrict__ Gsm,
-                                              const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
-                                              unsigned char* ring, uint64_t* full, uint64_t* empty, unsigned& gctr) {
+__device__ __forceinline__ void h3_partials(const EulerArgs<float>& a, const float* __restrict__ Gsm,
+                                            const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
+                                            unsigned char* ring, uint64_t* full, uint64_t* empty, unsigned& gctr,
+                                            float gsi) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
@@ -593,15 +583,17 @@ __device__ __forceinline__ void tf32_partials(const EulerArgs<float>& a, const f
   const int WC = twp >> 4, WK = a.WK, WR = kConsumerWarps / (WC * WK);
   const int wc = w % WC, wr = (w / WC) % WR, kw = w / (WC * WR);
   const int rt0 = wr * MR, n0 = wc * 16;
-  const int gq = l >> 2, i4 = l & 3;
-  const int ldg = a.ldg;
-  float acc[MR][2][4];
+  const int nkb16 = klen >> 4;  // 16-k blocks of this CTA's G_off block
+  const uint4* ga = reinterpret_cast<const uint4*>(Gsm) + (size_t)rt0 * nkb16 * 64 + l;
+  float acc[MR][2][2][4];
 #pragma unroll
   for (int i = 0; i < MR; ++i)
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][nt][q] = 0.f;
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][nt][p][q] = 0.f;
   bool ok = true;
   for (int ci = 0; ci < nch; ++ci) {
     const unsigned g = gctr + ci;
@@ -612,36 +604,33 @@ __device__ __forceinline__ void tf32_partials(const EulerArgs<float>& a, const f
       if (l == 0) set_error(a.err, DEV_TIMEOUT);
     }
     if (ok) {
-      const float* xs = reinterpret_cast<const float*>(ring + (size_t)s * a.slot_bytes) + (n0 + gq) * 8 + 2 * i4;
-      const float* gk = Gsm + (size_t)(rt0 * 16 + gq) * ldg + ci * a.kch + 2 * i4;
-      const int nkb = min(a.kch, klen - ci * a.kch) >> 3;
+      const uint2* xs = reinterpret_cast<const uint2*>(ring + (size_t)s * a.slot_bytes) + (size_t)n0 * 4 + l;
+      const int nkb = min(a.kch, klen - ci * a.kch) >> 4;
+      const uint4* gc = ga + (size_t)((ci * a.kch) >> 4) * 64;
 #pragma unroll 1
       for (int kb = kw; kb < nkb; kb += WK) {
-        uint32_t bh[2][2], bl[2][2];
+        uint2 xh[2], xl[2];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
-          const float2 v = *reinterpret_cast<const float2*>(xs + ((size_t)kb * twp + nt * 8) * 8);
-          split_tf32(v.x, bh[nt][0], bl[nt][0]);
-          split_tf32(v.y, bh[nt][1], bl[nt][1]);
+          xh[nt] = xs[((size_t)(2 * kb) * twp + nt * 8) * 4];
+          xl[nt] = xs[((size_t)(2 * kb + 1) * twp + nt * 8) * 4];
         }
+        const uint4* gp = gc + (size_t)kb * 64;
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
-          const float* gr = gk + (size_t)(i * 16) * ldg + kb * 8;
-          const float2 u0 = *reinterpret_cast<const float2*>(gr);              // row g
-          const float2 u8 = *reinterpret_cast<const float2*>(gr + 8 * ldg);    // row g + 8
-          uint32_t ah[4], al[4];
-          split_tf32(u0.x, ah[0], al[0]);
-          split_tf32(u8.x, ah[1], al[1]);
-          split_tf32(u0.y, ah[2], al[2]);
-          split_tf32(u8.y, ah[3], al[3]);
+          const uint4 ah = gp[(size_t)i * nkb16 * 64];
+          const uint4 al = gp[(size_t)i * nkb16 * 64 + 32];
 #pragma unroll
           for (int nt = 0; nt < 2; ++nt) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            mma1688(d, al, bh[nt][0], bh[nt][1]);
-            mma1688(d, ah, bl[nt][0], bl[nt][1]);
-            mma1688(d, ah, bh[nt][0], bh[nt][1]);
+            float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+            mma16816<__half>(dh, ah, xh[nt]);
+            mma16816<__half>(dl, ah, xl[nt]);
+            mma16816<__half>(dl, al, xh[nt]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][nt][q] += d[q];
+            for (int q = 0; q < 4; ++q) {
+              acc[i][nt][0][q] += dh[q];
+              acc[i][nt][1][q] += dl[q];
+            }
           }
         }
       }
@@ -653,35 +642,75 @@ __device__ __forceinline__ void tf32_partials(const EulerArgs<float>& a, const f
   // every consumer warp is done with the ring before it holds partials
   asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
   float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  const float wlo = 1.0f / 2048.0f;
+  const int gq = l >> 2, i4 = l & 3;
 #pragma unroll
   for (int i = 0; i < MR; ++i) {
     const int r = (rt0 + i) * 16 + gq;
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
       const int c = n0 + nt * 8 + 2 * i4;
-      *reinterpret_cast<float2*>(dst + (size_t)r * twp + c) = make_float2(acc[i][nt][0], acc[i][nt][1]);
-      *reinterpret_cast<float2*>(dst + (size_t)(r + 8) * twp + c) = make_float2(acc[i][nt][2], acc[i][nt][3]);
+      const float* h = acc[i][nt][0];
+      const float* o = acc[i][nt][1];
+      *reinterpret_cast<float2*>(dst + (size_t)r * twp + c) =
+          make_float2(fmaf(wlo, o[0], h[0]) * gsi, fmaf(wlo, o[1], h[1]) * gsi);
+      *reinterpret_cast<float2*>(dst + (size_t)(r + 8) * twp + c) =
+          make_float2(fmaf(wlo, o[2], h[2]) * gsi, fmaf(wlo, o[3], h[3]) * gsi);
     }
   }
 }
 
+// Stage this CTA's block of FP32 G_off for the FP32 tensor-core form: rows
+// [row0, row0 + nrows) (zero up to RPC_pad), k in [k0, k0 + klen) (klen a
+// multiple of 16), scaled by 2^-e with max |G| < 2^e and split into two FP16
+// parts in A-operand order (h3_partials).  Returns 2^e.  Uses P as scratch.
+__device__ __forceinline__ float stage_h3(const float* __restrict__ src, int Npad, int row0, int nrows, int k0,
+                                          int klen, int RPC_pad, float* Gsm, float* P) {
+  float m = 0.f;
+  for (int v = threadIdx.x; v < nrows * klen; v += kThreads) {
+    const int r = v / klen, k = v % klen;
+    m = fmaxf(m, fabsf(src[(size_t)(row0 + r) * Npad + k0 + k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) P[threadIdx.x >> 5] = m;
+  __syncthreads();
+  for (int i = 0; i < kThreads / 32; ++i) m = fmaxf(m, P[i]);
+  __syncthreads();
+  int ex = 0;
+  if (m > 0.f && m <= 1e30f) frexpf(m, &ex);
+  ex = max(-100, min(100, ex));
+  const float gsc = ldexpf(1.f, -ex);
+  __half* gh = reinterpret_cast<__half*>(Gsm);
+  const int nkb16 = klen >> 4;
+  const int total = (RPC_pad >> 4) * nkb16 * 512;
+  for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+    const int unit = idx >> 9, within = idx & 511;
+    const int rt = unit / nkb16, kb = unit % nkb16;
+    const int part = within >> 8, L = (within >> 3) & 31, e = within & 7;
+    const int r = rt * 16 + (L >> 2) + 8 * ((e >> 1) & 1);
+    const int k = kb * 16 + 4 * (L & 3) + 2 * (e >> 2) + (e & 1);
+    const float v = r < nrows ? src[(size_t)(row0 + r) * Npad + k0 + k] * gsc : 0.f;
+    const __half hi = __float2half_rn(v);
+    gh[idx] = part ? __float2half_rn((v - __half2float(hi)) * 2048.f) : hi;
+  }
+  return ldexpf(1.f, ex);
+}
+
 // Store X[k][t] = v of a block of twp trials in the layout the kernel form reads:
-// xoff for the FMA forms; [k / 8][t][k % 8] for the FP32 tensor-core form; for
-// the 16-bit tensor-core form the hi and lo parts at [k / 16][part][t][k % 16].
-// An X that overflows FP16 (amplitude beyond the range after the scale) sets
-// DEV_RANGE.
+// xoff for the FMA forms; for the tensor-core forms the hi and lo parts at
+// [k / 16][part][t][k % 16].  An X that overflows FP16 (amplitude beyond the
+// range after the scale) sets DEV_RANGE.
 template <typename GT, typename CT, bool WIDE, bool TC>
 __device__ __forceinline__ void xput(CT* Xb, int k, int t, int twp, CT v, int* err) {
-  if constexpr (TC && !tc_type<GT>::value) {
-    Xb[((size_t)(k >> 3) * twp + t) * 8 + (k & 7)] = v;
-  } else if constexpr (TC) {
-    GT* h = reinterpret_cast<GT*>(Xb);
+  if constexpr (TC) {
+    using HT = typename tc_x<GT>::type;
+    HT* h = reinterpret_cast<HT*>(Xb);
     const size_t o = ((size_t)(k >> 4) * 2 * twp + t) * 16 + (k & 15);
-    const GT hi = GT(v);
+    const HT hi = HT(v);
     const float hf = float(hi);
     if (isinf(hf) && isfinite(v)) set_error(err, DEV_RANGE);
     h[o] = hi;
-    h[o + (size_t)twp * 16] = GT((v - hf) * (float)(1 << tc_type<GT>::kLoShift));
+    h[o + (size_t)twp * 16] = HT((v - hf) * (float)(1 << tc_x<GT>::kLoShift));
   } else {
     Xb[xoff<WIDE>(k, t, twp)] = v;
   }
@@ -692,12 +721,12 @@ template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC>
 __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
                                                int cl, unsigned char* ring, CT* P, uint64_t* full, uint64_t* empty,
-                                               unsigned& gctr) {
+                                               unsigned& gctr, float gsi) {
   if constexpr (TC) {
     if constexpr (tc_type<GT>::value) {
       tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
     } else {
-      tf32_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+      h3_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, gsi);
     }
     sum_k_warps(a, ring, P, twp, nrows);
   } else if constexpr (WIDE) {
@@ -755,7 +784,11 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     fence_mbar_init();
   }
   // Stage this CTA's block of G_off: rows [row0, row0 + nrows), k in [k0, k0 + klen).
-  if (!STREAM) {
+  float gsi = 1.f;  // scale of the staged block (FP32 tensor-core form)
+  if constexpr (TC && !STREAM) {
+    gsi = stage_h3(reinterpret_cast<const float*>(a.Gs), Npad, row0, nrows, k0, klen, a.RPC_pad,
+                   reinterpret_cast<float*>(Gsm), reinterpret_cast<float*>(P));
+  } else if (!STREAM) {
     const GT* src = reinterpret_cast<const GT*>(a.Gs);
     const int ldg = a.ldg;
     const int total = a.RPC_pad * nqj;
@@ -780,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   // scale of X (tensor-core form): 2^-e with max |R| < 2^e; every CTA forms it
   // from all of R, so all agree without communication
   CT xsc = CT(1), xsi = CT(1);
-  if constexpr (TC && tc_type<GT>::value) {
+  if constexpr (TC) {
     double m = 0.0;
     for (size_t idx = threadIdx.x; idx < (size_t)N * T; idx += kThreads) m = fmax(m, fabs(a.R[idx]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -813,7 +846,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
       block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring,
-                                                    P, full, empty, gctr);
+                                                    P, full, empty, gctr, gsi);
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
@@ -857,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
       block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                    full, empty, gctr);
+                                                    full, empty, gctr, gsi);
       cluster.sync();
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
