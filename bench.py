@@ -47,6 +47,10 @@ WORKLOAD = "trials64_n2000_fp32"
 # (G_off streamed from HBM every step)
 SINGLE_WORKLOADS = [WORKLOAD, "single_n200_fp64", "mri_n16384_fp16"]
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal)
+# mma.sync m16n8k16 FP16 (FP32 accumulate) throughput measured on GB300 with a
+# register-only loop, 152 CTAs x 8-16 warps: the ceiling of the legacy MMA path
+# the tensor-core Euler forms use (tcgen05 would be the 2.25 PFLOP/s nominal)
+MMA_SYNC_F16_TFLOPS = 600.0
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -592,6 +596,7 @@ def main():
         return 0
 
     x_hat, sigma_hat, energy, stats, _ = results
+    form = int(stats[10])  # 0 / 1 FMA forms, 2 tensor cores
     peaks, peak_kind = measured_peaks()
     ck = clocks.summary()
     n_launch_euler = args.steps * w["n_outer"]
@@ -602,7 +607,8 @@ def main():
         # every step streams the stored G_off (Npad x Npad FP16) from HBM
         npad = (w["N"] + 31) // 32 * 32
         bytes_per_launch = float(npad) * npad * 2 * w["n_steps"]
-        roof = {"kernel": "euler_kernel<__half, float, MR, STREAM=true, WIDE=true> (FP16 G_off streamed)",
+        roof = {"kernel": "euler_kernel<__half, float, MR, STREAM=true, WIDE=true, TC=%s> (FP16 G_off streamed%s)"
+                          % (("true", ", mma.sync") if form == 2 else ("false", ", packed FMAs")),
                 "bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9,
                 "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
                 "peak_source": f"HBM copy bandwidth ({peak_kind})", "bytes_per_launch": bytes_per_launch,
@@ -616,8 +622,23 @@ def main():
                                "the step latency is the figure of merit",
                 "us_per_step": per_launch_s * 1e6 / w["n_steps"], "flops_per_launch": flops_per_launch,
                 "traffic": None}
+    elif form == 2:
+        # FP32 problem on the tensor cores: three FP16 MMAs per tile on split
+        # operands; the algorithmic figure counts the FP32 products once
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        achieved = flops_per_launch / per_launch_s / 1e12
+        roof = {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true, TC=true> "
+                          "(FP32 G_off resident on chip, three FP16 mma.sync per tile)",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"dense BF16 (= FP16) tensor rate, cuBLAS sustained ({peak_kind}); "
+                               "the kernel is timed inside a seconds-long solve",
+                "flops_per_launch": flops_per_launch,
+                "mma_tflops_executed": 3.0 * achieved,
+                "mma_sync_peak_tflops": MMA_SYNC_F16_TFLOPS,
+                "frac_of_mma_sync_peak": 3.0 * achieved / MMA_SYNC_F16_TFLOPS,
+                "traffic": recorded_traffic()}
     else:
-        roof = {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true> "
+        roof = {"kernel": "euler_kernel<float, float, MR, STREAM=false, WIDE=true, TC=false> "
                           "(FP32 G_off resident on chip, packed FMAs)",
                 "bound": "alu", "achieved": flops_per_launch / per_launch_s / 1e12,
                 "peak": fp32_simt_peak_tflops(sm_mhz), "unit": "TFLOP/s",
