@@ -74,7 +74,7 @@ def fp32_simt_peak_tflops(sm_mhz, num_sms=152):
     return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-KERNEL_SOURCES = ["euler_kernel.cuh", "kernels_common.cuh", "tma.cuh", "common.cuh"]
+KERNEL_SOURCES = ["euler_kernel.cuh", "kernels_common.cuh", "mma.cuh", "tma.cuh", "common.cuh"]
 
 
 def kernel_source_sha256():
@@ -337,14 +337,28 @@ def run_batch(args):
     gbytes = sum(((i.N + 127) // 128 * 128) * ((i.N + 31) // 32 * 32) * 2.0 for i in insts) * steps_all
     tflops = flops / t_b / 1e12
     gbs = gbytes / t_b / 1e9
-    fpeak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
     hpeak = float(peaks.get("hbm_gbs", 6800.0))
-    hbm = gbs / hpeak > tflops / fpeak
-    roof = {"kernel": "euler_batch_kernel<__nv_bfloat16, float, 8, PAIR=true>", "bound": "hbm" if hbm else "alu",
-            "achieved": gbs if hbm else tflops, "peak": hpeak if hbm else fpeak,
-            "unit": "GB/s" if hbm else "TFLOP/s", "frac": max(gbs / hpeak, tflops / fpeak),
-            "alu_frac": tflops / fpeak, "hbm_frac": gbs / hpeak, "traffic": None,
-            "peak_source": f"FP32 FMA peak and HBM copy bandwidth ({peak_kind})"}
+    if int(res[0][3][10]) == 4:
+        # tensor-core form: two FP16/BF16 MMAs per product (the two parts of X) on
+        # the mma.sync path, against its measured ceiling; and the G_off bytes
+        mma = 2.0 * tflops
+        hbm = gbs / hpeak > mma / MMA_SYNC_F16_TFLOPS
+        roof = {"kernel": "euler_batch_kernel<__nv_bfloat16, float, 2, PAIR=false, TC=true>",
+                "bound": "hbm" if hbm else "tensor", "achieved": gbs if hbm else mma,
+                "peak": hpeak if hbm else MMA_SYNC_F16_TFLOPS, "unit": "GB/s" if hbm else "TFLOP/s",
+                "frac": max(gbs / hpeak, mma / MMA_SYNC_F16_TFLOPS),
+                "tensor_frac_of_mma_sync": mma / MMA_SYNC_F16_TFLOPS, "hbm_frac": gbs / hpeak,
+                "algorithmic_tflops": tflops, "traffic": None,
+                "peak_source": f"measured mma.sync FP16/BF16 ceiling and HBM copy bandwidth ({peak_kind})"}
+    else:
+        fpeak = fp32_simt_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+        hbm = gbs / hpeak > tflops / fpeak
+        roof = {"kernel": "euler_batch_kernel<__nv_bfloat16, float, 8, PAIR=true, TC=false>",
+                "bound": "hbm" if hbm else "alu", "achieved": gbs if hbm else tflops,
+                "peak": hpeak if hbm else fpeak, "unit": "GB/s" if hbm else "TFLOP/s",
+                "frac": max(gbs / hpeak, tflops / fpeak),
+                "alu_frac": tflops / fpeak, "hbm_frac": gbs / hpeak, "traffic": None,
+                "peak_source": f"FP32 FMA peak and HBM copy bandwidth ({peak_kind})"}
     v_b = len(insts) / t_b
     v_p = b["n_plain"] / plain_s
     Ns = [i.N for i in insts]

@@ -399,13 +399,17 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   ProblemDev& P0 = ps[0]->P;
   cudaStream_t stream = P0.stream;
   g_alloc_stream = stream;
+  const bool btc = batch_tensor_form(prm->precision, trials, prm->tensor_form);
+  if (prm->tensor_form == 2 && !btc)
+    return fail(CS_EINVAL, "tensor_form = 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
+                           "trials");
   int64_t nmax = 0;
   for (int i = 0; i < n; ++i) {
     ProblemDev& P = ps[i]->P;
     SolveDev& S = ps[i]->S;
     S.done = false;
     nmax = std::max(nmax, P.N);
-    CS_CUDA(launch_store_tiled(P, prm->precision), "store tiled coupling");
+    CS_CUDA(launch_store_tiled(P, prm->precision, btc), "store tiled coupling");
     if ((st = ensure_solve(P, S, *prm, trials, false)) != CS_OK) return st;
     CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), stream), "memset singular");
   }
@@ -517,7 +521,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
     ps[i]->S.done = true;
     ps[i]->S.plan_cluster = 0;
     ps[i]->S.plan_ctas = std::min(n, P0.num_sms);
-    ps[i]->S.plan_form = 3;
+    ps[i]->S.plan_form = btc ? 4 : 3;
   }
   return CS_OK;
 }
@@ -534,9 +538,6 @@ static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   if (stats_out) std::memcpy(stats_out, st, sizeof(st));
   const int err = (int)st[3];
   if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a grid barrier timed out");
-  if (err == DEV_RANGE)
-    return fail(CS_ECUDA, "device error word 4: an amplitude left the FP16 range of the tensor-core Euler form "
-                          "(set tensor_form = 1)");
   if (err != 0) return fail(CS_ECUDA, "device error word " + std::to_string(err));
   return st[2] != 0.0 ? CS_ESINGULAR : CS_OK;
 }

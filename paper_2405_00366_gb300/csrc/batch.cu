@@ -17,13 +17,16 @@
 // into a shared-memory ring with bulk copies (mbarrier full/empty handshake);
 // eight consumer warps accumulate the tile's rows of U = G_off X, then update
 // those rows of c and e (kept in global memory, L2-resident) and write their
-// next X.
+// next X.  With BF16 / FP16 storage and 8 or 16 trials the product runs on the
+// tensor cores instead (tile_product_tc): the tiles then hold G_off in the
+// MMA's A-operand order and X is stored in two 16-bit parts.
 #include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
 #include "kernels_common.cuh"
+#include "mma.cuh"
 #include "tma.cuh"
 
 namespace cs {
@@ -36,18 +39,29 @@ constexpr int kRT = 128;                       // rows per tile (16 per consumer
 constexpr int kKC = 32;                        // columns (k) per tile
 
 // Tiled, swizzled copy of G_off (see the file comment), divided by its row
-// scales when the storage type is row-scaled.
+// scales when the storage type is row-scaled.  frag = 1: inside each tile the
+// A-operand order of the tensor-core form, [row tile of 16][k half][lane][8].
 template <typename GT>
 __global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int nrt, int nkc,
-                                   const float* __restrict__ gscale) {
+                                   const float* __restrict__ gscale, int frag) {
   const size_t total = (size_t)nrt * nkc * kRT * kKC;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const size_t tile = idx / (kRT * kKC);
     const int within = (int)(idx % (kRT * kKC));
-    const int r = within / kKC, kp = within % kKC;
     const int rt = (int)(tile / nkc), kc = (int)(tile % nkc);
-    const int k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    int r, k;
+    if (frag) {
+      const int sub = within >> 8, L = (within >> 3) & 31, e = within & 7;
+      int rr, kk;
+      tc_arow_col(L, e, rr, kk);
+      r = (sub >> 1) * 16 + rr;
+      k = 16 * (sub & 1) + kk;
+    } else {
+      r = within / kKC;
+      const int kp = within % kKC;
+      k = 4 * ((kp >> 2) ^ (r & 7)) + (kp & 3);
+    }
     const int row = rt * kRT + r, col = kc * kKC + k;
     double v = (row < N && col < N && row != col) ? G[(size_t)row * N + col] : 0.0;
     if constexpr (row_scaled<GT>::value) v = row < N ? v / gscale[row] : 0.0;
@@ -103,6 +117,35 @@ __host__ __device__ __forceinline__ size_t b_part_bytes(int twp, size_t cbytes, 
   return align128((size_t)kRT * (pair ? 64 : twp) * cbytes);
 }
 
+// Producer of one row tile (lane 0 of the producer warp): its column tiles of
+// G_off, tps per ring slot, each slot followed by the matching k rows of X.
+template <typename GT, typename CT>
+__device__ __forceinline__ void produce_row_tile(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
+                                                 int rt, unsigned char* ring, size_t slot, uint64_t* full,
+                                                 uint64_t* empty, unsigned gctr, unsigned* issued) {
+  const int twp = a.twp, nkc = I.nkc;
+  const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
+  const unsigned xbytes = (unsigned)(kKC * twp * sizeof(CT));
+  const int nch = (nkc + a.tps - 1) / a.tps;
+  fence_proxy_async_global();
+  const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
+      set_error(a.err, DEV_TIMEOUT);
+      break;
+    }
+    const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
+    unsigned char* dst = ring + (size_t)s * slot;
+    issued[s] = g + 1;
+    mbar_arrive_expect_tx(full + s, (unsigned)(nt * (gtile + xbytes)));
+    bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
+    bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
+  }
+}
+
 // Partial-free product of one row tile: U[r][tt] = sum_k G_off[rt*kRT + r][k] X[k][tt]
 // for r < kRT, written to P (kRT x twp).  Lane layout: CG column groups of four
 // trials, RG row groups, KG k groups (CG RG KG = 32), MR = 16 / RG rows per lane.
@@ -113,29 +156,10 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
-  const unsigned xbytes = (unsigned)(kKC * twp * sizeof(CT));
   const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
-    if (l == 0) {
-      fence_proxy_async_global();
-      const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
-      for (int ci = 0; ci < nch; ++ci) {
-        const unsigned g = gctr + ci;
-        const int s = (int)(g % a.slots);
-        const unsigned u = g / a.slots;
-        if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
-          set_error(a.err, DEV_TIMEOUT);
-          break;
-        }
-        const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
-        unsigned char* dst = ring + (size_t)s * slot;
-        issued[s] = g + 1;
-        mbar_arrive_expect_tx(full + s, (unsigned)(nt * (gtile + xbytes)));
-        bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
-        bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
-      }
-    }
+    if (l == 0) produce_row_tile<GT, CT>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
     gctr += nch;
     return true;
   }
@@ -222,29 +246,10 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
-  const unsigned xbytes = (unsigned)(kKC * twp * sizeof(float));
   const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
-    if (l == 0) {
-      fence_proxy_async_global();
-      const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
-      for (int ci = 0; ci < nch; ++ci) {
-        const unsigned g = gctr + ci;
-        const int s = (int)(g % a.slots);
-        const unsigned u = g / a.slots;
-        if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
-          set_error(a.err, DEV_TIMEOUT);
-          break;
-        }
-        const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
-        unsigned char* dst = ring + (size_t)s * slot;
-        issued[s] = g + 1;
-        mbar_arrive_expect_tx(full + s, (unsigned)(nt * (gtile + xbytes)));
-        bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
-        bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
-      }
-    }
+    if (l == 0) produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
     gctr += nch;
     return true;
   }
@@ -316,6 +321,105 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
   return ok;
 }
 
+// Tensor-core form of one row tile (BF16 / FP16 G_off, FP32 compute, twp = 8 NT
+// trials): the ring slots hold G_off in A-operand order and X in two 16-bit
+// parts ([k / 16][part][t][k % 16], scaled by xsc); warp w takes rows 16 w ..
+// 16 w + 15 of the row tile for every trial and every k, two MMAs per
+// 16 x 8 x 16 tile (hi and lo of X).  The MMAs of one ring slot chain in
+// accumulators that start from zero and are then added to the FP32 sums
+// (round to nearest).  P (kRT x twp) receives U, scaled back by xsi.
+template <typename GT, int NT>
+__device__ __forceinline__ bool tile_product_tc(const BArgs<float>& a, const BInst<float>& I,
+                                                const float* __restrict__ X, int rt, unsigned char* ring,
+                                                size_t slot, float* P, uint64_t* full, uint64_t* empty,
+                                                unsigned& gctr, unsigned* issued, float xsi) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int twp = a.twp, nkc = I.nkc;
+  const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
+  const int nch = (nkc + a.tps - 1) / a.tps;
+  bool ok = true;
+  if (w == kBWarps) {
+    if (l == 0) produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
+    gctr += nch;
+    return true;
+  }
+  constexpr int kTileU4 = kRT * kKC * 2 / 16;  // 16-byte words per column tile
+  float acc[NT][2][4];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[nt][p][q] = 0.f;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    if (ok && !mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+      ok = false;
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+    }
+    if (ok) {
+      const uint4* gt = reinterpret_cast<const uint4*>(ring + (size_t)s * slot) + w * 64 + l;
+      const uint2* xs = reinterpret_cast<const uint2*>(ring + (size_t)s * slot + a.tps * gtile) + l;
+      const int nkb = min(a.tps, nkc - ci * a.tps) * (kKC / 16);
+      float d[NT][2][4];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) d[nt][p][q] = 0.f;
+#pragma unroll 1
+      for (int kb = 0; kb < nkb; ++kb) {
+        // column tile kb / 2 of the slot, k half kb % 2, row tile w
+        const uint4 av = gt[(size_t)(kb >> 1) * kTileU4 + (kb & 1) * 32];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma16816<GT>(d[nt][0], av, xs[((size_t)(2 * kb) * twp + nt * 8) * 4]);
+          mma16816<GT>(d[nt][1], av, xs[((size_t)(2 * kb + 1) * twp + nt * 8) * 4]);
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[nt][p][q] += d[nt][p][q];
+    }
+    __syncwarp();
+    if (l == 0) mbar_arrive(empty + s);
+  }
+  gctr += nch;
+  const float wlo = 1.0f / (float)(1 << tc_type<GT>::kLoShift);
+  const int r = w * 16 + (l >> 2), c = 2 * (l & 3);
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const float* h = acc[nt][0];
+    const float* o = acc[nt][1];
+    *reinterpret_cast<float2*>(P + (size_t)r * twp + nt * 8 + c) =
+        make_float2(fmaf(wlo, o[0], h[0]) * xsi, fmaf(wlo, o[1], h[1]) * xsi);
+    *reinterpret_cast<float2*>(P + (size_t)(r + 8) * twp + nt * 8 + c) =
+        make_float2(fmaf(wlo, o[2], h[2]) * xsi, fmaf(wlo, o[3], h[3]) * xsi);
+  }
+  return ok;
+}
+
+// Store X[k][t] = v in the layout of the launch's product form; the
+// tensor-core form stores two 16-bit parts (X scaled so that |X| <= |c|).
+template <typename GT, typename CT, bool PAIR, bool TC>
+__device__ __forceinline__ void bxput(CT* X, int k, int t, int twp, CT v) {
+  if constexpr (TC) {
+    GT* h = reinterpret_cast<GT*>(X);
+    const GT hi = GT(v);
+    const float hf = float(hi);
+    h[tc_xidx(k, t, twp, 0)] = hi;
+    h[tc_xidx(k, t, twp, 1)] = GT((v - hf) * (float)(1 << tc_type<GT>::kLoShift));
+  } else {
+    X[xoff<PAIR>(k, t, twp)] = v;
+  }
+}
+
 // U of row rl (tile-local) and trial t: the partials of the row tile, summed
 // over the k-warp planes of the wide form (one plane otherwise).
 template <typename CT, bool PAIR>
@@ -331,11 +435,13 @@ __device__ __forceinline__ CT tile_sum(const CT* P, int rl, int t, int twp) {
 }
 
 // Product of one row tile in the form the launch was built for.
-template <typename GT, typename CT, int MR, bool PAIR>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC>
 __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
                                                  int rt, unsigned char* ring, size_t slot, CT* P, uint64_t* full,
-                                                 uint64_t* empty, unsigned& gctr, unsigned* issued) {
-  if constexpr (PAIR) {
+                                                 uint64_t* empty, unsigned& gctr, unsigned* issued, float xsi) {
+  if constexpr (TC) {
+    return tile_product_tc<GT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued, xsi);
+  } else if constexpr (PAIR) {
     return tile_product_pair<GT>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
   } else {
     return tile_product<GT, CT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
@@ -343,11 +449,30 @@ __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst
 }
 
 // One CIM run of problem I.  Returns false (in every thread) if a wait timed out.
-template <typename GT, typename CT, int MR, bool PAIR>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC>
 __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned char* ring, size_t slot, CT* P,
                              uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued) {
   const int T = a.T, twp = a.twp, N = I.N;
   const size_t NT = (size_t)N * T;
+  // tensor-core form: X scaled by 2^-e with max |R| < 2^e (exact; U scaled back)
+  CT xsc = CT(1);
+  float xsi = 1.f;
+  if constexpr (TC) {
+    double m = 0.0;
+    for (size_t o = threadIdx.x; o < NT; o += kBThreads) m = fmax(m, fabs(I.R[o]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    double* red = reinterpret_cast<double*>(P);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    for (int i = 0; i < kBThreads / 32; ++i) m = fmax(m, red[i]);
+    __syncthreads();
+    int ex = 0;
+    if (m > 0.0 && m <= 1e30) frexp(m, &ex);
+    ex = max(-100, min(100, ex));
+    xsc = CT(ldexp(1.0, -ex));
+    xsi = (float)ldexp(1.0, ex);
+  }
   CT* c = I.state;
   CT* e = I.state + NT;
   CT* b = I.state + 2 * NT;
@@ -358,13 +483,13 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   if (a.field == CS_FIELD_CN) {
     for (size_t idx = threadIdx.x; idx < NT; idx += kBThreads) {
       const int r = (int)(idx / T), t = (int)(idx % T);
-      I.X0[xoff<PAIR>(r, t, twp)] = CT(I.R[idx]);
+      bxput<GT, CT, PAIR, TC>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
     }
     fence_proxy_async_global();
     __syncthreads();
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
       ok = __syncthreads_and(
-          row_tile_product<GT, CT, MR, PAIR>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued));
+          row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued, xsi));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int r = rt * kRT + idx / T, t = idx % T;
         if (r >= N) continue;
@@ -387,7 +512,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     c[o] = c0;
     e[o] = CT(1);
     const CT Rr = CT(I.R[o]);
-    I.X1[xoff<PAIR>(r, t, twp)] = (a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0));
+    bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp, ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
   }
   fence_proxy_async_global();
   __syncthreads();
@@ -399,8 +524,8 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
     const bool last = (n + 1 == a.n_steps);
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
-      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
-                                                                issued));
+      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
+                                                                    issued, xsi));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int rl = idx / T, t = idx % T, r = rt * kRT + rl;
         if (r >= N) continue;
@@ -414,7 +539,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
         c[o] = cn;
         e[o] = en;
-        Xn[xoff<PAIR>(r, t, twp)] = (a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0));
+        bxput<GT, CT, PAIR, TC>(Xn, r, t, twp, ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
         if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
       }
       __syncthreads();
@@ -426,7 +551,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   return ok;
 }
 
-template <typename GT, typename CT, int MR, bool PAIR>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC>
 __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT), a.tps);
@@ -454,7 +579,7 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
     __syncthreads();
     if (qi >= a.n) break;
     const BInst<CT> I = a.insts[a.order[qi]];
-    ok = run_instance<GT, CT, MR, PAIR>(a, I, ring, slot, P, full, empty, gctr, issued);
+    ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, ring, slot, P, full, empty, gctr, issued);
   }
   // After a timeout, let any copy still in flight land before the CTA exits.
   if (!ok && threadIdx.x == kBWarps * 32) {
@@ -463,10 +588,10 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
   }
 }
 
-template <typename GT, typename CT, int MR, bool PAIR>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC = false>
 cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
-  auto fn = euler_batch_kernel<GT, CT, MR, PAIR>;
+  auto fn = euler_batch_kernel<GT, CT, MR, PAIR, TC>;
   int optin = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -513,13 +638,20 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.timeout_cycles = L.timeout_cycles;
   e = cudaMemsetAsync(L.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  euler_batch_kernel<GT, CT, MR, PAIR><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
+  euler_batch_kernel<GT, CT, MR, PAIR, TC><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename GT, typename CT>
 cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
+  if constexpr (tc_type<GT>::value && std::is_same<CT, float>::value) {
+    // the tensor-core form (batch_tensor_form): MR carries the n-tiles of 8 trials
+    if (batch_tensor_form(L.prm->precision, L.T, L.prm->tensor_form)) {
+      if (twp == 8) return launch_batch_typed<GT, CT, 1, false, true>(L, st);
+      return launch_batch_typed<GT, CT, 2, false, true>(L, st);
+    }
+  }
   if constexpr (std::is_same<CT, float>::value) {
     // the wide form (packed FMAs) for trial blocks of 8, 16, 32 or 64
     if (twp == 8 || twp == 16 || twp == 32 || twp == 64) return launch_batch_typed<GT, CT, 8, true>(L, st);
@@ -546,8 +678,12 @@ int64_t tiled_elems(int64_t N, int64_t Npad) {
   return nrt * kRT * Npad;
 }
 
-cudaError_t launch_store_tiled(ProblemDev& P, int precision) {
-  if (P.gt_prec == precision && P.Gt) return cudaSuccess;
+bool batch_tensor_form(int precision, int trials, int tensor_form) {
+  return tensor_form != 1 && (precision == CS_P_BF16 || precision == CS_P_FP16) && (trials == 8 || trials == 16);
+}
+
+cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag) {
+  if (P.gt_prec == precision && P.Gt && P.gt_frag == (int)frag) return cudaSuccess;
   if (P.Gt) { dev_free(P.Gt, P.stream); P.Gt = nullptr; P.gt_prec = -1; }
   const size_t gb = storage_bytes(precision);
   const int64_t elems = tiled_elems(P.N, P.Npad);
@@ -557,23 +693,26 @@ cudaError_t launch_store_tiled(ProblemDev& P, int precision) {
   const int blocks = P.num_sms * 4;
   float* sc = P.gscale;
   switch (precision) {
-    case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc, sc); break;
-    case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc, sc); break;
+    case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc, sc, 0); break;
+    case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc, sc, 0); break;
     case CS_P_BF16:
-      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc, sc);
+      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc, sc, (int)frag);
       break;
     case CS_P_FP16:
-      store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc, sc);
+      store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc, sc, (int)frag);
       break;
     case CS_P_FP8:
       if ((e = ensure_row_scales(P)) != cudaSuccess) return e;
       store_tiled_kernel<__nv_fp8_e4m3><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_fp8_e4m3*)P.Gt, N, nrt, nkc,
-                                                                      P.gscale);
+                                                                      P.gscale, 0);
       break;
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();
-  if (e == cudaSuccess) P.gt_prec = precision;
+  if (e == cudaSuccess) {
+    P.gt_prec = precision;
+    P.gt_frag = (int)frag;
+  }
   return e;
 }
 

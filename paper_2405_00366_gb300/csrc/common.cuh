@@ -33,7 +33,7 @@ template <> __device__ __forceinline__ float widen<float, float>(float v) { retu
 
 // ------------------------------------------------------------------ error word
 // Device error codes written into the per-solve error word (first writer wins).
-enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NONFINITE = 2, DEV_BADARG = 3, DEV_RANGE = 4 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NONFINITE = 2, DEV_BADARG = 3 };
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 

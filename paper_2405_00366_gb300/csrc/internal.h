@@ -40,7 +40,7 @@ struct ProblemDev {
   void* Gs = nullptr;     // Npad x Npad, G in storage precision with zero diagonal and zero padding
   int gs_prec = -1;       // precision held in Gs
   void* Gt = nullptr;     // G_off in storage precision, tiled for streaming (batched solves)
-  int gt_prec = -1;
+  int gt_prec = -1, gt_frag = 0;
   float* gscale = nullptr; // N row scales of G_off for FP8 storage (largest |G_off[r][k]| / 448)
   void* Gt2 = nullptr;    // G_off tiles of a streaming Euler plan (see euler.cu)
   int gt2_prec = -1, gt2_rpc = 0, gt2_rpcpad = 0, gt2_nc = 0, gt2_frag = 0;
@@ -118,7 +118,10 @@ struct BatchLaunch {
 };
 size_t batch_inst_bytes();
 void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst);
-cudaError_t launch_store_tiled(ProblemDev& P, int precision);
+cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag);
+// Whether a batch of this precision and trial count runs the batched kernel's
+// tensor-core form (BF16 / FP16 storage, 8 or 16 trials, tensor_form != 1).
+bool batch_tensor_form(int precision, int trials, int tensor_form);
 cudaError_t ensure_row_scales(ProblemDev& P);
 size_t storage_bytes(int precision);
 cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);

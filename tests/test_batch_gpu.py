@@ -25,8 +25,8 @@ def oracle_params(w):
     return oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS})
 
 
-def run_batch(insts, w, trials):
-    prm = cs.params_from_workload(w)
+def run_batch(insts, w, trials, **over):
+    prm = cs.params_from_workload(w, **over)
     hs = [cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam) for i in insts]
     try:
         cs.cs_solve_batch(hs, prm, trials)
@@ -116,14 +116,37 @@ def test_reduced_precision_support_and_rmse(precision):
     assert abs(oracle.rmse(g[0]["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
 
 
+@pytest.mark.parametrize("precision,T", [("bf16", 16), ("fp16", 8)])
+def test_batch_tensor_cores_support_and_rmse(precision, T):
+    """The batched kernel's tensor-core form (16-bit G_off, 8 or 16 trials, stats[10]
+    = 4) against the FP64 oracle with the reduced-precision gate (final support
+    identical, RMSE within 1e-3), and against the same batch on FMAs
+    (tensor_form = 1): identical supports."""
+    w = cs_inputs.workload("trials64_n2000_fp32", N=500, M=300, nnz=50, n_outer=4, n_steps=800, precision=precision)
+    inst = cs_inputs.workload_instance(w)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T)
+    g = run_batch([inst], w, T)[0]
+    f = run_batch([inst], w, T, tensor_form=1)[0]
+    assert g["stats"][10] == 4 and f["stats"][10] == 3
+    np.testing.assert_array_equal(g["sigma"], r["sigma"])
+    assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+    np.testing.assert_array_equal(g["sigma"], f["sigma"])
+
+
 def test_batch_uneven_bf16_shapes():
     """Uneven instances in the shape of the batched workload (alpha in {0.3, 0.5, 0.7},
-    a in {0.05, 0.1, 0.2}, 16 trials, BF16), scaled down: every result is a valid
-    refit (zero gradient on its support) and its energy is the recomputed objective."""
+    a in {0.05, 0.1, 0.2}, 16 trials, BF16), scaled down (sizes with partial ring
+    slots): every result is a valid refit (zero gradient on its support) and its
+    energy is the recomputed objective; the tensor-core form (the default here) and
+    the FMA form agree on the supports up to 1% of N."""
     insts = cs_inputs.uneven_batch(8, 256, 700, [0.3, 0.5, 0.7], [0.05, 0.1, 0.2], 0.01, 0.03, seed=3)
+    assert any((i.N + 31) // 32 % 4 for i in insts)
     w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300, precision="bf16", seed=1)
     g = run_batch(insts, w, 16)
-    for inst, res in zip(insts, g):
+    f = run_batch(insts, w, 16, tensor_form=1)
+    for inst, res, fma in zip(insts, g, f):
+        assert res["stats"][10] == 4 and fma["stats"][10] == 3
+        assert oracle.hamming_loss(res["sigma"], fma["sigma"]) <= 0.01
         S = np.flatnonzero(res["sigma"])
         resid = inst.y - inst.A[:, S] @ res["x_hat"][S]
         assert res["energy"] == pytest.approx(0.5 * resid @ resid + inst.lam * S.size, rel=1e-10)
