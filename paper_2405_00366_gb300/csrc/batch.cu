@@ -117,19 +117,20 @@ __host__ __device__ __forceinline__ size_t b_part_bytes(int twp, size_t cbytes, 
   return align128((size_t)kRT * (pair ? 64 : twp) * cbytes);
 }
 
-// Producer of one row tile (lane 0 of the producer warp): its column tiles of
-// G_off, tps per ring slot, each slot followed by the matching k rows of X.
+// Producer of one row tile (lane 0 of the producer warp): chunks [ci0, ci1) of
+// its column tiles of G_off, tps per ring slot, each slot followed by the
+// matching k rows of X; chunk ci is ring use gctr + ci.
 template <typename GT, typename CT>
 __device__ __forceinline__ void produce_row_tile(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
                                                  int rt, unsigned char* ring, size_t slot, uint64_t* full,
-                                                 uint64_t* empty, unsigned gctr, unsigned* issued) {
+                                                 uint64_t* empty, unsigned gctr, unsigned* issued, int ci0,
+                                                 int ci1) {
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
   const unsigned xbytes = (unsigned)(kKC * twp * sizeof(CT));
-  const int nch = (nkc + a.tps - 1) / a.tps;
   fence_proxy_async_global();
   const GT* gsrc = reinterpret_cast<const GT*>(I.Gt) + (size_t)rt * nkc * kRT * kKC;
-  for (int ci = 0; ci < nch; ++ci) {
+  for (int ci = ci0; ci < ci1; ++ci) {
     const unsigned g = gctr + ci;
     const int s = (int)(g % a.slots);
     const unsigned u = g / a.slots;
@@ -159,7 +160,7 @@ __device__ __forceinline__ bool tile_product(const BArgs<CT>& a, const BInst<CT>
   const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
-    if (l == 0) produce_row_tile<GT, CT>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
+    if (l == 0) produce_row_tile<GT, CT>(a, I, X, rt, ring, slot, full, empty, gctr, issued, 0, nch);
     gctr += nch;
     return true;
   }
@@ -249,7 +250,7 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
   const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
-    if (l == 0) produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
+    if (l == 0) produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued, 0, nch);
     gctr += nch;
     return true;
   }
@@ -327,19 +328,31 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
 // 16 w + 15 of the row tile for every trial and every k, two MMAs per
 // 16 x 8 x 16 tile (hi and lo of X).  The MMAs of one ring slot chain in
 // accumulators that start from zero and are then added to the FP32 sums
-// (round to nearest).  P (kRT x twp) receives U, scaled back by xsi.
+// (round to nearest).  P (kRT x twp) receives U, scaled back by xsi.  The
+// producer issues the next row tile's first chunks before the CTA-wide sync
+// that ends this product (pre counts them; every row tile of a pass reads the
+// same X, so only the pass's last row tile issues none).
 template <typename GT, int NT>
 __device__ __forceinline__ bool tile_product_tc(const BArgs<float>& a, const BInst<float>& I,
                                                 const float* __restrict__ X, int rt, unsigned char* ring,
                                                 size_t slot, float* P, uint64_t* full, uint64_t* empty,
-                                                unsigned& gctr, unsigned* issued, float xsi) {
+                                                unsigned& gctr, unsigned* issued, float xsi, int& pre) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int twp = a.twp, nkc = I.nkc;
   const size_t gtile = (size_t)kRT * kKC * sizeof(GT);
   const int nch = (nkc + a.tps - 1) / a.tps;
   bool ok = true;
   if (w == kBWarps) {
-    if (l == 0) produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued);
+    if (l == 0) {
+      // the chunks not issued ahead, then the first ring-full of the next row
+      // tile of this pass (same X), whose copies then land during the update
+      produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued, pre, nch);
+      pre = 0;
+      if (rt + 1 < I.nrt) {
+        pre = min(a.slots, nch);
+        produce_row_tile<GT, float>(a, I, X, rt + 1, ring, slot, full, empty, gctr + nch, issued, 0, pre);
+      }
+    }
     gctr += nch;
     return true;
   }
@@ -438,9 +451,10 @@ __device__ __forceinline__ CT tile_sum(const CT* P, int rl, int t, int twp) {
 template <typename GT, typename CT, int MR, bool PAIR, bool TC>
 __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
                                                  int rt, unsigned char* ring, size_t slot, CT* P, uint64_t* full,
-                                                 uint64_t* empty, unsigned& gctr, unsigned* issued, float xsi) {
+                                                 uint64_t* empty, unsigned& gctr, unsigned* issued, float xsi,
+                                                 int& pre) {
   if constexpr (TC) {
-    return tile_product_tc<GT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued, xsi);
+    return tile_product_tc<GT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued, xsi, pre);
   } else if constexpr (PAIR) {
     return tile_product_pair<GT>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
   } else {
@@ -454,6 +468,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
                              uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued) {
   const int T = a.T, twp = a.twp, N = I.N;
   const size_t NT = (size_t)N * T;
+  int pre = 0;  // producer: chunks of the next row tile already issued
   // tensor-core form: X scaled by 2^-e with max |R| < 2^e (exact; U scaled back)
   CT xsc = CT(1);
   float xsi = 1.f;
@@ -489,7 +504,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     __syncthreads();
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
       ok = __syncthreads_and(
-          row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued, xsi));
+          row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued, xsi, pre));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int r = rt * kRT + idx / T, t = idx % T;
         if (r >= N) continue;
@@ -525,7 +540,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     const bool last = (n + 1 == a.n_steps);
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
       ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
-                                                                    issued, xsi));
+                                                                    issued, xsi, pre));
       // the row tile's update, kU elements per thread at a time: every load of
       // the state (global memory, L2-resident) is issued before the first
       // update, so the L2 latency is paid once per kU elements (measured on
