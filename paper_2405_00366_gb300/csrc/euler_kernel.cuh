@@ -458,8 +458,8 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
 
 template <typename GT, int MR>
 __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const float* __restrict__ Xblk, int twp,
-                                            int k0, int klen, int cl, unsigned char* ring, uint64_t* full,
-                                            uint64_t* empty, unsigned& gctr) {
+                                            int k0, int klen, int cl, unsigned char* ring, float* P,
+                                            uint64_t* full, uint64_t* empty, unsigned& gctr) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
@@ -518,9 +518,13 @@ __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const flo
     if (l == 0) mbar_arrive(empty + s);
   }
   gctr += nch;
-  // every consumer warp is done with the ring before it holds partials
-  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
-  float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  // one k-warp: the partials go straight to P; else every consumer warp is done
+  // with the ring before it holds the k-warps' partials
+  float* dst = P;
+  if (WK > 1) {
+    asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+    dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  }
   const float wlo = 1.0f / (float)(1 << tc_type<GT>::kLoShift);
   const int gq = l >> 2, c = 2 * (l & 3);
 #pragma unroll
@@ -552,8 +556,8 @@ __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const flo
 template <int MR>
 __device__ __forceinline__ void h3_partials(const EulerArgs<float>& a, const float* __restrict__ Gsm,
                                             const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
-                                            unsigned char* ring, uint64_t* full, uint64_t* empty, unsigned& gctr,
-                                            float gsi) {
+                                            unsigned char* ring, float* P, uint64_t* full, uint64_t* empty,
+                                            unsigned& gctr, float gsi) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
@@ -620,9 +624,13 @@ __device__ __forceinline__ void h3_partials(const EulerArgs<float>& a, const flo
     if (l == 0) mbar_arrive(empty + s);
   }
   gctr += nch;
-  // every consumer warp is done with the ring before it holds partials
-  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
-  float* dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  // one k-warp: the partials go straight to P; else every consumer warp is done
+  // with the ring before it holds the k-warps' partials
+  float* dst = P;
+  if (WK > 1) {
+    asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+    dst = reinterpret_cast<float*>(ring) + (size_t)kw * a.RPC_pad * twp;
+  }
   const float wlo = 1.0f / 2048.0f;
   const int gq = l >> 2, i4 = l & 3;
 #pragma unroll
@@ -706,11 +714,13 @@ __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT*
                                                unsigned& gctr, float gsi) {
   if constexpr (TC) {
     if constexpr (tc_type<GT>::value) {
-      tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+      tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, P, full, empty, gctr);
     } else {
-      h3_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, gsi);
+      h3_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, P, full, empty, gctr, gsi);
     }
-    sum_k_warps(a, ring, P, twp, nrows);
+    // (with one k-warp the partials are already in P; the cluster barrier that
+    // follows orders them before any reader)
+    if (a.WK > 1) sum_k_warps(a, ring, P, twp, nrows);
   } else if constexpr (WIDE) {
     wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
     sum_k_warps(a, ring, P, twp, nrows);
