@@ -94,7 +94,8 @@ def test_trajectory_fp64_single():
 @pytest.mark.parametrize("field,form", [("cn", 1), ("bn", 1), ("cn", 2), ("bn", 2)])
 def test_trajectory_fp32_trials64(field, form):
     """The N = 2000, M = 1200, 64-trial workload: the first 200 Euler steps of every
-    trial, with FP32 FMAs (tensor_form = 1) and with 3xTF32 tensor-core MMAs (2)."""
+    trial, with FP32 FMAs (tensor_form = 1) and with the FP32 tensor-core form (2:
+    three FP16 MMAs on split operands)."""
     w = cs_inputs.workload("trials64_n2000_fp32", n_outer=1, field=field, tensor_form=form)
     inst = cs_inputs.workload_instance(w)
     g = gpu_solve(inst, w, 64, record_steps=200)
@@ -145,8 +146,9 @@ def test_solve_ragged(precision, field):
 
 @pytest.mark.parametrize("trials,cluster,field", [(16, 0, "cn"), (32, 2, "bn"), (64, 1, "cn"), (64, 8, "bn")])
 def test_solve_ragged_fp32_tensor_cores(trials, cluster, field):
-    """The FP32 tensor-core form (3xTF32 MMAs, tensor_form = 2) on N = 333 (ragged
-    row tiles and k blocks): whole solves against the oracle to the FP32 tolerances."""
+    """The FP32 tensor-core form (three FP16 MMAs on split operands, tensor_form = 2)
+    on N = 333 (ragged row tiles and k blocks): whole solves against the oracle to
+    the FP32 tolerances."""
     inst = cs_inputs.random_instance(333, 211, 30, 0.01, 0.04, seed=7)
     w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=4, n_steps=600, precision="fp32", field=field,
              seed=11, tensor_form=2, cluster_size=cluster)
