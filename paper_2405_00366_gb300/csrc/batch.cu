@@ -539,14 +539,66 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
     const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
     const bool last = (n + 1 == a.n_steps);
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
+      constexpr int kU = 8;
+      const int ne = kRT * T;
+      if constexpr (TC) {
+        // Tensor-core form (T <= 16, so the kRT T elements of a row tile are at
+        // most kU per consumer thread): each consumer thread loads the state of
+        // its kU elements of the row tile
+        // before the product and updates them after it, so the loads' latency
+        // (the state is in global memory) is hidden behind the product
+        // (measured on GB300: the update had been 45% of the kernel's time).
+        constexpr int kUT = kBWarps * 32;
+        const int tid = threadIdx.x;
+        CT cv[kU], ev[kU], bv[kU];
+        double Rd[kU];
+        if (tid < kUT) {
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = u * kUT + tid;
+            const int r = rt * kRT + idx / T;
+            cv[u] = ev[u] = bv[u] = CT(0);
+            Rd[u] = 0.0;
+            if (idx < ne && r < N) {
+              const size_t o = (size_t)r * T + idx % T;
+              cv[u] = c[o];
+              ev[u] = e[o];
+              bv[u] = b[o];
+              Rd[u] = I.R[o];
+            }
+          }
+        }
+        ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty,
+                                                                      gctr, issued, xsi, pre));
+        if (tid < kUT) {
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = u * kUT + tid;
+            const int rl = idx / T, t = idx % T, r = rt * kRT + rl;
+            if (idx < ne && r < N) {
+              const size_t o = (size_t)r * T + t;
+              const CT Rr = CT(Rd[u]), cc = cv[u], ee = ev[u];
+              const CT f = wcoef * Rr * tile_sum<CT, PAIR>(P, rl, t, twp) + bv[u];
+              const CT c2 = cc * cc;
+              const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
+              const CT en = ee + dt * (-beta * (c2 - tau) * ee);
+              c[o] = cn;
+              e[o] = en;
+              bxput<GT, CT, PAIR, TC>(Xn, r, t, twp,
+                                      ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
+              if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
+            }
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
                                                                     issued, xsi, pre));
       // the row tile's update, kU elements per thread at a time: every load of
       // the state (global memory, L2-resident) is issued before the first
       // update, so the L2 latency is paid once per kU elements (measured on
       // GB300: 9% less time per batch than one element at a time)
-      constexpr int kU = 8;
-      const int ne = kRT * T;
       for (int base = 0; base < ne; base += kU * kBThreads) {
         CT cv[kU], ev[kU], bv[kU], Rv[kU], Uv[kU];
 #pragma unroll
