@@ -87,6 +87,11 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
 //    of HBM), plus the k-warp reduction;
 //  * narrow split (every other case; measured at about 45% of FFMA issue):
 //    FMAs at 128 per clock / 0.45, or streamed G bytes;
+//  * tensor-core forms (tensor_form != 1): streamed 16-bit G_off with 8 trials,
+//    the larger of two m16n8k16 MMAs per 16 x 16 tile at one per 2 clocks and
+//    the streamed G bytes; resident FP32 G_off with blocks of 16/32/64 trials,
+//    three MMAs per 16 x 8 x 16 tile at one per 2 clocks and 70% of that
+//    (mma.sync rates measured on GB300), plus the k-warp reduction;
 // each plus X bytes at 44 per clock (measured: the X traffic of a step adds to
 // its time rather than overlapping the product), a fixed cost per cluster rank
 // for the reduction through distributed shared memory, and the step barrier: a
