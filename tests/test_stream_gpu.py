@@ -8,6 +8,7 @@ import torch
 import cs_inputs
 import oracle
 from paper_2405_00366_gb300 import cs
+from storage_rounding import round_to_storage
 
 pytestmark = pytest.mark.gpu
 
@@ -80,15 +81,6 @@ def test_streamed_bf16_autotuned_matches_resident():
 
 
 # ------------------------------------------------------------ tensor-core form
-def round_to_storage(G, precision):
-    """G rounded to nearest, ties to even, in the 16-bit storage type (as the
-    library stores G_off)."""
-    if precision == "fp16":
-        return G.astype(np.float16).astype(np.float64)
-    m, e = np.frexp(G)  # G = m 2^e, 1/2 <= |m| < 1; BF16 keeps 8 significant bits
-    return np.ldexp(np.rint(m * 256.0), e - 8)
-
-
 def rel_traj_err(c, ref):
     """Per-step ||c - ref||_inf / max(||ref||_inf, 1e-2)."""
     num = np.abs(c - ref).reshape(c.shape[0], -1).max(axis=1)
