@@ -164,6 +164,8 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->stream_g == 1 && p->precision == CS_P_FP64) return fail(CS_EINVAL, "FP64 G_off is never streamed");
   if (p->autotune != 0 && p->autotune != 1) return fail(CS_EINVAL, "autotune must be 0 or 1");
   if (p->tensor_form < 0 || p->tensor_form > 2) return fail(CS_EINVAL, "tensor_form must be 0, 1 or 2");
+  if (p->tensor_form == 2 && (p->precision == CS_P_FP64 || p->precision == CS_P_FP8))
+    return fail(CS_EINVAL, "tensor_form = 2: no tensor-core form for FP64 or FP8 storage");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -368,7 +370,9 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     CS_CUDA(mark(p, TM_EULER, true), "event");
     cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
     if (e == cudaErrorInvalidConfiguration)
-      return fail(CS_EINVAL, "N too large for the on-chip Euler kernel at this precision");
+      return fail(CS_EINVAL, prm->tensor_form == 2
+                                 ? "tensor_form = 2: no tensor-core work split for this shape and trial count"
+                                 : "N too large for the on-chip Euler kernel at this precision");
     if (e != cudaSuccess)
       return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
     CS_CUDA(mark(p, TM_EULER, false), "event");

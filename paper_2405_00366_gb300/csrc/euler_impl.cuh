@@ -278,7 +278,11 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
       }
     }
   }
-  if (!found) { g_where = "make_plan: no work split fits"; return cudaErrorInvalidConfiguration; }
+  if (!found) {
+    g_where = tensor_form == 2 ? "make_plan: no tensor-core work split for this shape (tensor_form = 2)"
+                               : "make_plan: no work split fits";
+    return cudaErrorInvalidConfiguration;
+  }
   *out = bp;
   if (cands) std::stable_sort(cands->begin(), cands->end(), [](const std::pair<double, Plan>& x,
                                                                 const std::pair<double, Plan>& y) {

@@ -154,3 +154,25 @@ def test_mri_shaped_small_tensor_cores():
         assert (g["stats"][10] == 2) == (tf == 2)
         assert oracle.hamming_loss(g["sigma"], r["sigma"]) <= 0.01
         assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
+
+
+def test_tensor_form_2_where_no_tensor_form_applies():
+    """tensor_form = 2 asks for the tensor-core form only: FP64 storage, an FP32
+    solve with 5 trials (blocks narrower than 16) and a BF16 batch with 4 trials
+    have none, and each is refused with CS_EINVAL (no silent fallback)."""
+    inst = cs_inputs.random_instance(64, 40, 6, 0.0, 0.05, seed=1)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=10)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        for precision, T in (("fp64", 1), ("fp32", 5)):
+            with pytest.raises(cs.CSError) as ei:
+                cs.cs_solve(h, cs.params_from_workload(w, precision=precision, tensor_form=2), T)
+            assert ei.value.status == cs.CS_EINVAL
+        with pytest.raises(cs.CSError) as ei:
+            cs.cs_solve_batch([h], cs.params_from_workload(w, precision="bf16", tensor_form=2), 4)
+        assert ei.value.status == cs.CS_EINVAL
+        # the problem stays usable: the same solve with the planner's choice works
+        cs.cs_solve(h, cs.params_from_workload(w, precision="fp32"), 5)
+        cs.cs_result(h)
+    finally:
+        cs.cs_problem_destroy(h)
