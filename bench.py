@@ -74,7 +74,7 @@ def fp32_simt_peak_tflops(sm_mhz, num_sms=152):
     return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-KERNEL_SOURCES = ["euler_kernel.cuh", "kernels_common.cuh", "mma.cuh", "tma.cuh", "common.cuh"]
+KERNEL_SOURCES = ["euler_kernel.cuh", "kernels_common.cuh", "mma.cuh", "tma.cuh", "common.cuh", "tcgen05.cuh"]
 
 
 def kernel_source_sha256():
@@ -494,8 +494,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tensor-form", type=int, choices=[0, 1, 2], default=0,
-                    help="cs_params.tensor_form: 0 planner, 1 FMA forms only, 2 tensor-core form only")
+    ap.add_argument("--tensor-form", type=int, choices=[0, 1, 2, 3, 4], default=0,
+                    help="cs_params.tensor_form: 0 planner, 1 FMA forms only, 2 tensor cores only, 3 mma.sync forms only, 4 tcgen05 form only")
     ap.add_argument("--reference-step-s", type=float, default=8.0)
     ap.add_argument("--n-outer", type=int, default=None,
                     help="override the workload's outer iterations (short runs for profiling only)")
@@ -610,7 +610,7 @@ def main():
         return 0
 
     x_hat, sigma_hat, energy, stats, _ = results
-    form = int(stats[10])  # 0 / 1 FMA forms, 2 tensor cores
+    form = int(stats[10])  # 0 / 1 FMA forms, 2 tensor cores (mma.sync), 5 tensor cores (tcgen05)
     peaks, peak_kind = measured_peaks()
     ck = clocks.summary()
     n_launch_euler = args.steps * w["n_outer"]
@@ -636,6 +636,28 @@ def main():
                                "the step latency is the figure of merit",
                 "us_per_step": per_launch_s * 1e6 / w["n_steps"], "flops_per_launch": flops_per_launch,
                 "traffic": None}
+    elif form == 5:
+        # FP32 problem on the tcgen05 tensor cores: one M = 128 MMA per 16-k block
+        # on the stacked FP16 parts of G (64 rows hi over lo) and X (hi over lo);
+        # the roofline is the product's own precision (FP32), the executed MMA
+        # rate against the dense FP16 tensor rate beside it
+        achieved = flops_per_launch / per_launch_s / 1e12
+        C, ctas = int(stats[8]), int(stats[9])
+        npad = (w["N"] + 31) // 32 * 32
+        mma_flops = 2.0 * (ctas // max(C, 1)) * (npad // 16) * 128 * (2 * min(T, 64)) * 16 * ((T + 63) // 64)
+        tpeak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        executed = mma_flops * w["n_steps"] / per_launch_s / 1e12
+        roof = {"kernel": "euler_kernel<float, float, 1, STREAM=false, WIDE=true, TC=true, TC5=true> "
+                          "(FP32 G_off resident on chip as FP16 hi/lo parts, one tcgen05 M=128 MMA per 16-k block, "
+                          "TMEM accumulators)",
+                "bound": "alu", "achieved": achieved, "peak": fp32_simt_peak_tflops(sm_mhz), "unit": "TFLOP/s",
+                "peak_source": f"FP32, the precision of the product: 152 SMs x 128 lanes x 2 flop x {sm_mhz} MHz "
+                               f"(max SM clock, {peak_kind})",
+                "flops_per_launch": flops_per_launch,
+                "tensor_pipe": {"executed_tflops": executed, "peak": tpeak, "frac": executed / tpeak,
+                                "peak_source": f"dense BF16 (= FP16) tensor rate, cuBLAS sustained ({peak_kind})",
+                                "executed_flops_per_step": mma_flops},
+                "traffic": recorded_traffic()}
     elif form == 2:
         # FP32 problem on the tensor cores: three FP16 MMAs per tile on split
         # operands; the algorithmic figure counts the FP32 products once
@@ -660,6 +682,8 @@ def main():
                 "flops_per_launch": flops_per_launch, "traffic": recorded_traffic()}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["launch_ms"] = per_launch_s * 1e3
+    roof["form"] = form
+    roof["us_per_euler_step"] = per_launch_s * 1e6 / w["n_steps"]
     ms_sorted = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": args.steps,

@@ -89,16 +89,20 @@ typedef struct {
                            1: the first solve of a shape in this process times the cost model's
                            four cheapest splits on this GPU (48 steps each, synchronising the
                            problem's stream) and keeps the fastest for later solves */
-  int32_t tensor_form;  /* G_off X on the tensor cores (mma.sync): FP32 problems with trial
-                           blocks of 16, 32 or 64 (G_off and X each split into two FP16
-                           parts, three MMAs per tile: FP32-level accuracy); streamed FP16 /
-                           BF16 G_off with exactly 8 trials, and batches of FP16 / BF16
-                           problems with 8 or 16 trials (the stored G_off times X in two
-                           16-bit parts).  X is scaled by a power of two from max |R|, so
-                           |X| <= |c| and FP16 X overflows only on runs whose explicit Euler
-                           steps already diverge.  0: the planner chooses; 1: FMA forms only;
-                           2: the tensor-core form only (the solve fails where it does not
-                           apply) */
+  int32_t tensor_form;  /* the product G_off X on the tensor cores.  FP32 problems with trial
+                           blocks of 16, 32 or 64: G_off and X each split into two FP16 parts
+                           (FP32-level accuracy), either on the tcgen05 tensor cores (one
+                           M = 128 MMA per 16 k on the stacked parts, TMEM accumulators;
+                           resident G_off, at most 64 rows per cluster) or on the mma.sync
+                           path (three MMAs per tile); streamed FP16 / BF16 G_off with exactly
+                           8 trials, and batches of FP16 / BF16 problems with 8 or 16 trials
+                           (mma.sync: the stored G_off times X in two 16-bit parts).  X is
+                           scaled by a power of two from max |R|, so |X| <= |c| and FP16 X
+                           overflows only on runs whose explicit Euler steps already diverge.
+                           0: the planner chooses among every form; 1: FMA forms only;
+                           2: tensor-core forms only; 3: mma.sync tensor-core forms only;
+                           4: the tcgen05 form only (resident FP32 G_off).  2, 3 and 4 make
+                           the solve fail with CS_EINVAL where no such form applies */
 } cs_params;
 
 typedef struct cs_problem cs_problem;
@@ -154,7 +158,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
  *   [7] energy of the kept trial  [8] cluster size and [9] CTAs of the Euler kernel
  *   [10] form of the Euler kernel: 0 FP32/FP64 FMAs (narrow split), 1 packed FP32
  *        FMAs (wide split), 2 tensor cores (mma.sync), 3 batched (one problem per CTA),
- *        4 batched on tensor cores
+ *        4 batched on tensor cores (mma.sync), 5 tensor cores (tcgen05, TMEM)
  * Host pointers.  Returns CS_ETIMEOUT if a device wait timed out,
  * CS_ESINGULAR (with valid outputs) if the ridge was needed. */
 #define CS_STATS_LEN 11

@@ -20,7 +20,7 @@ paper's order and notation, with NumPy in float64:
 * Eq. etaSchedulling (threshold schedule), eta = sqrt(2 lambda) when fixed
 * Eq. doublel0     objective E = 1/2 ||y - A(sigma o R)||^2 + lambda ||sigma||_0
 
-Readings where the paper is silent (each one is listed in the design doc):
+Readings where the paper is silent, stated here in full:
 
 * R is defined for every r.  The refit on support S solves the normal
   equations G_SS R_S = (A^T y)_S; off the support R_r is the Jacobi fixed

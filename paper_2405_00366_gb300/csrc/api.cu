@@ -123,7 +123,7 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     CS_CUDA(alloc(&S.x_hat, N), "cudaMalloc x_hat");
     CS_CUDA(alloc(&S.sigma_hat, N), "cudaMalloc sigma_hat");
     CS_CUDA(alloc(&S.stats, CS_STATS_LEN), "cudaMalloc stats");
-    CS_CUDA(alloc(&S.bar, 1), "cudaMalloc barrier");
+    CS_CUDA(alloc(&S.bar, kMaxEulerCtas + 1), "cudaMalloc publication flags");
     CS_CUDA(alloc(&S.err, 1), "cudaMalloc err");
     CS_CUDA(alloc(&S.singular, 1), "cudaMalloc singular");
     S.cap_trials = trials;
@@ -163,9 +163,11 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->stream_g != 0 && p->stream_g != 1) return fail(CS_EINVAL, "stream_g must be 0 or 1");
   if (p->stream_g == 1 && p->precision == CS_P_FP64) return fail(CS_EINVAL, "FP64 G_off is never streamed");
   if (p->autotune != 0 && p->autotune != 1) return fail(CS_EINVAL, "autotune must be 0 or 1");
-  if (p->tensor_form < 0 || p->tensor_form > 2) return fail(CS_EINVAL, "tensor_form must be 0, 1 or 2");
-  if (p->tensor_form == 2 && (p->precision == CS_P_FP64 || p->precision == CS_P_FP8))
-    return fail(CS_EINVAL, "tensor_form = 2: no tensor-core form for FP64 or FP8 storage");
+  if (p->tensor_form < 0 || p->tensor_form > 4) return fail(CS_EINVAL, "tensor_form must be 0, 1, 2, 3 or 4");
+  if (p->tensor_form >= 2 && (p->precision == CS_P_FP64 || p->precision == CS_P_FP8))
+    return fail(CS_EINVAL, "tensor_form >= 2: no tensor-core form for FP64 or FP8 storage");
+  if (p->tensor_form == 4 && (p->precision != CS_P_FP32 || p->stream_g == 1))
+    return fail(CS_EINVAL, "tensor_form = 4: the tcgen05 form is built for resident FP32 G_off only");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -370,8 +372,8 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     CS_CUDA(mark(p, TM_EULER, true), "event");
     cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
     if (e == cudaErrorInvalidConfiguration)
-      return fail(CS_EINVAL, prm->tensor_form == 2
-                                 ? "tensor_form = 2: no tensor-core work split for this shape and trial count"
+      return fail(CS_EINVAL, prm->tensor_form >= 2
+                                 ? "tensor_form >= 2: no tensor-core work split of that kind for this shape and trials"
                                  : "N too large for the on-chip Euler kernel at this precision");
     if (e != cudaSuccess)
       return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
@@ -404,8 +406,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   cudaStream_t stream = P0.stream;
   g_alloc_stream = stream;
   const bool btc = batch_tensor_form(prm->precision, trials, prm->tensor_form);
-  if (prm->tensor_form == 2 && !btc)
-    return fail(CS_EINVAL, "tensor_form = 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
+  if (prm->tensor_form >= 2 && !btc)
+    return fail(CS_EINVAL, "tensor_form >= 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
                            "trials");
   int64_t nmax = 0;
   for (int i = 0; i < n; ++i) {
@@ -541,7 +543,7 @@ static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   st[10] = p->S.plan_form;
   if (stats_out) std::memcpy(stats_out, st, sizeof(st));
   const int err = (int)st[3];
-  if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a grid barrier timed out");
+  if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a device-side wait timed out");
   if (err != 0) return fail(CS_ECUDA, "device error word " + std::to_string(err));
   return st[2] != 0.0 ? CS_ESINGULAR : CS_OK;
 }

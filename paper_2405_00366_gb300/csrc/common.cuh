@@ -1,6 +1,6 @@
-// Shared device helpers of the CUDA path: numeric conversions, the bounded
-// grid barrier, block reductions and the counter-based generator of the
-// initial amplitudes.
+// Shared device helpers of the CUDA path: numeric conversions, the device
+// error word, acquire/release accesses, block reductions and the
+// counter-based generator of the initial amplitudes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -46,39 +46,6 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
-
-// Grid-wide barrier over co-resident CTAs built on a monotonically increasing
-// arrival counter: barrier number k (k = 1, 2, ...) completes when the counter
-// reaches k * gridDim.x.  The wait is bounded by `timeout_cycles` of clock64;
-// on expiry the CTA sets DEV_TIMEOUT in *err and every CTA returns false from
-// this and all later barriers, so the kernel always ends.  Returns true when
-// the barrier completed normally.  Must be called by every thread of the CTA.
-// `phantom` adds CTAs that never arrive (a test of the timeout path).  The spin
-// polls only the counter; the error word and the clock are looked at every
-// 2048 cycles, so each poll is one L2 round trip.
-__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned k, int* err,
-                                             long long timeout_cycles, unsigned phantom = 0) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    red_release_gpu_add(counter, 1u);
-    const unsigned target = k * (gridDim.x + phantom);
-    const long long t0 = clock64();
-    long long next = t0 + 2048;
-    while (ld_acquire_gpu(counter) < target) {
-      const long long now = clock64();
-      if (now < next) continue;
-      if (ld_volatile(err) != 0) { ok = 0; break; }
-      if (now - t0 > timeout_cycles) { set_error(err, DEV_TIMEOUT); ok = 0; break; }
-      next = now + 2048;
-    }
-    if (ok && ld_volatile(err) != 0) ok = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 // ------------------------------------------------------------------ reductions
 // Deterministic block sum (fixed tree order) of one double per thread.

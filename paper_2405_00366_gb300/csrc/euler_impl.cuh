@@ -16,7 +16,7 @@ namespace cs {
 namespace {
 struct Plan {
   int C, NC, RPC, RPC_pad, ORW, kq, kch, slots, RW, RG, MR, WK, ldg;
-  bool stream, wide, tc;
+  bool stream, wide, tc, tc5;
   size_t smem, slot_bytes, xoff;
 };
 
@@ -26,14 +26,14 @@ using EulerFn = void (*)(EulerArgs<CT>);
 template <typename GT, typename CT, bool STREAM, bool WIDE, bool TC = false>
 EulerFn<CT> kernel_for_s(int MR) {
   switch (MR) {
-    case 1: return euler_kernel<GT, CT, 1, STREAM, WIDE, TC>;
-    case 2: return euler_kernel<GT, CT, 2, STREAM, WIDE, TC>;
-    case 3: return euler_kernel<GT, CT, 3, STREAM, WIDE, TC>;
-    case 4: return euler_kernel<GT, CT, 4, STREAM, WIDE, TC>;
-    case 5: return euler_kernel<GT, CT, 5, STREAM, WIDE, TC>;
-    case 6: return euler_kernel<GT, CT, 6, STREAM, WIDE, TC>;
-    case 7: return euler_kernel<GT, CT, 7, STREAM, WIDE, TC>;
-    default: return euler_kernel<GT, CT, 8, STREAM, WIDE, TC>;
+    case 1: return euler_kernel<GT, CT, 1, STREAM, WIDE, TC, false>;
+    case 2: return euler_kernel<GT, CT, 2, STREAM, WIDE, TC, false>;
+    case 3: return euler_kernel<GT, CT, 3, STREAM, WIDE, TC, false>;
+    case 4: return euler_kernel<GT, CT, 4, STREAM, WIDE, TC, false>;
+    case 5: return euler_kernel<GT, CT, 5, STREAM, WIDE, TC, false>;
+    case 6: return euler_kernel<GT, CT, 6, STREAM, WIDE, TC, false>;
+    case 7: return euler_kernel<GT, CT, 7, STREAM, WIDE, TC, false>;
+    default: return euler_kernel<GT, CT, 8, STREAM, WIDE, TC, false>;
   }
 }
 
@@ -60,7 +60,10 @@ EulerFn<CT> kernel_for_w(int MR, bool stream) {
 }
 
 template <typename GT, typename CT>
-EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
+EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc, bool tc5 = false) {
+  if constexpr (h3able<GT, CT>::value) {
+    if (tc5) return euler_kernel<GT, CT, 1, false, true, true, true>;
+  }
   if constexpr (tensorable<GT, CT>::value) {
     if (tc) return kernel_for_s<GT, CT, true, true, true>(MR);
   }
@@ -91,7 +94,10 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc) {
 //    the larger of two m16n8k16 MMAs per 16 x 16 tile at one per 2 clocks and
 //    the streamed G bytes; resident FP32 G_off with blocks of 16/32/64 trials,
 //    three MMAs per 16 x 8 x 16 tile at one per 2 clocks and 70% of that
-//    (mma.sync rates measured on GB300), plus the k-warp reduction;
+//    (mma.sync rates measured on GB300), plus the k-warp reduction; and the
+//    tcgen05 form (resident FP32 G_off, at most 64 rows per cluster): one
+//    M = 128 MMA per 16-k block plus the epilogue's TMEM loads
+//    (tensor_form = 3 keeps the mma.sync forms only);
 // each plus X bytes at 44 per clock (measured: the X traffic of a step adds to
 // its time rather than overlapping the product), a fixed cost per cluster rank
 // for the reduction through distributed shared memory, and the step barrier: a
@@ -123,6 +129,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
   // the FP32 one (resident): blocks of one width in {16, 32, 64}
   const bool tc_ok = tensorable<GT, CT>::value && tensor_form != 1 && T == 8;
   const bool h3_ok = h3able<GT, CT>::value && tensor_form != 1 && twmax >= 16 && wide_ok;
+  // the tcgen05 form (resident FP32 G_off): the same trial blocks, at most 64 rows per cluster
+  const bool tc5_ok = h3able<GT, CT>::value && tensor_form != 1 && tensor_form != 3 && twmax >= 16 && wide_ok;
+  // tensor_form: 0 any form, 1 FMA forms only, 2 tensor-core forms only, 3 mma.sync forms only,
+  // 4 the tcgen05 form only
   double best_cost = 0.0;
   bool found = false;
   Plan bp{};
@@ -133,21 +143,26 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
     for (int C : csizes) {
       if (hint > 0 && C != hint) continue;
       if (C > nq || sms < C) continue;
-      // variants: wide with WK = 1, 2, 4, 8 k-warps, narrow (WK = 0), and
-      // (streamed) the tensor-core form with WK = 1, 2, 4, 8 (v >= 5)
-      for (int v = 0; v < 9; ++v) {
+      // variants: wide with WK = 1, 2, 4, 8 k-warps, narrow (WK = 0), the
+      // mma.sync tensor-core forms with WK = 1, 2, 4, 8 (v = 5 .. 8) and the
+      // tcgen05 form (v = 9, resident only)
+      for (int v = 0; v < 10; ++v) {
+        const bool tc5 = v == 9;
         const bool tc = v >= 5;
-        const int WK = tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0);
+        const int WK = tc5 ? 1 : (tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0));
         const bool wide = WK > 0;
         if (wide && !wide_ok) continue;
-        if (tc && !(stream ? tc_ok : h3_ok)) continue;
-        if (tc && !stream && WK * (twmax / 16) > kConsumerWarps) continue;
-        if (!tc && tensor_form == 2) continue;
+        if (tc5 && (stream || !tc5_ok)) continue;
+        if (tc && !tc5 && !(stream ? tc_ok : h3_ok)) continue;
+        if (!tc5 && tensor_form == 4) continue;
+        if (tc && !tc5 && !stream && WK * (twmax / 16) > kConsumerWarps) continue;
+        if (!tc && tensor_form >= 2) continue;
         Plan pl{};
         pl.C = C;
         pl.stream = stream;
         pl.wide = wide;
         pl.tc = tc;
+        pl.tc5 = tc5;
         pl.WK = wide ? WK : 1;
         if (stream) {
           pl.kq = ((nq + C - 1) / C + 7) / 8 * 8;  // whole 32-column tiles per rank
@@ -174,7 +189,12 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           pl.NC = (N + pl.RPC - 1) / pl.RPC;  // no cluster without rows
           if (pl.NC != NC && NC != std::min(sms / C, N)) continue;
           const int rw_need = (pl.RPC + WR - 1) / WR;
-          if (wide) {
+          if (tc5) {
+            // one M = 128 MMA covers 64 rows (hi over lo); fewer clusters only need more rows
+            if (pl.RPC > 64) break;
+            pl.RG = 1;
+            pl.MR = 1;
+          } else if (wide) {
             pl.RG = RGw;
             pl.MR = (rw_need + RGw - 1) / RGw;
           } else {
@@ -188,14 +208,18 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           if (pl.MR > kMaxRowsPerLane) break;  // fewer clusters only need more rows
           pl.RW = pl.RG * pl.MR;
           pl.RPC_pad = WR * pl.RW;
+          if (tc5) {
+            pl.RW = 8;
+            pl.RPC_pad = 64;
+          }
           pl.ORW = (pl.RPC + C - 1) / C;
-          EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, stream, wide, tc);
+          EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, stream, wide, tc, tc5);
           cudaFuncAttributes fa;
           e = cudaFuncGetAttributes(&fa, fn);
           if (e != cudaSuccess) { g_where = "cudaFuncGetAttributes"; return e; }
           const size_t cap = (size_t)optin - fa.sharedSizeBytes;
           const size_t gblock = stream ? 0 : (size_t)pl.RPC_pad * pl.ldg * sizeof(GT);
-          const size_t kpart = wide ? (size_t)WK * pl.RPC_pad * twmax * sizeof(float) : 0;
+          const size_t kpart = (wide && !tc5) ? (size_t)WK * pl.RPC_pad * twmax * sizeof(float) : 0;
           // streamed plans: the most G_off tiles per slot (4, 2, 1) that leave 3
           // slots (measured: one tile per slot keeps too few bytes in flight)
           pl.slots = 0;
@@ -243,7 +267,15 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
           const double gbytes =
               stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) * std::max(1.0, 128.0 / pl.kch) : 0.0;
           double cost;
-          if (tc && stream) {
+          if (tc5) {
+            // one M = 128 MMA per 16-k block (about 176 clocks each on GB300 for
+            // any N up to 256, measured), the epilogue's TMEM loads (kTc5Acc
+            // accumulators, 16 columns per load), X bytes as for the other forms
+            const double nkb = pl.kq * 4 / 16.0;
+            const double mma = nkb * nblk * 176.0;
+            const double epi = nblk * (twmax / 16.0) * kTc5Acc * 2.0 * 40.0;
+            cost = mma + xbytes / 44.0 + epi;
+          } else if (tc && stream) {
             // MMAs (two per 16 x 16 tile of G_off: the two parts of X), taken at
             // one per two clocks per SM (measured on GB300), overlap the streamed bytes
             const double mmas = (double)pl.RPC_pad / 16.0 * pl.kq * 4 / 16.0 * 2.0;
@@ -279,7 +311,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
     }
   }
   if (!found) {
-    g_where = tensor_form == 2 ? "make_plan: no tensor-core work split for this shape (tensor_form = 2)"
+    g_where = tensor_form >= 2 ? "make_plan: no tensor-core work split of the requested kind for this shape"
                                : "make_plan: no work split fits";
     return cudaErrorInvalidConfiguration;
   }
@@ -351,17 +383,19 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
   a.theta = sqrt(prm.tau) * eta * eta / 4.0;
   a.field = prm.field; a.init_kind = prm.init_kind; a.init_scale = prm.init_scale;
   a.seed = prm.seed; a.instance = prm.instance; a.outer = outer;
-  a.bar = S.bar; a.err = S.err; a.timeout_cycles = timeout_cycles;
+  a.flags = S.bar; a.err = S.err; a.timeout_cycles = timeout_cycles;
   a.phantom = (unsigned)prm.test_phantom_ctas;
   S.plan_cluster = pl.C;
   S.plan_ctas = pl.C * pl.NC;
-  S.plan_form = pl.tc ? 2 : (pl.wide ? 1 : 0);
+  S.plan_form = pl.tc5 ? 5 : (pl.tc ? 2 : (pl.wide ? 1 : 0));
 
-  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, pl.stream, pl.wide, pl.tc);
+  if (pl.C * pl.NC > kMaxEulerCtas) { g_where = "launch_plan: grid larger than the flag array"; return cudaErrorInvalidConfiguration; }
+  EulerFn<CT> fn = kernel_for<GT, CT>(pl.MR, pl.stream, pl.wide, pl.tc, pl.tc5);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) { g_where = "cudaFuncSetAttribute(launch)"; return e; }
-  e = cudaMemsetAsync(S.bar, 0, sizeof(unsigned), P.stream);
-  if (e != cudaSuccess) { g_where = "cudaMemsetAsync(barrier)"; return e; }
+  // the per-CTA publication flags and the word after them (never written)
+  e = cudaMemsetAsync(S.bar, 0, sizeof(unsigned) * ((size_t)pl.C * pl.NC + 1), P.stream);
+  if (e != cudaSuccess) { g_where = "cudaMemsetAsync(flags)"; return e; }
   g_where = pl.C == 1 ? "cudaLaunchKernelEx(cooperative)" : "cudaLaunchKernelEx(cluster)";
   // A cooperative launch guarantees that every CTA is resident, which the grid
   // barrier needs; the runtime does not combine it with clusters, so a cluster
@@ -388,7 +422,7 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
 }
 
 // Autotuner: time the kTuneCands cheapest candidate splits of the cost model,
-// plus the cheapest of each kernel form (FMA, tensor cores) not among them, on
+// plus the cheapest of each kernel form (FMA, mma.sync, tcgen05) not among them, on
 // this GPU (kTuneSteps Euler steps each, twice, CUDA events on the problem's
 // stream; the second run counts) and return the fastest.  The runs only write
 // the solve's scratch (X, sigma), which the real run rewrites.
@@ -404,9 +438,9 @@ cudaError_t autotune_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int 
   float best = 0.f;
   const int steps = std::min(prm.n_steps, kTuneSteps);
   std::vector<size_t> pick;
-  bool form_seen[2] = {false, false};
+  bool form_seen[3] = {false, false, false};
   for (size_t c = 0; c < cands.size(); ++c) {
-    const int f = cands[c].second.tc ? 1 : 0;
+    const int f = cands[c].second.tc5 ? 2 : (cands[c].second.tc ? 1 : 0);
     if ((int)pick.size() < kTuneCands || !form_seen[f]) {
       pick.push_back(c);
       form_seen[f] = true;

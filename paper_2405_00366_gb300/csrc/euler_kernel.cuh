@@ -23,8 +23,15 @@
 //  * the C partials of a row are summed through distributed shared memory:
 //    CTA j reduces and updates rows [j*RPC/C, (j+1)*RPC/C) of its cluster,
 //    whose c, e, b stay in its shared memory, and writes their next X;
-//  * all CTAs then meet at a bounded grid barrier; X is double-buffered in
-//    global memory, so one barrier per step suffices.
+//  * each CTA then publishes its rows of the next X (a per-CTA release flag
+//    counting its publications); before streaming a chunk of k rows of X, the
+//    producer warp waits (bounded) only for the flags of the CTAs that own
+//    those rows, so the X stream of a step starts chunk by chunk as its owners
+//    finish instead of behind a grid-wide barrier.  X is double-buffered in
+//    global memory: a CTA rewrites a buffer only after the cluster barrier that
+//    follows its product, by which time its cluster (whose ranks cover every k)
+//    has seen every CTA publish the X it reads, hence every CTA has finished
+//    reading the buffer's previous contents.
 // Versus every CTA reading all of X, the cluster cuts the L2 -> SM traffic of
 // X by C.  C = 1 is the plain row-block split.
 #pragma once
@@ -38,6 +45,7 @@
 #include "internal.h"
 #include "kernels_common.cuh"
 #include "mma.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace cg = cooperative_groups;
@@ -96,10 +104,10 @@ struct EulerArgs {
   double init_scale;
   uint64_t seed;
   int instance, outer;
-  unsigned* bar;
+  unsigned* flags;  // per CTA: X publications so far (gridDim.x words, then one word never written)
   int* err;
   long long timeout_cycles;
-  unsigned phantom;
+  unsigned phantom;  // test hook: nonzero makes every X wait also wait for the never-written word
 };
 
 // X is stored in blocks of kTChunk trials: block t0 (t0 a multiple of 64) holds
@@ -111,6 +119,12 @@ __host__ __device__ __forceinline__ size_t xblock(int t0, int Npad) { return (si
 __host__ __device__ __forceinline__ int xwidth(int t0, int T) {
   return round4(T - t0 < kTChunk ? T - t0 : kTChunk);
 }
+
+// 32-bit words after the mbarriers: [0] TMEM address (tcgen05 form), [1..8]
+// last use + 1 of each ring slot issued by the producer (for the drain before
+// exit), [9] the X version (publication count) the next products read.
+constexpr int kMaxSlots = 8;
+constexpr int kMiscWords = 2 + kMaxSlots;
 
 // Shared-memory layout of one CTA (byte offsets): resident G block (absent when
 // streaming), ring, partials (prows rows), owned state, mbarriers.
@@ -125,7 +139,9 @@ __host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t
   s.part = s.ring + align128((size_t)slots * slot_bytes);
   s.st = s.part + align128((size_t)prows * twmax * cbytes);
   s.bars = s.st + align128((size_t)4 * ORW * T * cbytes);
-  s.total = s.bars + 2 * (size_t)slots * sizeof(uint64_t);
+  // full[slots], empty[slots], the accumulator barrier of the tcgen05 form, then
+  // kMiscWords 32-bit words (TMEM address, barrier outcomes, last ring uses)
+  s.total = s.bars + (2 * (size_t)slots + 1) * sizeof(uint64_t) + kMiscWords * sizeof(uint32_t);
   return s;
 }
 
@@ -170,27 +186,91 @@ __global__ void store_cluster_tiles_kernel(const double* __restrict__ G, GT* __r
   }
 }
 
-// Producer side of one block of trials (lane 0 of warp 8): stream this CTA's
-// k rows of X (and, when streaming, the G_off tiles) through the ring.  `gctr`
-// counts ring uses across calls so the mbarrier phases stay consistent.
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// CTA that owns (updates and publishes) row r of X: cluster r / RPC, rank
+// (r mod RPC) / ORW.
+template <typename CT>
+__device__ __forceinline__ int x_owner(const EulerArgs<CT>& a, int r) {
+  return (r / a.RPC) * a.C + (r % a.RPC) / a.ORW;
+}
+
+// Owners of the rows of X publish in order of their rows, so the producer
+// warp tracks a frontier: every owner below `front` is known to have published
+// the X version `need`.  advance_front() polls the 32 owners from the frontier
+// on (one acquire load per lane, all at once) and moves the frontier past the
+// leading run of those that have published, until it passes owner `target`.
+// Bounded: after timeout_cycles of clock64 it sets DEV_TIMEOUT, and once the
+// error word is set it stops waiting (the kernel then runs on and the solve
+// reports the timeout).  `phantom` (a test hook) also waits for a word that
+// is never written.  Executed by the whole warp; every decision is warp-uniform.
+template <typename CT>
+__device__ __forceinline__ void advance_front(const EulerArgs<CT>& a, int& front, int target, int olimit,
+                                              unsigned need, bool phantom) {
+  const int l = threadIdx.x & 31;
+  const long long t0 = __shfl_sync(0xffffffffu, clock64(), 0);
+  long long next = t0 + 2048;
+  while (front <= target || phantom) {
+    const int o = front + l;
+    bool ok = o > olimit || ld_acquire_gpu(a.flags + o) >= need;
+    if (phantom && l == 31) ok = ld_acquire_gpu(a.flags + gridDim.x) >= need;  // never written
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    const int run = __ffs(~bal) == 0 ? 32 : __ffs(~bal) - 1;  // leading published owners
+    front += run;
+    if (front > target && !(phantom && !(bal >> 31))) return;
+    const long long now = __shfl_sync(0xffffffffu, clock64(), 0);
+    if (now < next) continue;
+    next = now + 2048;
+    if (__any_sync(0xffffffffu, ld_volatile(a.err) != 0)) { front = olimit + 1; return; }
+    if (now - t0 > a.timeout_cycles) {
+      if (l == 0) set_error(a.err, DEV_TIMEOUT);
+      front = olimit + 1;
+      return;
+    }
+  }
+}
+
+// Producer side of one block of trials (warp 8; lane 0 issues the copies):
+// stream this CTA's k rows of X (and, when streaming, the G_off tiles) through
+// the ring, each chunk once its owners have published the X version the
+// products read (last[kMaxSlots]).  `gctr` counts ring uses across calls so
+// the mbarrier phases stay consistent; last[s] records the last use of slot s.
 template <typename GT, typename CT, bool STREAM>
 __device__ __forceinline__ void produce_chunks(const EulerArgs<CT>& a, const CT* __restrict__ Xblk, int twp, int k0,
                                                int klen, int cl, unsigned char* ring, uint64_t* full,
-                                               uint64_t* empty, unsigned gctr) {
+                                               uint64_t* empty, unsigned gctr, uint32_t* last) {
   const int nch = (klen + a.kch - 1) / a.kch;
-  if ((threadIdx.x & 31) == 0) {
-    // earlier generic accesses of X and of the ring come before the copies
-    fence_proxy_async_global();
-    fence_proxy_async_shared();
-    for (int ci = 0; ci < nch; ++ci) {
-      const unsigned g = gctr + ci;
-      const int s = (int)(g % a.slots);
-      const unsigned u = g / a.slots;
-      if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
-        set_error(a.err, DEV_TIMEOUT);
-        break;
-      }
-      const int kr = min(a.kch, klen - ci * a.kch);
+  const int l = threadIdx.x & 31;
+  const unsigned need = last[kMaxSlots];
+  const int kend = min(k0 + klen, a.N);  // rows at or past N are padding: no owner, never rewritten
+  int front = k0 < kend ? x_owner(a, k0) : 0;
+  const int olimit = k0 < kend ? x_owner(a, kend - 1) : -1;
+  bool phantom = a.phantom != 0;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    const unsigned u = g / a.slots;
+    int ok = 1;
+    if (l == 0 && u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
+      set_error(a.err, DEV_TIMEOUT);
+      ok = 0;
+    }
+    if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+    const int kr = min(a.kch, klen - ci * a.kch);
+    const int klast = min(k0 + ci * a.kch + kr, a.N) - 1;  // last row of the chunk that has an owner
+    if (klast >= k0 + ci * a.kch || phantom) {
+      advance_front(a, front, klast >= k0 + ci * a.kch ? x_owner(a, klast) : -1, olimit, need, phantom);
+      phantom = false;
+    }
+    __syncwarp();
+    if (l == 0) {
+      // the owners' X writes (generic proxy, ordered by their release and the
+      // acquires above) and earlier generic accesses of the ring come before
+      // the copies (async proxy)
+      fence_proxy_async_global();
+      fence_proxy_async_shared();
       const unsigned bytes = (unsigned)((size_t)kr * twp * sizeof(CT));
       unsigned char* slot = ring + (size_t)s * a.slot_bytes;
       if constexpr (STREAM) {
@@ -204,6 +284,7 @@ __device__ __forceinline__ void produce_chunks(const EulerArgs<CT>& a, const CT*
         mbar_arrive_expect_tx(full + s, bytes);
       }
       bulk_copy_g2s(slot + a.xoff, Xblk + (size_t)(k0 + ci * a.kch) * twp, bytes, full + s);
+      last[s] = g + 1;
     }
   }
 }
@@ -222,12 +303,12 @@ template <typename GT, typename CT, int MR, bool STREAM>
 __device__ __forceinline__ void cluster_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                  const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
                                                  int cl, unsigned char* ring, CT* P, uint64_t* full,
-                                                 uint64_t* empty, unsigned& gctr) {
+                                                 uint64_t* empty, unsigned& gctr, uint32_t* last) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   const int ldg = a.ldg;
   if (w == kConsumerWarps) {
-    produce_chunks<GT, CT, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    produce_chunks<GT, CT, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, last);
     gctr += nch;
     return;
   }
@@ -324,11 +405,11 @@ template <typename GT, int MR, bool STREAM>
 __device__ __forceinline__ void wide_partials(const EulerArgs<float>& a, const GT* __restrict__ Gsm,
                                               const float* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
                                               int cl, unsigned char* ring, float* P, uint64_t* full,
-                                              uint64_t* empty, unsigned& gctr) {
+                                              uint64_t* empty, unsigned& gctr, uint32_t* last) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
-    produce_chunks<GT, float, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    produce_chunks<GT, float, STREAM>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, last);
     gctr += nch;
     return;
   }
@@ -459,11 +540,11 @@ __device__ __forceinline__ void sum_k_warps(const EulerArgs<float>& a, const uns
 template <typename GT, int MR>
 __device__ __forceinline__ void tc_partials(const EulerArgs<float>& a, const float* __restrict__ Xblk, int twp,
                                             int k0, int klen, int cl, unsigned char* ring, float* P,
-                                            uint64_t* full, uint64_t* empty, unsigned& gctr) {
+                                            uint64_t* full, uint64_t* empty, unsigned& gctr, uint32_t* last) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
-    produce_chunks<GT, float, true>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    produce_chunks<GT, float, true>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, last);
     gctr += nch;
     return;
   }
@@ -557,11 +638,11 @@ template <int MR>
 __device__ __forceinline__ void h3_partials(const EulerArgs<float>& a, const float* __restrict__ Gsm,
                                             const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
                                             unsigned char* ring, float* P, uint64_t* full, uint64_t* empty,
-                                            unsigned& gctr, float gsi) {
+                                            unsigned& gctr, float gsi, uint32_t* last) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nch = (klen + a.kch - 1) / a.kch;
   if (w == kConsumerWarps) {
-    produce_chunks<float, float, false>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr);
+    produce_chunks<float, float, false>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, last);
     gctr += nch;
     return;
   }
@@ -686,15 +767,240 @@ __device__ __forceinline__ float stage_h3(const float* __restrict__ src, int Npa
   return ldexpf(1.f, ex);
 }
 
+// ------------------------------------------------------------------ tcgen05 form
+// FP32 problems on the fifth-generation tensor cores (tcgen05.mma, TMEM
+// accumulators), for resident FP32 G_off with trial blocks of 16, 32 or 64
+// and at most 64 rows per cluster.  Same split as the mma.sync form
+// (G = hi + 2^-11 lo and X = hi + 2^-11 lo, FP16 parts, G scaled by a power of
+// two per CTA, X by one from max |R|), arranged so that ONE M = 128 MMA per
+// 16-k block forms every product needed: the A operand stacks the CTA's 64
+// rows of G_hi over the same rows of G_lo (128 rows), the B operand stacks
+// X_hi over X_lo (2 twp rows), so
+//     D = [[G_hi X_hi, G_hi X_lo], [G_lo X_hi, G_lo X_lo]]
+// (the last quarter is not used) and U = G_hi X_hi + 2^-11 (G_hi X_lo +
+// G_lo X_hi) is formed from TMEM with round-to-nearest FP32 additions.
+// Accumulation: the 16-k blocks go round-robin to kTc5Acc accumulators (TMEM
+// columns acc * 2 twp ..), so consecutive MMAs are independent and each
+// accumulator chains at most klen / (16 kTc5Acc) of them: the tensor cores'
+// accumulation truncates, and short chains keep its bias below the rounding
+// error of an FP32 sum over the k range.
+// Roles: warp 8 lane 0 streams the X chunks into the ring (bulk copies);
+// thread 0 issues the MMAs of each chunk once it has landed and commits them
+// to the slot's empty barrier (the slot is refilled only after those MMAs have
+// read it), and after the last chunk to the accumulator barrier; the eight
+// consumer warps then read the accumulators (warp w: TMEM lanes 32 (w % 4) ..
+// + 31, one column half) and leave this CTA's partial U in P.
+// Layouts (canonical no-swizzle K-major, tcgen05.cuh): the G block as
+// [16-k block][128 stacked rows] (4 KB per block); X of a block of twp trials
+// as [16-k block][2 twp stacked rows] (64 twp bytes per block), so any run of
+// whole 16-k blocks is one contiguous bulk copy.
+constexpr int kTc5Acc = 4;
+constexpr uint32_t kTc5Cols = 512;  // TMEM columns: kTc5Acc accumulators of up to 128 columns
+
+// Stage this CTA's block of FP32 G_off for the tcgen05 form: rows
+// [row0, row0 + nrows) (nrows <= 64, zero up to 64), k in [k0, k0 + klen)
+// (klen a multiple of 16), scaled by 2^-e with max |G| < 2^e, split into FP16
+// hi (A rows 0..63) and lo (A rows 64..127).  Returns 2^e.  Uses P as scratch.
+__device__ __forceinline__ float stage_tc5(const float* __restrict__ src, int Npad, int row0, int nrows, int k0,
+                                           int klen, unsigned char* Gsm, float* P) {
+  float m = 0.f;
+  for (int v = threadIdx.x; v < nrows * klen; v += kThreads) {
+    const int r = v / klen, k = v % klen;
+    m = fmaxf(m, fabsf(src[(size_t)(row0 + r) * Npad + k0 + k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) P[threadIdx.x >> 5] = m;
+  __syncthreads();
+  for (int i = 0; i < kThreads / 32; ++i) m = fmaxf(m, P[i]);
+  __syncthreads();
+  int ex = 0;
+  if (m > 0.f && m <= 1e30f) frexpf(m, &ex);
+  ex = max(-100, min(100, ex));
+  const float gsc = ldexpf(1.f, -ex);
+  const int total = (klen >> 4) * 128 * 16;  // halves: 128 stacked rows x 16 k per block
+  for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+    const int kb = idx >> 11, within = idx & 2047;
+    const int rho = within >> 4, kk = within & 15;
+    const int part = rho >> 6, r = rho & 63;
+    const float v = r < nrows ? src[(size_t)(row0 + r) * Npad + k0 + kb * 16 + kk] * gsc : 0.f;
+    const __half hi = __float2half_rn(v);
+    *reinterpret_cast<__half*>(Gsm + (size_t)kb * 4096 + tc5::canon_off(rho, kk)) =
+        part ? __float2half_rn((v - __half2float(hi)) * 2048.f) : hi;
+  }
+  // these generic-proxy writes are read by the tensor cores (async proxy)
+  fence_proxy_async_shared();
+  return ldexpf(1.f, ex);
+}
+
+// Sum over the first nacc accumulators (2 twp columns apart) of 16 columns of
+// this warp's TMEM lanes starting at column c0; round-to-nearest, fixed order
+// (((acc0 + acc1) + acc2) + acc3); zeros when nacc = 0.
+__device__ __forceinline__ void tc5_sum16(uint32_t lane_base, int c0, int NN, int nacc, float (&s)[16]) {
+  if (nacc == kTc5Acc) {
+    tc5::ld16x4_sum(lane_base + (uint32_t)c0, (uint32_t)NN, s);
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s[i] = 0.f;
+  if (nacc == 0) return;
+  tc5::ld16(lane_base + (uint32_t)c0, s);
+  for (int acc = 1; acc < nacc; ++acc) {
+    float v[16];
+    tc5::ld16(lane_base + (uint32_t)(acc * NN + c0), v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s[i] += v[i];
+  }
+}
+
+// Index of partial (r, t) in P for a block of twp trials.  The tcgen05 form's
+// epilogue writes a whole row per lane, so its groups of four trials are
+// swizzled by the row (group t / 4 stored at (t / 4) xor (r mod twp / 4)): the
+// 16-byte stores of eight consecutive rows then fall in distinct banks.
+template <bool TC5>
+__device__ __forceinline__ int pidx(int r, int t, int twp) {
+  if constexpr (TC5) return r * twp + ((((t >> 2) ^ (r & ((twp >> 2) - 1))) << 2) | (t & 3));
+  return r * twp + t;
+}
+
+// Partial products of this CTA's block for one block of twp trials on the
+// tcgen05 tensor cores (see above): P[r][t] = sum over this CTA's k range of
+// G_off[row0 + r][k] X[k][t], r < 64.  `gctr` counts ring uses and `round`
+// accumulator rounds across calls, so the mbarrier phases stay consistent.
+__device__ __forceinline__ void tc5_partials(const EulerArgs<float>& a, const unsigned char* Gsm,
+                                             const float* __restrict__ Xblk, int twp, int k0, int klen, int cl,
+                                             unsigned char* ring, float* P, uint64_t* full, uint64_t* empty,
+                                             uint64_t* accbar, unsigned& gctr, unsigned& round, uint32_t tmem,
+                                             float gsi, uint32_t* last) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nch = (klen + a.kch - 1) / a.kch;
+  const int nkb = klen >> 4;
+  const int NN = 2 * twp;
+  if (w == kConsumerWarps) {
+    produce_chunks<float, float, false>(a, Xblk, twp, k0, klen, cl, ring, full, empty, gctr, last);
+    gctr += nch;
+    if (nkb > 0) ++round;
+    return;
+  }
+  if (threadIdx.x == 0 && nkb > 0) {
+    // Descriptors advance by adding to their start-address field (bytes / 16;
+    // shared addresses stay below 2^18, so the 14-bit field never carries):
+    // the MMA issue loop is a handful of instructions per MMA, which keeps the
+    // tensor cores fed (one M = 128, N = 128 MMA every 64 clocks).
+    const uint32_t idesc = tc5::idesc_f16_f32(128, NN);
+    uint64_t adesc = tc5::smem_desc(smem_u32(Gsm), tc5::kLBO, tc5::kSBO);
+    const uint64_t bdesc0 = tc5::smem_desc(smem_u32(ring), tc5::kLBO, tc5::kSBO);
+    const uint64_t bstep = (uint64_t)(NN * 32 / 16);
+    uint32_t acc_col = 0, acc_on = 0, acc_n = 0;
+    for (int ci = 0; ci < nch; ++ci) {
+      const unsigned g = gctr + ci;
+      const int s = (int)(g % a.slots);
+      const unsigned u = g / a.slots;
+      if (!mbar_wait(full + s, u & 1u, a.timeout_cycles)) {
+        set_error(a.err, DEV_TIMEOUT);
+        break;
+      }
+      tc5::fence_after_sync();
+      uint64_t bdesc = bdesc0 + (uint64_t)(((size_t)s * a.slot_bytes) >> 4);
+      const int nb = min(a.kch, klen - ci * a.kch) >> 4;
+      for (int jb = 0; jb < nb; ++jb) {
+        tc5::mma_f16(tmem + acc_col, adesc, bdesc, idesc, acc_on);
+        adesc += 256;  // next 16-k block of G: 4096 bytes
+        bdesc += bstep;
+        acc_col += (uint32_t)NN;
+        if (++acc_n == (uint32_t)kTc5Acc) {
+          acc_n = 0;
+          acc_col = 0;
+          acc_on = 1u;
+        }
+      }
+      tc5::commit(empty + s);  // the slot is free once these MMAs have read it
+    }
+    tc5::commit(accbar);  // always, so that the wait below ends
+  }
+  gctr += nch;
+  const int q = w & 3, h = w >> 2;  // TMEM lane quarter and column half of this warp
+  const int r = 32 * (q & 1) + l;   // block row of this lane (quarters 2, 3 hold the G_lo rows)
+  const int nacc = min(nkb, kTc5Acc);
+  bool ok = true;
+  if (nkb > 0) {
+    ok = mbar_wait(accbar, round & 1u, a.timeout_cycles);
+    ++round;
+    if (!ok) set_error(a.err, DEV_TIMEOUT);
+  }
+  __syncwarp();  // lane 0 of warp 0 issued the MMAs: reconverge before the warp-wide TMEM loads
+  tc5::fence_after_sync();
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+  float* Pr = P + (size_t)r * twp;
+  const int swz = r & ((twp >> 2) - 1);
+  float keep[64];  // G_hi rows: the sums of column part h (X_hi for h = 0, X_lo for h = 1)
+  if (q >= 2) {
+    // G_lo X_hi: 16-column chunks of [0, twp), alternating between the two warps of the quarter
+#pragma unroll 1
+    for (int c0 = 16 * h; c0 < twp; c0 += 32) {
+      float sm[16];
+      tc5_sum16(lane_base, c0, NN, nacc, sm);
+#pragma unroll
+      for (int g4 = 0; g4 < 4; ++g4)
+        *reinterpret_cast<float4*>(Pr + ((((c0 >> 2) + g4) ^ swz) << 2)) =
+            make_float4(sm[4 * g4], sm[4 * g4 + 1], sm[4 * g4 + 2], sm[4 * g4 + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      if (cc * 16 < twp) {
+        float sm[16];
+        tc5_sum16(lane_base, h * twp + cc * 16, NN, nacc, sm);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) keep[cc * 16 + i] = sm[i];
+      }
+    }
+  }
+  tc5::fence_before_sync();
+  // consumer warps only (the producer warp has left): P = G_lo X_hi, then
+  // += G_hi X_lo, then U = (G_hi X_hi + 2^-11 P) 2^e
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+  if (q < 2 && h == 1) {
+#pragma unroll
+    for (int g4 = 0; g4 < 16; ++g4)
+      if (g4 * 4 < twp) {
+        float4* d = reinterpret_cast<float4*>(Pr + ((g4 ^ swz) << 2));
+        const float4 v = *d;
+        *d = make_float4(keep[4 * g4] + v.x, keep[4 * g4 + 1] + v.y, keep[4 * g4 + 2] + v.z, keep[4 * g4 + 3] + v.w);
+      }
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+  if (q < 2 && h == 0) {
+    const float wlo = 1.0f / 2048.0f;
+#pragma unroll
+    for (int g4 = 0; g4 < 16; ++g4)
+      if (g4 * 4 < twp) {
+        float4* d = reinterpret_cast<float4*>(Pr + ((g4 ^ swz) << 2));
+        const float4 v = *d;
+        *d = make_float4(fmaf(wlo, v.x, keep[4 * g4]) * gsi, fmaf(wlo, v.y, keep[4 * g4 + 1]) * gsi,
+                         fmaf(wlo, v.z, keep[4 * g4 + 2]) * gsi, fmaf(wlo, v.w, keep[4 * g4 + 3]) * gsi);
+      }
+  }
+  (void)ok;
+}
+
 // Store X[k][t] = v of a block of twp trials in the layout the kernel form reads:
-// xoff for the FMA forms; for the tensor-core forms the hi and lo parts at
-// [k / 16][part][t][k % 16].  (With X scaled so that |X| <= |c|, FP16 overflows
-// only past |c| = 6.5e4; the explicit Euler step is unstable from about
-// |c| = (2 / (3 dt))^(1/2), 8 at dt = 0.01, so only a run that is already
-// diverging gets there, and then every form yields non-finite amplitudes.)
-template <typename GT, typename CT, bool WIDE, bool TC>
+// xoff for the FMA forms; for the mma.sync tensor-core forms the hi and lo
+// parts at [k / 16][part][t][k % 16]; for the tcgen05 form the parts as rows t
+// and twp + t of the 16-k block's canonical K-major tile.  (With X scaled so
+// that |X| <= |c|, FP16 overflows only past |c| = 6.5e4; the explicit Euler
+// step is unstable from about |c| = (2 / (3 dt))^(1/2), 8 at dt = 0.01, so
+// only a run that is already diverging gets there, and then every form yields
+// non-finite amplitudes.)
+template <typename GT, typename CT, bool WIDE, bool TC, bool TC5>
 __device__ __forceinline__ void xput(CT* Xb, int k, int t, int twp, CT v) {
-  if constexpr (TC) {
+  if constexpr (TC5) {
+    __half* h = reinterpret_cast<__half*>(Xb);
+    const __half hi = __float2half_rn((float)v);
+    const __half lo = __float2half_rn(((float)v - __half2float(hi)) * 2048.f);
+    const size_t blk = (size_t)(k >> 4) * (2 * twp) * 16;
+    h[blk + tc5::canon_off(t, k & 15) / 2] = hi;
+    h[blk + tc5::canon_off(twp + t, k & 15) / 2] = lo;
+  } else if constexpr (TC) {
     using HT = typename tc_x<GT>::type;
     HT* h = reinterpret_cast<HT*>(Xb);
     const HT hi = HT(v);
@@ -706,26 +1012,37 @@ __device__ __forceinline__ void xput(CT* Xb, int k, int t, int twp, CT v) {
   }
 }
 
+// Ring and accumulator state of one CTA that the block products carry across calls.
+struct RingState {
+  unsigned gctr = 0;   // ring uses so far
+  unsigned round = 0; // accumulator rounds of the tcgen05 form so far
+};
+
 // One block of trials: this CTA's partial products in P (rows < nrows).
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC>
+template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC, bool TC5>
 __device__ __forceinline__ void block_partials(const EulerArgs<CT>& a, const GT* __restrict__ Gsm,
                                                const CT* __restrict__ Xblk, int twp, int k0, int klen, int nrows,
                                                int cl, unsigned char* ring, CT* P, uint64_t* full, uint64_t* empty,
-                                               unsigned& gctr, float gsi) {
-  if constexpr (TC) {
+                                               uint64_t* accbar, RingState& rs, float gsi, uint32_t* last,
+                                               uint32_t tmem) {
+  if constexpr (TC5) {
+    tc5_partials(a, reinterpret_cast<const unsigned char*>(Gsm), Xblk, twp, k0, klen, cl, ring, P, full, empty,
+                 accbar, rs.gctr, rs.round, tmem, gsi, last);
+  } else if constexpr (TC) {
     if constexpr (tc_type<GT>::value) {
-      tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, P, full, empty, gctr);
+      tc_partials<GT, MR>(a, Xblk, twp, k0, klen, cl, ring, P, full, empty, rs.gctr, last);
     } else {
-      h3_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, P, full, empty, gctr, gsi);
+      h3_partials<MR>(a, Gsm, Xblk, twp, k0, klen, cl, ring, P, full, empty, rs.gctr, gsi, last);
     }
     // (with one k-warp the partials are already in P; the cluster barrier that
     // follows orders them before any reader)
     if (a.WK > 1) sum_k_warps(a, ring, P, twp, nrows);
   } else if constexpr (WIDE) {
-    wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
+    wide_partials<GT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, rs.gctr, last);
     sum_k_warps(a, ring, P, twp, nrows);
   } else {
-    cluster_partials<GT, CT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, gctr);
+    cluster_partials<GT, CT, MR, STREAM>(a, Gsm, Xblk, twp, k0, klen, nrows, cl, ring, P, full, empty, rs.gctr,
+                                         last);
   }
 }
 
@@ -739,7 +1056,14 @@ __device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, si
   return s;
 }
 
-template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC>
+// Failure discipline: no CTA leaves early.  Every wait on another CTA (the X
+// owners' flags, the ring mbarriers) is bounded and, once the error word is
+// set, stops waiting, so after a timeout every CTA still runs the remaining
+// steps (on stale data; the solve reports CS_ETIMEOUT) and meets its cluster at
+// every cluster barrier.  At the end a CTA lets the bulk copies it issued land
+// (bounded waits), and the tcgen05 form waits for its MMAs and frees its TMEM,
+// before the cluster leaves together (peers read each other's shared memory).
+template <typename GT, typename CT, int MR, bool STREAM, bool WIDE, bool TC, bool TC5>
 __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -767,17 +1091,33 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   CT* R_s = b_s + (size_t)a.ORW * T;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
   uint64_t* empty = full + a.slots;
+  uint64_t* accbar = empty + a.slots;
+  uint32_t* misc = reinterpret_cast<uint32_t*>(accbar + 1);
+  uint32_t* last = misc + 1;  // per ring slot: last use issued + 1; last[kMaxSlots]: X version to read
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.slots; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, kConsumerWarps);
+      mbar_init(empty + i, TC5 ? 1 : kConsumerWarps);
     }
+    mbar_init(accbar, 1);
+    for (int i = 0; i <= kMaxSlots; ++i) last[i] = 0;
     fence_mbar_init();
   }
+  if constexpr (TC5) {
+    __syncwarp();
+    if (threadIdx.x < 32) {
+      tc5::tmem_alloc(misc, kTc5Cols);
+      tc5::tmem_relinquish();
+      tc5::fence_before_sync();
+    }
+  }
   // Stage this CTA's block of G_off: rows [row0, row0 + nrows), k in [k0, k0 + klen).
-  float gsi = 1.f;  // scale of the staged block (FP32 tensor-core form)
-  if constexpr (TC && !STREAM) {
+  float gsi = 1.f;  // scale of the staged block (FP32 tensor-core forms)
+  if constexpr (TC5) {
+    gsi = stage_tc5(reinterpret_cast<const float*>(a.Gs), Npad, row0, nrows, k0, klen,
+                    reinterpret_cast<unsigned char*>(Gsm), reinterpret_cast<float*>(P));
+  } else if constexpr (TC && !STREAM) {
     gsi = stage_h3(reinterpret_cast<const float*>(a.Gs), Npad, row0, nrows, k0, klen, a.RPC_pad,
                    reinterpret_cast<float*>(Gsm), reinterpret_cast<float*>(P));
   } else if (!STREAM) {
@@ -802,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     const int r = idx / T, t = idx % T;
     R_s[idx] = CT(a.R[(size_t)(row0 + own0 + r) * T + t]);
   }
-  // scale of X (tensor-core form): 2^-e with max |R| < 2^e; every CTA forms it
+  // scale of X (tensor-core forms): 2^-e with max |R| < 2^e; every CTA forms it
   // from all of R, so all agree without communication
   CT xsc = CT(1), xsi = CT(1);
   if constexpr (TC) {
@@ -820,30 +1160,68 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     xsi = CT(ldexp(1.0, ex));
   }
   __syncthreads();
-  unsigned gctr = 0;
+  uint32_t tmem = 0;
+  if constexpr (TC5) {
+    tc5::fence_after_sync();
+    tmem = misc[0];
+  }
+  RingState rs;
   const double st = sqrt(a.tau);
   const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
-  unsigned bar_k = 0;
+  unsigned pub = 0;  // X versions this CTA has published (the same count in every thread)
+
+  // Publish this CTA's rows of the X just written: every thread orders its X
+  // stores before later async-proxy reads, the CTA synchronises (the next
+  // version to read goes to shared memory for the producer warp), and thread 0
+  // releases the version on the CTA's flag.
+  auto publish = [&]() {
+    fence_proxy_async_global();
+    ++pub;
+    if (threadIdx.x == 0) last[kMaxSlots] = pub;
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_gpu(a.flags + blockIdx.x, pub);
+  };
+  // the exit: bulk copies in flight land, MMAs complete, TMEM is freed, then
+  // the cluster leaves together
+  auto leave = [&]() {
+    if (threadIdx.x == kConsumerWarps * 32) {
+      for (int s = 0; s < a.slots; ++s)
+        if (last[s] > 0) (void)mbar_wait(full + s, ((last[s] - 1) / (unsigned)a.slots) & 1u, a.timeout_cycles);
+    }
+    if constexpr (TC5) {
+      if (threadIdx.x == 0 && klen >= 16) {
+        tc5::commit(accbar);
+        (void)mbar_wait(accbar, rs.round & 1u, a.timeout_cycles);
+      }
+      tc5::fence_before_sync();
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        tc5::fence_after_sync();
+        tc5::tmem_dealloc(tmem, kTc5Cols);
+      }
+    }
+    cluster.sync();
+  };
 
   // ---- prologue: b (or q), initial c and e, first X.
   if (a.field == CS_FIELD_CN) {
     for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
       const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-      xput<GT, CT, WIDE, TC>(a.X0 + xblock(t0, Npad), row0 + own0 + r, t - t0, twp,
-                             CT(a.R[(size_t)(row0 + own0 + r) * T + t]) * xsc);
+      xput<GT, CT, WIDE, TC, TC5>(a.X0 + xblock(t0, Npad), row0 + own0 + r, t - t0, twp,
+                                  CT(a.R[(size_t)(row0 + own0 + r) * T + t]) * xsc);
     }
-    fence_proxy_async_global();
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
+    publish();
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring,
-                                                    P, full, empty, gctr, gsi);
+      block_partials<GT, CT, MR, STREAM, WIDE, TC, TC5>(a, Gsm, a.X0 + xblock(t0, Npad), twp, k0, klen, nrows, cl,
+                                                         ring, P, full, empty, accbar, rs, gsi, last, tmem);
       cluster.sync();
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         const int gr = row0 + own0 + r;
-        const CT v = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr) * xsi;
+        const CT v = sum_partials(cluster, P, (size_t)pidx<TC5>(own0 + r, tt, twp), C) *
+                     row_scale<GT, CT>(a.gscale, gr) * xsi;
         const double Rr = a.R[(size_t)gr * T + t0 + tt];
         b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
       }
@@ -865,11 +1243,10 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     e_s[idx] = CT(1);
     const CT Rr = R_s[idx];
     const int t0 = t - t % kTChunk, twp = xwidth(t0, T);
-    xput<GT, CT, WIDE, TC>(a.X1 + xblock(t0, Npad), gr, t - t0, twp,
-                           ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
+    xput<GT, CT, WIDE, TC, TC5>(a.X1 + xblock(t0, Npad), gr, t - t0, twp,
+                                ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
   }
-  fence_proxy_async_global();
-  if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) { cluster.sync(); return; }
+  publish();
 
   // ---- Euler steps
   const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
@@ -877,18 +1254,19 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   CT* Xn = a.X0;
   for (int n = 0; n < a.n_steps; ++n) {
     const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
-    const bool last = (n + 1 == a.n_steps);
+    const bool last_step = (n + 1 == a.n_steps);
     const bool rec = n < a.record_steps;
     for (int t0 = 0; t0 < T; t0 += kTChunk) {
       const int tw = min(kTChunk, T - t0), twp = round4(tw);
-      block_partials<GT, CT, MR, STREAM, WIDE, TC>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring, P,
-                                                    full, empty, gctr, gsi);
+      block_partials<GT, CT, MR, STREAM, WIDE, TC, TC5>(a, Gsm, Xc + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring,
+                                                         P, full, empty, accbar, rs, gsi, last, tmem);
       cluster.sync();
       CT* Xnb = Xn + xblock(t0, Npad);
       for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
         const int r = idx / tw, tt = idx % tw;
         const int gr = row0 + own0 + r;
-        const CT U = sum_partials(cluster, P, (size_t)(own0 + r) * twp + tt, C) * row_scale<GT, CT>(a.gscale, gr) * xsi;
+        const CT U = sum_partials(cluster, P, (size_t)pidx<TC5>(own0 + r, tt, twp), C) *
+                     row_scale<GT, CT>(a.gscale, gr) * xsi;
         const size_t so = (size_t)r * T + t0 + tt;
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
@@ -898,25 +1276,24 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
         c_s[so] = cn;
         e_s[so] = en;
-        xput<GT, CT, WIDE, TC>(Xnb, gr, tt, twp, ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
+        xput<GT, CT, WIDE, TC, TC5>(Xnb, gr, tt, twp,
+                                    ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
         const size_t o = (size_t)gr * T + t0 + tt;
         if (rec) {
           const size_t ro = (size_t)n * N * T + o;
           a.rec_c[ro] = (double)cn;
           a.rec_e[ro] = (double)en;
         }
-        if (last) a.sigma[o] = cn > CT(0) ? 1 : 0;
+        if (last_step) a.sigma[o] = cn > CT(0) ? 1 : 0;
       }
       // every CTA of the cluster has read this CTA's partials before they are rewritten
       if (t0 + kTChunk < T) cluster.sync();
     }
-    if (last) break;
-    // the next X is read by bulk copies (async proxy) of every CTA after the barrier
-    fence_proxy_async_global();
-    if (!grid_barrier(a.bar, ++bar_k, a.err, a.timeout_cycles, a.phantom)) break;
+    if (last_step) break;
+    publish();  // the next X, read by bulk copies (async proxy) of the CTAs whose k range holds these rows
     CT* tmp = Xc; Xc = Xn; Xn = tmp;
   }
-  cluster.sync();  // peers may still read this CTA's partials
+  leave();  // peers may still read this CTA's partials until the cluster leaves together
 }
 
 }  // namespace

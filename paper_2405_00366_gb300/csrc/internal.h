@@ -26,6 +26,9 @@ enum { TM_GRAM = 0, TM_EULER = 1, TM_REFIT = 2, TM_OTHER = 3, TM_COUNT = 4 };
 // the 32-column tiles of the streamed layout).
 constexpr int64_t kPadN = 32;
 
+// Largest grid of the persistent Euler kernel (one CTA per SM at most).
+constexpr int kMaxEulerCtas = 1024;
+
 // Device buffers of one problem (all owned by the library).
 struct ProblemDev {
   int64_t M = 0, N = 0, Npad = 0;  // Npad: N rounded up to a multiple of kPadN
@@ -94,7 +97,7 @@ struct SolveDev {
   double* x_hat = nullptr;      // N, kept trial
   uint8_t* sigma_hat = nullptr; // N
   double* stats = nullptr;      // CS_STATS_LEN
-  unsigned* bar = nullptr;      // grid barrier counter
+  unsigned* bar = nullptr;      // Euler kernel: per-CTA X publication flags (kMaxEulerCtas + 1 words)
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
   RefitJob* job = nullptr;      // this problem's refit job (device copy)

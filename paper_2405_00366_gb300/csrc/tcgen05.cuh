@@ -1,0 +1,158 @@
+// Inline-PTX wrappers for the fifth-generation tensor cores of sm_100-class
+// GPUs (tcgen05): tensor-memory (TMEM) allocation, the single-thread MMA with
+// shared-memory operand descriptors and a TMEM accumulator, its completion on
+// an mbarrier, and warp loads of the accumulator back to registers.
+//
+// Operand layout used throughout (the "no swizzle", K-major canonical form of
+// the PTX ISA's shared-memory matrix descriptors): a matrix of R rows x 16 k of
+// a 16-bit type is a grid of core matrices, each 8 rows x 8 k (16 bytes per
+// row, the 8 rows contiguous: 128 bytes).  Core matrix (row group i, k half h)
+// starts at  base + i * SBO + h * LBO.  This library always uses
+// LBO = 128 (the two k halves of a row group adjacent) and SBO = 256 (row
+// groups back to back), so one 16-k block of R rows is R * 32 contiguous bytes:
+//   element (r, k) at  (r / 8) * 256 + ((k / 8) & 1) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// Consecutive 16-k blocks follow each other (R * 32 bytes apart).
+//
+// Accumulator layout for M = 128 with one CTA (cta_group::1): row i of D is
+// TMEM lane i, column j of D is TMEM column (base + j), FP32.  Warp w of a CTA
+// may read only lanes 32 (w % 4) .. 32 (w % 4) + 31.
+#pragma once
+
+#include <stdint.h>
+
+namespace cs {
+namespace tc5 {
+
+// ------------------------------------------------------------------ descriptors
+// Shared-memory matrix descriptor (64 bits): start address >> 4 in bits 0-13,
+// leading-dimension byte offset >> 4 in bits 16-29, stride-dimension byte
+// offset >> 4 in bits 32-45, the descriptor version 1 in bits 46-47, base
+// offset 0 (bits 49-51), absolute leading offsets (bit 52 = 0) and layout
+// "no swizzle" (bits 61-63 = 0).  Addresses are shared-window byte addresses
+// (below 2^18), multiples of 16.
+__host__ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor (32 bits) of a dense kind::f16 MMA with FP16 A and B,
+// FP32 accumulation, both operands K-major: D format F32 (1) in bits 4-5, A and
+// B format F16 (0) in bits 7-9 and 10-12, no negation (bits 13-14), K-major A
+// and B (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+// M = 128 (one CTA); N a multiple of 16 in [16, 256].
+__host__ __device__ __forceinline__ uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) inside one 16-k block of the canonical layout.
+__host__ __device__ __forceinline__ uint32_t canon_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+constexpr uint32_t kLBO = 128, kSBO = 256;
+
+// ------------------------------------------------------------------ TMEM
+// Allocate `ncols` TMEM columns (a power of two in [32, 512]) for this CTA and
+// write their address to the shared word `dst`.  Executed by one whole warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s), "r"(ncols) : "memory");
+}
+// Give up the right to allocate more (lets other CTAs on the SM allocate).
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// Free an allocation.  Executed by the warp that allocated it.
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Ordering of tcgen05 operations across thread synchronisation.
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ MMA
+// D[tmem] (+)= A B^T for A (M x 16) and B (N x 16), both K-major in shared
+// memory, issued by one thread.  accumulate = 0 overwrites D.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// One arrival on the mbarrier `bar` (this CTA's shared memory) once every
+// tcgen05 MMA issued so far by this thread has completed (its shared-memory
+// operands are free and its accumulator is written).
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s) : "memory");
+}
+
+// ------------------------------------------------------------------ loads
+// 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: lane
+// 32 (warp % 4) + lane id), starting at taddr's column.  The load and its
+// completion wait are one asm statement, so the registers are valid on return.
+// Executed by a whole warp.
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns, as ld32.
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns from each of four accumulators (columns
+// taddr + a * stride, a = 0..3), summed in the fixed order 0 + 1 + 2 + 3 with
+// round-to-nearest additions; four loads and one completion wait.
+__device__ __forceinline__ void ld16x4_sum(uint32_t taddr, uint32_t stride, float (&v)[16]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride), "r"(taddr + 3 * stride)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+    v[i] = ((__uint_as_float(r[i]) + __uint_as_float(r[16 + i])) + __uint_as_float(r[32 + i])) +
+           __uint_as_float(r[48 + i]);
+}
+
+// TMEM address of lane `lane`, column `col` relative to an allocation at `base`.
+__device__ __forceinline__ uint32_t taddr(uint32_t base, int lane, int col) {
+  return base + ((uint32_t)lane << 16) + (uint32_t)col;
+}
+
+}  // namespace tc5
+}  // namespace cs

@@ -90,3 +90,50 @@ def test_planted_refit_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(om, "refit_exact", wrong)
     monkeypatch.setattr(oracle, "refit_exact", wrong)
     assert _fails(pins.test_refit_matches_lstsq_and_is_jacobi_fixed_point)
+
+
+def _jacobi_undamped(Goff, hz, g, sigma, R, dtc, iters):
+    s = sigma.astype(float)
+    for _ in range(iters):
+        R = (hz - Goff @ (s * R)) / g
+    return R
+
+
+def _jacobi_complement_step(Goff, hz, g, sigma, R, dtc, iters):
+    s = sigma.astype(float)
+    for _ in range(iters):
+        R = R + (1.0 - dtc) * ((hz - Goff @ (s * R)) / g - R)
+    return R
+
+
+def _jacobi_ignores_sigma(Goff, hz, g, sigma, R, dtc, iters):
+    for _ in range(iters):
+        R = R + dtc * ((hz - Goff @ R) / g - R)
+    return R
+
+
+def _jacobi_gauss_seidel(Goff, hz, g, sigma, R, dtc, iters):
+    s = sigma.astype(float)
+    R = R.copy()
+    for _ in range(iters):
+        for r in range(R.size):
+            R[r] = R[r] + dtc * ((hz[r] - Goff[r] @ (s * R)) / g[r] - R[r])
+    return R
+
+
+def _jacobi_extra_sweep(Goff, hz, g, sigma, R, dtc, iters):
+    s = sigma.astype(float)
+    for _ in range(iters + 1):
+        R = R + dtc * ((hz - Goff @ (s * R)) / g - R)
+    return R
+
+
+@pytest.mark.parametrize("fake", [_jacobi_undamped, _jacobi_complement_step, _jacobi_ignores_sigma,
+                                  _jacobi_gauss_seidel, _jacobi_extra_sweep])
+def test_planted_jacobi_mistake_is_caught(monkeypatch, fake):
+    """An undamped sweep, the step applied as (1 - dtc), the support ignored, an
+    in-place (Gauss-Seidel) sweep and one sweep too many each fail the hand-worked
+    two-sweep pin."""
+    monkeypatch.setattr(om, "refit_jacobi", fake)
+    monkeypatch.setattr(oracle, "refit_jacobi", fake)
+    assert _fails(pins.test_damped_jacobi_two_sweeps_hand_worked)

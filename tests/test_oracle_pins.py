@@ -166,6 +166,30 @@ def test_refit_singular_support_uses_ridge():
     np.testing.assert_allclose(R, mn, rtol=0, atol=1e-3 * np.abs(mn).max())
 
 
+def jacobi_golden():
+    rows = {}
+    with open(os.path.join(GOLDEN, "jacobi_two_sweeps.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#") and not line.startswith("name"):
+                name, *vals = line.split()
+                rows[name] = np.array([float(v) for v in vals])
+    return rows
+
+
+def test_damped_jacobi_two_sweeps_hand_worked():
+    """The damped step R <- R + dtc (R~ - R) and the sweep count, against two sweeps
+    worked by hand (tests/golden/jacobi_two_sweeps.txt)."""
+    G = np.array([[2.0, 0.5, -0.25], [0.5, 1.0, 0.0], [-0.25, 0.0, 4.0]])
+    g = np.diag(G).copy()
+    hz = np.array([0.5, -1.0, 0.25])
+    sigma = np.array([1, 1, 0], dtype=np.uint8)
+    R0 = np.array([1.0, 2.0, -1.0])
+    gold = jacobi_golden()
+    for iters, key in ((1, "R1"), (2, "R2")):
+        R = oracle.refit_jacobi(G - np.diag(g), hz, g, sigma, R0.copy(), 0.1, iters)
+        np.testing.assert_allclose(R, gold[key], rtol=0, atol=1e-15)
+
+
 def test_jacobi_refit_converges_to_exact():
     inst = cs_inputs.random_instance(100, 70, 10, 0.05, 0.1, seed=8)
     G, hz, g = oracle.gram(inst.A, inst.y)

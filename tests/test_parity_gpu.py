@@ -91,15 +91,22 @@ def test_trajectory_fp64_single():
     assert rel_traj_err(e, r["trajectory"][1]).max() <= 1e-10
 
 
-@pytest.mark.parametrize("field,form", [("cn", 1), ("bn", 1), ("cn", 2), ("bn", 2)])
+# stats[10] of each tensor_form for FP32 problems with trial blocks of 16 to 64:
+# 1 FMA forms (0 or 1), 2 any tensor-core form (2 or 5), 3 mma.sync (2), 4 tcgen05 (5)
+FORM_STAT = {1: (0, 1), 2: (2, 5), 3: (2,), 4: (5,)}
+
+
+@pytest.mark.parametrize("field,form", [("cn", 1), ("bn", 1), ("cn", 4), ("bn", 4), ("cn", 3), ("bn", 3)])
 def test_trajectory_fp32_trials64(field, form):
     """The N = 2000, M = 1200, 64-trial workload: the first 200 Euler steps of every
-    trial, with FP32 FMAs (tensor_form = 1) and with the FP32 tensor-core form (2:
-    three FP16 MMAs on split operands)."""
+    trial, with FP32 FMAs (tensor_form = 1), on the tcgen05 tensor cores (4: one
+    M = 128 MMA per 16-k block on the stacked FP16 splits of G and X, TMEM
+    accumulators) and on the mma.sync tensor cores (3: three FP16 MMAs on split
+    operands)."""
     w = cs_inputs.workload("trials64_n2000_fp32", n_outer=1, field=field, tensor_form=form)
     inst = cs_inputs.workload_instance(w)
     g = gpu_solve(inst, w, 64, record_steps=200)
-    assert (g["stats"][10] == 2) == (form == 2)
+    assert g["stats"][10] in FORM_STAT[form]
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=64, record_steps=200, max_steps=200)
     c, e = g["trajectory"]
     err_c = rel_traj_err(c, r["trajectory"][0])
@@ -144,16 +151,18 @@ def test_solve_ragged(precision, field):
     _compare_solve(g, r, inst, 5, 1e-9 if precision == "fp64" else 1e-5, precision == "fp64")
 
 
-@pytest.mark.parametrize("trials,cluster,field", [(16, 0, "cn"), (32, 2, "bn"), (64, 1, "cn"), (64, 8, "bn")])
-def test_solve_ragged_fp32_tensor_cores(trials, cluster, field):
-    """The FP32 tensor-core form (three FP16 MMAs on split operands, tensor_form = 2)
-    on N = 333 (ragged row tiles and k blocks): whole solves against the oracle to
-    the FP32 tolerances."""
+@pytest.mark.parametrize("trials,cluster,field,form", [(16, 0, "cn", 4), (32, 2, "bn", 4), (64, 1, "cn", 4),
+                                                        (64, 8, "bn", 4), (128, 4, "cn", 4), (16, 0, "cn", 3),
+                                                        (64, 8, "bn", 3), (32, 0, "cn", 2)])
+def test_solve_ragged_fp32_tensor_cores(trials, cluster, field, form):
+    """The FP32 tensor-core forms (tcgen05: tensor_form = 4; mma.sync: 3; either: 2) on N = 333
+    (ragged row blocks and k ranges; 128 trials: two blocks of 64 in one launch):
+    whole solves against the oracle to the FP32 tolerances."""
     inst = cs_inputs.random_instance(333, 211, 30, 0.01, 0.04, seed=7)
     w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=4, n_steps=600, precision="fp32", field=field,
-             seed=11, tensor_form=2, cluster_size=cluster)
+             seed=11, tensor_form=form, cluster_size=cluster)
     g = gpu_solve(inst, w, trials)
-    assert g["stats"][10] == 2
+    assert g["stats"][10] in FORM_STAT[form]
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=trials)
     _compare_solve(g, r, inst, trials, 1e-5, False)
 
@@ -258,13 +267,17 @@ def test_two_trial_blocks_match_oracle():
 def test_trials64_full_size_properties():
     """The N = 2000, 64-trial workload at full size (30 x 2000 steps), in the launch
     configuration the benchmark times (autotuned work split).  The oracle runs trials 0
-    and 1 for the first two outer iterations; the rest is checked by properties that hold
-    at any size."""
+    and 1 for the first two outer iterations, and the same launch configuration stopped
+    after two outer iterations must give their supports exactly and R to 1e-5; the full
+    run is checked by properties that hold at any size."""
     w = cs_inputs.workload("trials64_n2000_fp32", autotune=1)
     inst = cs_inputs.workload_instance(w)
     g = gpu_solve(inst, w, 64)
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(dict(w, n_outer=2)), trials=2)
     np.testing.assert_array_equal(g["support_sizes"][:2, :2], r["support_sizes"])
+    g2 = gpu_solve(inst, dict(w, n_outer=2), 64)
+    np.testing.assert_array_equal(g2["sigmas"][:, :2], r["sigmas"])
+    np.testing.assert_allclose(g2["R"][:, :2], r["R"], rtol=0, atol=1e-5)
     G, hz, gd = oracle.gram(inst.A, inst.y)
     for t in range(64):
         s = g["sigmas"][:, t]

@@ -13,12 +13,16 @@ import pytest
 import torch
 
 import cs_inputs
+import oracle
 from paper_2405_00366_gb300 import cs
 
 pytestmark = pytest.mark.gpu
 
 
 def test_objective_static_matches_solver_energies_twice():
+    """Two calls in a row through the C ABI: each equals the solver's own per-trial
+    energies (the allocating path) and the FP64 oracle's objective (Eq. doublel0)
+    of the same (R, sigma), to 1e-12 relative."""
     w = cs_inputs.workload("trials64_n2000_fp32", n_outer=2, n_steps=400)
     inst = cs_inputs.workload_instance(w)
     T = 8
@@ -40,7 +44,10 @@ def test_objective_static_matches_solver_energies_twice():
                                           inst.M, inst.N, T, inst.lam, P(out.data_ptr()), None)
         assert st == cs.CS_OK, cs.cs_last_error()
         torch.cuda.synchronize()
-        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=0)
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+        orc = [oracle.objective(inst.A, inst.y, sig[:, t] * R[:, t], sig[:, t], inst.lam) for t in range(T)]
+        np.testing.assert_allclose(got, orc, rtol=1e-12, atol=0)
 
 
 def test_objective_static_rejects_sizes_beyond_its_scratch():
