@@ -145,9 +145,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
       if (C > nq || sms < C) continue;
       // variants: wide with WK = 1, 2, 4, 8 k-warps, narrow (WK = 0), the
       // mma.sync tensor-core forms with WK = 1, 2, 4, 8 (v = 5 .. 8) and the
-      // tcgen05 form (v = 9, resident only)
-      for (int v = 0; v < 10; ++v) {
-        const bool tc5 = v == 9;
+      // tcgen05 form (resident only) with 16 KB (v = 9) or 32 KB (v = 10) X chunks
+      for (int v = 0; v < 11; ++v) {
+        const bool tc5 = v >= 9;
+        const int xchunk = v == 10 ? 32768 : 16384;
         const bool tc = v >= 5;
         const int WK = tc5 ? 1 : (tc ? 1 << (v - 5) : (v < 4 ? 1 << v : 0));
         const bool wide = WK > 0;
@@ -170,8 +171,10 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
         } else {
           pl.kq = (nq + C - 1) / C;
           if (tc) pl.kq = (pl.kq + 3) / 4 * 4;  // whole blocks of 16 k per rank
-          // 16 KB of X per bulk copy (measured: fewer, larger chunks cut the ring overhead)
-          pl.kch = std::max(4, std::min(pl.kq * 4, (int)((16384 / (twmax * sizeof(CT))) & ~(size_t)3)));
+          // 16 KB (or 32 KB) of X per bulk copy: each copy costs about 350 clocks of
+          // the copy engine whatever its size up to 32 KB (measured on GB300), so
+          // fewer, larger chunks stream X faster
+          pl.kch = std::max(4, std::min(pl.kq * 4, (int)((xchunk / (twmax * sizeof(CT))) & ~(size_t)3)));
         }
         // resident G rows: an odd number of quads apart, so the rows a half-warp
         // reads start in different banks
@@ -229,7 +232,7 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             const size_t gtile = stream ? (size_t)tps * pl.RPC_pad * kStreamK * sizeof(GT) : 0;
             pl.xoff = align128(gtile);
             pl.slot_bytes = align128(pl.xoff + (size_t)pl.kch * twmax * sizeof(CT));
-            const int min_slots = (stream && tps > 1) ? 3 : (stream ? 2 : 3);
+            const int min_slots = (stream && tps > 1) ? 3 : ((stream || tc5) ? 2 : 3);
             for (int slots = 8; slots >= min_slots; --slots) {
               if ((size_t)slots * pl.slot_bytes < kpart) break;  // the ring holds the k-warp partials
               pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
@@ -268,13 +271,15 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
               stream ? (double)pl.RPC_pad * pl.kq * 4 * sizeof(GT) * std::max(1.0, 128.0 / pl.kch) : 0.0;
           double cost;
           if (tc5) {
-            // one M = 128 MMA per 16-k block (about 176 clocks each on GB300 for
-            // any N up to 256, measured), the epilogue's TMEM loads (kTc5Acc
-            // accumulators, 16 columns per load), X bytes as for the other forms
+            // one M = 128 MMA per 16-k block (64 clocks at N = 128, about 45 at
+            // N <= 64, measured on GB300) overlapping the X stream (about 360
+            // clocks per bulk copy of up to 32 KB, measured), then the
+            // epilogue's TMEM loads (four accumulators per 16 columns)
             const double nkb = pl.kq * 4 / 16.0;
-            const double mma = nkb * nblk * 176.0;
-            const double epi = nblk * (twmax / 16.0) * kTc5Acc * 2.0 * 40.0;
-            cost = mma + xbytes / 44.0 + epi;
+            const double mma = nkb * nblk * (twmax >= 64 ? 64.0 : 48.0);
+            const double copies = std::ceil(pl.kq * 4.0 / pl.kch) * nblk * 360.0;
+            const double epi = nblk * (twmax / 16.0) * 400.0;
+            cost = std::max(mma, copies) + epi + 256.0;
           } else if (tc && stream) {
             // MMAs (two per 16 x 16 tile of G_off: the two parts of X), taken at
             // one per two clocks per SM (measured on GB300), overlap the streamed bytes

@@ -1056,6 +1056,40 @@ __device__ __forceinline__ CT sum_partials(cg::cluster_group& cluster, CT* P, si
   return s;
 }
 
+// kUpd elements per thread per pass of the update: their C x kUpd remote
+// partials are all loaded before any is summed (the distributed-shared-memory
+// latency is paid once per pass, not once per load); each sum keeps the fixed
+// order 0 + P_0 + P_1 + ... of sum_partials.
+constexpr int kUpd = 4;
+template <int CC, typename CT>
+__device__ __forceinline__ void gather_sums(cg::cluster_group& cluster, const CT* P, const int (&off)[kUpd],
+                                            const bool (&val)[kUpd], CT (&out)[kUpd]) {
+  CT v[kUpd][CC];
+#pragma unroll
+  for (int jj = 0; jj < CC; ++jj) {
+    const CT* Pj = cluster.map_shared_rank(P, jj);
+#pragma unroll
+    for (int k = 0; k < kUpd; ++k) v[k][jj] = val[k] ? Pj[off[k]] : CT(0);
+  }
+#pragma unroll
+  for (int k = 0; k < kUpd; ++k) {
+    CT s = CT(0);
+#pragma unroll
+    for (int jj = 0; jj < CC; ++jj) s += v[k][jj];
+    out[k] = s;
+  }
+}
+template <typename CT>
+__device__ __forceinline__ void gather_sums_c(cg::cluster_group& cluster, const CT* P, int C, const int (&off)[kUpd],
+                                              const bool (&val)[kUpd], CT (&out)[kUpd]) {
+  switch (C) {
+    case 1: gather_sums<1>(cluster, P, off, val, out); break;
+    case 2: gather_sums<2>(cluster, P, off, val, out); break;
+    case 4: gather_sums<4>(cluster, P, off, val, out); break;
+    default: gather_sums<8>(cluster, P, off, val, out); break;
+  }
+}
+
 // Failure discipline: no CTA leaves early.  Every wait on another CTA (the X
 // owners' flags, the ring mbarriers) is bounded and, once the error word is
 // set, stops waiting, so after a timeout every CTA still runs the remaining
@@ -1262,11 +1296,25 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
                                                          P, full, empty, accbar, rs, gsi, last, tmem);
       cluster.sync();
       CT* Xnb = Xn + xblock(t0, Npad);
-      for (int idx = threadIdx.x; idx < nown * tw; idx += kThreads) {
+      const int nel = nown * tw;
+      for (int base = threadIdx.x; base < nel; base += kUpd * kThreads) {
+        int off[kUpd];
+        bool val[kUpd];
+        CT Us[kUpd];
+#pragma unroll
+        for (int k = 0; k < kUpd; ++k) {
+          const int idx = base + k * kThreads;
+          val[k] = idx < nel;
+          off[k] = val[k] ? pidx<TC5>(own0 + idx / tw, idx % tw, twp) : 0;
+        }
+        gather_sums_c(cluster, P, C, off, val, Us);
+#pragma unroll
+        for (int k = 0; k < kUpd; ++k) {
+        const int idx = base + k * kThreads;
+        if (!val[k]) continue;
         const int r = idx / tw, tt = idx % tw;
         const int gr = row0 + own0 + r;
-        const CT U = sum_partials(cluster, P, (size_t)pidx<TC5>(own0 + r, tt, twp), C) *
-                     row_scale<GT, CT>(a.gscale, gr) * xsi;
+        const CT U = Us[k] * row_scale<GT, CT>(a.gscale, gr) * xsi;
         const size_t so = (size_t)r * T + t0 + tt;
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
@@ -1285,6 +1333,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
           a.rec_e[ro] = (double)en;
         }
         if (last_step) a.sigma[o] = cn > CT(0) ? 1 : 0;
+        }
       }
       // every CTA of the cluster has read this CTA's partials before they are rewritten
       if (t0 + kTChunk < T) cluster.sync();
