@@ -425,7 +425,7 @@ def run_serve(args):
         for _, inst, w, T in reqs:
             seen.setdefault((inst.N, w["precision"]), (inst, w, T))
         for inst, w, T in seen.values():
-            tk = cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
+            tk = cs.cs_server_submit_host(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
             cs.cs_server_wait(sv, tk)
             cs.cs_server_result(sv, tk, inst.N)
     finally:
@@ -440,7 +440,7 @@ def run_serve(args):
                 while time.perf_counter() - t0 < arr:
                     time.sleep(min(0.001, arr - (time.perf_counter() - t0)))
                 tickets.append((time.perf_counter(),
-                                cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)))
+                                cs.cs_server_submit_host(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)))
             lat, rmse = [], []
             for (ts, tk), (arr, inst, w, T) in zip(tickets, reqs):
                 cs.cs_server_wait(sv, tk)

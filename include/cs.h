@@ -19,6 +19,9 @@
  *    cs_problem_destroy.
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is queued on it in order.
+ *  - Threads: calls on different problems (and servers) may be made from
+ *    different host threads at the same time; calls on one problem must not
+ *    overlap each other.
  *  - Matrices are row-major.  Per-trial arrays are laid out [r][t]: element
  *    (r, t) of an N x T array is at r * T + t.
  */
@@ -134,19 +137,24 @@ cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t
  * Errors: CS_EINVAL for bad parameters or trials < 1; CS_ENOMEM; CS_ECUDA. */
 cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
 
-/* Queue one full solve (Algorithm 1) of every problem ps[0..n) with the same
- * parameters and `trials` (<= 64) trials each, as a batch: each outer iteration
- * of all problems is one persistent launch in which every CTA takes whole
- * problems from a device work queue (largest N first) and streams that
- * problem's G_off tiles from memory, then one refit launch covers every
- * (problem, trial).  All outer iterations and the objective are captured
- * into one CUDA graph, submitted to the problems' stream as a single launch.
- * Problem i draws its initial amplitudes with instance number i.  All problems
- * must have been created on the same device and stream.  Results are read per
- * problem with cs_result / cs_result_trials.
+/* Queue one full solve (Algorithm 1) of every problem ps[0..n) as a batch:
+ * problem i with its own parameters *prm[i] and trials[i] (<= 64) trials.
+ * Problems that share a storage precision, a trial count and the tensor-core
+ * decision form a group; each outer iteration of a group is one persistent
+ * launch in which every CTA takes whole problems from a device work queue
+ * (largest N first) and streams that problem's G_off tiles from memory, then
+ * one refit launch covers every (problem, trial) of the group.  A problem
+ * leaves the batch after its own n_outer iterations.  All outer iterations and
+ * the objective are captured into one CUDA graph, submitted to the problems'
+ * stream as a single launch.  Problem i draws its initial amplitudes with
+ * instance number i (prm[i]->instance is not used).  All problems must have
+ * been created on the same device and stream and appear once each.  Results
+ * are read per problem with cs_result / cs_result_trials.
+ * ps, prm and trials are host arrays of n entries.
  * Errors: CS_EINVAL (parameters, trials > 64, record_steps != 0, mixed
- * streams), CS_ENOMEM, CS_ECUDA. */
-cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials);
+ * streams, a problem given twice, tensor_form >= 2 without a batched
+ * tensor-core form), CS_ENOMEM, CS_ECUDA. */
+cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prm, const int32_t* trials, int32_t n);
 
 /* Wait for the last solve and copy out the kept trial (lowest energy, ties to
  * the lower trial index): x_hat = sigma o R (N doubles), sigma_hat (N bytes,
@@ -159,9 +167,16 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
  *   [10] form of the Euler kernel: 0 FP32/FP64 FMAs (narrow split), 1 packed FP32
  *        FMAs (wide split), 2 tensor cores (mma.sync), 3 batched (one problem per CTA),
  *        4 batched on tensor cores (mma.sync), 5 tensor cores (tcgen05, TMEM)
+ *   [11] error of the coupling against FP64: max_r |(G_off^s x_hat)_r - (G_off x_hat)_r|
+ *        / max_r |(G_off x_hat)_r|, G_off^s being G_off rounded to the storage precision
+ *        the Euler kernels used (0 for FP64), both products formed in FP64
+ *   [12] FP64 residual of the refit: max over the support of |h^z_r - (G x_hat)_r| /
+ *        max over the support of |h^z_r| (the normal equations G_SS R_S = h^z_S of
+ *        Algorithm 1's refit; about 1e-15 for the exact refit, larger with the ridge
+ *        or the damped Jacobi refit)
  * Host pointers.  Returns CS_ETIMEOUT if a device wait timed out,
  * CS_ESINGULAR (with valid outputs) if the ridge was needed. */
-#define CS_STATS_LEN 11
+#define CS_STATS_LEN 13
 cs_status cs_result(cs_problem* p, double* x_hat, uint8_t* sigma_hat, double* energy,
                     double* stats);
 
@@ -227,9 +242,10 @@ void cs_problem_destroy(cs_problem* p);
  * are scanned in arrival order; each is admitted when a slot is free, its
  * device-memory estimate fits what is left of `hbm_budget_bytes` and its grid
  * fits the SMs not held by running requests (a request that does not fit yet
- * does not hold back smaller ones behind it).  An admitted request forms its
- * problem (Gram on the GPU) and queues its solve on its slot's stream with
- * cooperative launches, so the solves of several requests overlap on the GPU.
+ * does not hold back smaller ones behind it).  An admitted request takes its
+ * problem (the caller's, or one it forms from host data) and queues its solve
+ * on its slot's stream with cooperative launches, so the solves of several
+ * requests overlap on the GPU.
  * When a solve finishes, the worker copies its result to host memory and
  * releases its device memory, SMs and slot at once.  A result is the same
  * whether the request ran alone or among others (same work split, fixed
@@ -239,13 +255,26 @@ typedef struct cs_server cs_server;
 /* Errors: CS_EINVAL (max_slots outside [1, 256], zero budget), CS_ECUDA. */
 cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server** out);
 
-/* Queue one reconstruction: A (M x N row-major) and y (M) are HOST pointers,
- * copied before the call returns; params and trials as for cs_solve (the
- * server sets cluster_size = 1 and, if 0, max_ctas as above).  *ticket names the
- * request.  Errors: CS_EINVAL, CS_ENOMEM if the request can never fit the
- * budget. */
-cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,
-                           const cs_params* prm, int32_t trials, uint64_t* ticket);
+/* Queue one reconstruction of the caller's problem p (made by
+ * cs_problem_create): its G, h^z and g, formed once at creation, serve every
+ * request on it, so a problem solved again (another seed, lambda schedule or
+ * trial count) costs no new Gram.  params and trials as for cs_solve (the server
+ * sets cluster_size = 1 and, if 0, max_ctas as above).  While the request runs
+ * the problem is the server's: its work moves to one of the server's streams
+ * (ordered after what was already queued on the problem's own stream) and
+ * returns to the problem's stream when the request finishes; requests on the
+ * same problem run one after the other.  The caller must not use or destroy p
+ * until the request has finished.  *ticket names the request.
+ * Errors: CS_EINVAL (NULL arguments, trials < 1), CS_ENOMEM if the request can
+ * never fit the budget. */
+cs_status cs_server_submit(cs_server* sv, cs_problem* p, const cs_params* prm, int32_t trials, uint64_t* ticket);
+
+/* Queue one reconstruction from host data: A (M x N row-major) and y (M) are
+ * HOST pointers, copied before the call returns; the server forms the problem
+ * (its Gram) when it admits the request and frees it when the request ends.
+ * Otherwise as cs_server_submit. */
+cs_status cs_server_submit_host(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,
+                                const cs_params* prm, int32_t trials, uint64_t* ticket);
 
 /* Non-blocking: *done = 1 once the request has finished (or failed). */
 cs_status cs_server_poll(cs_server* sv, uint64_t ticket, int32_t* done);

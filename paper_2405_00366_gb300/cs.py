@@ -25,7 +25,7 @@ CS_REFIT_EXACT, CS_REFIT_JACOBI = 0, 1
 CS_PUMP_LINEAR, CS_PUMP_SIGMOID = 0, 1
 CS_INIT_UNIFORM, CS_INIT_NORMAL = 0, 1
 CS_P_FP64, CS_P_FP32, CS_P_BF16, CS_P_FP16, CS_P_FP8 = 0, 1, 2, 3, 4
-CS_STATS_LEN = 11
+CS_STATS_LEN = 13
 
 PRECISIONS = {"fp64": CS_P_FP64, "fp32": CS_P_FP32, "bf16": CS_P_BF16, "fp16": CS_P_FP16, "fp8": CS_P_FP8}
 FIELDS = {"cn": CS_FIELD_CN, "bn": CS_FIELD_BN}
@@ -74,7 +74,8 @@ def lib():
         L.cs_problem_create.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_int, P,
                                         ctypes.POINTER(P)]
         L.cs_solve.argtypes = [P, ctypes.POINTER(cs_params), ctypes.c_int32]
-        L.cs_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(cs_params), ctypes.c_int32]
+        L.cs_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ctypes.POINTER(cs_params)),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
         L.cs_result.argtypes = [P, P, P, P, P]
         L.cs_result_trials.argtypes = [P, P, P, P, P]
         L.cs_trajectory.argtypes = [P, P, P]
@@ -83,8 +84,10 @@ def lib():
         L.cs_objective_static.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_double, P, P]
         L.cs_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(P)]
-        L.cs_server_submit.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
-                                       ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+        L.cs_server_submit.argtypes = [P, P, ctypes.POINTER(cs_params), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.cs_server_submit_host.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
         L.cs_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
         L.cs_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64]
         L.cs_server_result.argtypes = [P, ctypes.c_uint64, P, P, P, P, P]
@@ -97,7 +100,8 @@ def lib():
         L.cs_last_error.restype = ctypes.c_char_p
         for name in ["cs_problem_create", "cs_solve", "cs_solve_batch", "cs_result", "cs_result_trials", "cs_trajectory",
                      "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static",
-                     "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_wait", "cs_server_result"]:
+                     "cs_server_create", "cs_server_submit", "cs_server_submit_host", "cs_server_poll",
+                     "cs_server_wait", "cs_server_result"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -165,10 +169,19 @@ def cs_solve(problem, params: cs_params, trials: int) -> None:
     _check(lib().cs_solve(problem, ctypes.byref(params), int(trials)))
 
 
-def cs_solve_batch(problems, params: cs_params, trials: int) -> None:
-    """Queue one batched solve of several problems (same stream) with shared parameters."""
-    arr = (ctypes.c_void_p * len(problems))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in problems])
-    _check(lib().cs_solve_batch(arr, len(problems), ctypes.byref(params), int(trials)))
+def cs_solve_batch(problems, params, trials) -> None:
+    """Queue one batched solve of several problems (same stream).  `params` is one
+    cs_params for every problem or a sequence with one per problem; `trials` is one
+    int or a sequence with one per problem."""
+    n = len(problems)
+    arr = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in problems])
+    plist = list(params) if isinstance(params, (list, tuple)) else [params] * n
+    tlist = list(trials) if isinstance(trials, (list, tuple, np.ndarray)) else [trials] * n
+    if len(plist) != n or len(tlist) != n:
+        raise ValueError("one params and one trial count per problem")
+    pp = (ctypes.POINTER(cs_params) * n)(*[ctypes.pointer(q) for q in plist])
+    tt = (ctypes.c_int32 * n)(*[int(t) for t in tlist])
+    _check(lib().cs_solve_batch(arr, pp, tt, n))
 
 
 def cs_result(problem):
@@ -244,13 +257,21 @@ def cs_server_create(hbm_budget_bytes: int, max_slots: int):
     return h
 
 
-def cs_server_submit(server, A, y, lam: float, params: cs_params, trials: int) -> int:
-    """Queue one request (host arrays); returns its ticket."""
+def cs_server_submit(server, problem, params: cs_params, trials: int) -> int:
+    """Queue one request on a problem made by cs_problem_create (its Gram is reused);
+    returns its ticket."""
+    t = ctypes.c_uint64()
+    _check(lib().cs_server_submit(server, problem, ctypes.byref(params), int(trials), ctypes.byref(t)))
+    return t.value
+
+
+def cs_server_submit_host(server, A, y, lam: float, params: cs_params, trials: int) -> int:
+    """Queue one request from host arrays (the server forms the problem); returns its ticket."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     t = ctypes.c_uint64()
-    _check(lib().cs_server_submit(server, A.ctypes.data, y.ctypes.data, A.shape[0], A.shape[1], float(lam),
-                                  ctypes.byref(params), int(trials), ctypes.byref(t)))
+    _check(lib().cs_server_submit_host(server, A.ctypes.data, y.ctypes.data, A.shape[0], A.shape[1], float(lam),
+                                       ctypes.byref(params), int(trials), ctypes.byref(t)))
     return t.value
 
 

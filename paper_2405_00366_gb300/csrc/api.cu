@@ -66,7 +66,9 @@ cs_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-cudaStream_t g_alloc_stream = nullptr;  // stream of the allocation in progress
+// stream of the allocation in progress on this thread (calls on different
+// problems may run on different threads at once)
+thread_local cudaStream_t g_alloc_stream = nullptr;
 
 template <typename T>
 cudaError_t alloc(T** p, size_t elems) {
@@ -75,7 +77,7 @@ cudaError_t alloc(T** p, size_t elems) {
 
 void free_solve(SolveDev& S, cudaStream_t st) {
   void* ptrs[] = {S.R, S.X0, S.X1, S.state, S.lead, S.job, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
-                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular};
+                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular, S.err4};
   for (void* q : ptrs) dev_free(q, st);
   S = SolveDev();
 }
@@ -126,6 +128,7 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     CS_CUDA(alloc(&S.bar, kMaxEulerCtas + 1), "cudaMalloc publication flags");
     CS_CUDA(alloc(&S.err, 1), "cudaMalloc err");
     CS_CUDA(alloc(&S.singular, 1), "cudaMalloc singular");
+    CS_CUDA(alloc(&S.err4, 4), "cudaMalloc error scratch");
     S.cap_trials = trials;
     S.cap_outer = prm.n_outer;
     S.cap_record = rec;
@@ -200,6 +203,11 @@ cudaError_t mark(cs_problem* p, int cat, bool begin) {
 
 }  // namespace
 
+cudaStream_t problem_stream(const cs_problem* p) { return p->P.stream; }
+void set_problem_stream(cs_problem* p, cudaStream_t s) { p->P.stream = s; }
+int64_t problem_N(const cs_problem* p) { return p->P.N; }
+int64_t problem_M(const cs_problem* p) { return p->P.M; }
+
 RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) {
   RefitJob J;
   J.G = P.G;
@@ -225,6 +233,8 @@ RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) 
   J.refit = prm.refit;
   J.jacobi_iters = prm.jacobi_iters;
   J.jacobi_dt = prm.jacobi_dt;
+  J.precision = prm.precision;
+  J.gscale = prm.precision == CS_P_FP8 ? P.gscale : nullptr;
   return J;
 }
 
@@ -384,84 +394,137 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     P.launches += 2;
   }
   CS_CUDA(mark(p, TM_OTHER, true), "event");
-  CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream), "finish launch");
+  CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream, S.err4), "finish launch");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
-  P.launches += 2;
+  P.launches += 4;  // energy, selection, error against FP64 and its ratio
   S.done = true;
   return CS_OK;
 }
 
-cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm, int32_t trials) {
-  if (!ps || n < 1) return fail(CS_EINVAL, "need at least one problem");
-  cs_status st = check_params(prm, trials);
-  if (st != CS_OK) return st;
-  if (trials > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials");
-  if (prm->record_steps != 0) return fail(CS_EINVAL, "a batched solve does not record trajectories");
+cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, const int32_t* trials, int32_t n) {
+  if (!ps || !prms || !trials || n < 1) return fail(CS_EINVAL, "need at least one problem, with its params and trials");
   for (int i = 0; i < n; ++i) {
     if (!ps[i]) return fail(CS_EINVAL, "problem is NULL");
+    cs_status st = check_params(prms[i], trials[i]);
+    if (st != CS_OK) return st;
+    if (trials[i] > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials per problem");
+    if (prms[i]->record_steps != 0) return fail(CS_EINVAL, "a batched solve does not record trajectories");
+    if (prms[i]->tensor_form == 4) return fail(CS_EINVAL, "tensor_form = 4: the batched kernel has no tcgen05 form");
     if (ps[i]->P.stream != ps[0]->P.stream || ps[i]->P.device != ps[0]->P.device)
       return fail(CS_EINVAL, "the problems of a batch must share one stream and device");
+    for (int k = 0; k < i; ++k)
+      if (ps[k] == ps[i]) return fail(CS_EINVAL, "a problem appears twice in one batch");
   }
   ProblemDev& P0 = ps[0]->P;
   cudaStream_t stream = P0.stream;
   g_alloc_stream = stream;
-  const bool btc = batch_tensor_form(prm->precision, trials, prm->tensor_form);
-  if (prm->tensor_form >= 2 && !btc)
-    return fail(CS_EINVAL, "tensor_form >= 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
-                           "trials");
+  // Groups of problems that one batched launch can take: the same storage
+  // precision, trial count and tensor-core decision.  Within a group the jobs
+  // are ordered by n_outer (descending), so the problems still running at outer
+  // iteration `it` are a prefix of the group.
+  struct Group {
+    int precision, T;
+    bool btc;
+    std::vector<int> idx;
+  };
+  std::vector<Group> groups;
+  std::vector<char> btcs(n);
+  for (int i = 0; i < n; ++i) {
+    const cs_params& p = *prms[i];
+    const bool btc = batch_tensor_form(p.precision, trials[i], p.tensor_form);
+    if (p.tensor_form >= 2 && !btc)
+      return fail(CS_EINVAL, "tensor_form >= 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
+                             "trials");
+    btcs[i] = btc;
+    size_t g = 0;
+    while (g < groups.size() &&
+           !(groups[g].precision == p.precision && groups[g].T == trials[i] && groups[g].btc == btc))
+      ++g;
+    if (g == groups.size()) groups.push_back(Group{p.precision, trials[i], btc, {}});
+    groups[g].idx.push_back(i);
+  }
+  int n_outer_max = 0;
   int64_t nmax = 0;
+  int refit_items_max = 0;
+  cs_status st = CS_OK;
+  for (Group& G : groups) {
+    std::stable_sort(G.idx.begin(), G.idx.end(), [&](int a, int b) { return prms[a]->n_outer > prms[b]->n_outer; });
+    refit_items_max = std::max(refit_items_max, (int)G.idx.size() * G.T);
+  }
   for (int i = 0; i < n; ++i) {
     ProblemDev& P = ps[i]->P;
     SolveDev& S = ps[i]->S;
     S.done = false;
     nmax = std::max(nmax, P.N);
-    CS_CUDA(launch_store_tiled(P, prm->precision, btc), "store tiled coupling");
-    if ((st = ensure_solve(P, S, *prm, trials, false)) != CS_OK) return st;
+    n_outer_max = std::max(n_outer_max, prms[i]->n_outer);
+    CS_CUDA(launch_store_tiled(P, prms[i]->precision, btcs[i]), "store tiled coupling");
+    if ((st = ensure_solve(P, S, *prms[i], trials[i], false)) != CS_OK) return st;
     CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), stream), "memset singular");
   }
-  // batch-owned buffers, released (stream-ordered) after the last kernel
+  // batch-owned buffers, released (stream-ordered) after the graph
   const size_t ib = batch_inst_bytes();
+  // descriptors: for every outer iteration and group, the problems still running, largest N first
+  std::vector<unsigned char> hinst;
+  std::vector<std::vector<size_t>> inst_off(n_outer_max, std::vector<size_t>(groups.size(), 0));
+  std::vector<std::vector<int>> inst_cnt(n_outer_max, std::vector<int>(groups.size(), 0));
+  for (int it = 0; it < n_outer_max; ++it)
+    for (size_t g = 0; g < groups.size(); ++g) {
+      std::vector<int> act;
+      for (int i : groups[g].idx)
+        if (prms[i]->n_outer > it) act.push_back(i);
+      std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return ps[a]->P.N > ps[b]->P.N; });
+      inst_off[it][g] = hinst.size();
+      inst_cnt[it][g] = (int)act.size();
+      hinst.resize(hinst.size() + ib * act.size());
+      for (size_t k = 0; k < act.size(); ++k) {
+        const int i = act[k];
+        const double eta = eta_at(it, *prms[i], ps[i]->P.lambda);
+        fill_batch_inst(hinst.data() + inst_off[it][g] + ib * k, ps[i]->P, ps[i]->S, *prms[i],
+                        std::sqrt(prms[i]->tau) * eta * eta / 4.0, i);
+      }
+    }
+  // refit jobs: per group, in the group's order (n_outer descending)
+  std::vector<RefitJob> jobs;
+  std::vector<size_t> job_off(groups.size());
   void* d_insts = nullptr;
   int* d_order = nullptr;
   int* d_queue = nullptr;
   int* d_err = nullptr;
   RefitJob* d_jobs = nullptr;
   double* pool = nullptr;
+  double* d_err4 = nullptr;
+  CS_CUDA(alloc(&d_err, 1), "cudaMalloc batch error word");
+  for (size_t g = 0; g < groups.size(); ++g) {
+    job_off[g] = jobs.size();
+    for (int i : groups[g].idx) {
+      jobs.push_back(make_job(ps[i]->P, ps[i]->S, *prms[i]));
+      jobs.back().err = d_err;
+    }
+  }
   const size_t stride = (size_t)nmax * nmax + 2 * (size_t)nmax;
-  int pool_blocks = std::min(n * trials, P0.num_sms);
+  int pool_blocks = std::min(refit_items_max, P0.num_sms);
   while (pool_blocks > 1 && (double)pool_blocks * stride * 8.0 > 16e9) --pool_blocks;
-  CS_CUDA(dev_alloc(&d_insts, ib * n * (size_t)prm->n_outer, stream), "cudaMalloc batch descriptors");
+  CS_CUDA(dev_alloc(&d_insts, std::max<size_t>(hinst.size(), 1), stream), "cudaMalloc batch descriptors");
   CS_CUDA(alloc(&d_order, n), "cudaMalloc batch order");
   CS_CUDA(alloc(&d_queue, 1), "cudaMalloc batch queue");
-  CS_CUDA(alloc(&d_err, 1), "cudaMalloc batch error word");
   CS_CUDA(alloc(&d_jobs, n), "cudaMalloc batch jobs");
+  CS_CUDA(alloc(&d_err4, 4 * (size_t)n), "cudaMalloc batch error scratch");
   CS_CUDA(alloc(&pool, (size_t)pool_blocks * stride), "cudaMalloc batch refit workspace");
   CS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream), "memset err");
   std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ps[a]->P.N > ps[b]->P.N; });
+  for (int i = 0; i < n; ++i) order[i] = i;  // descriptors are stored in processing order
   CS_CUDA(cudaMemcpyAsync(d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, stream), "copy order");
-  std::vector<RefitJob> jobs(n);
-  for (int i = 0; i < n; ++i) {
-    jobs[i] = make_job(ps[i]->P, ps[i]->S, *prm);
-    jobs[i].err = d_err;
-  }
   CS_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), n * sizeof(RefitJob), cudaMemcpyHostToDevice, stream), "copy jobs");
+  CS_CUDA(cudaMemcpyAsync(d_insts, hinst.data(), hinst.size(), cudaMemcpyHostToDevice, stream), "copy descriptors");
   int khz = 0;
   CS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, P0.device), "clock rate");
-  const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
-  CS_CUDA(launch_init_R(d_jobs, n, trials, P0.num_sms, stream), "init R");
-  // the descriptors of every outer iteration (eta changes), staged in one copy
-  std::vector<unsigned char> hinst(ib * n * (size_t)prm->n_outer);
-  for (int it = 0; it < prm->n_outer; ++it)
-    for (int i = 0; i < n; ++i) {
-      const double eta = eta_at(it, *prm, ps[i]->P.lambda);
-      fill_batch_inst(hinst.data() + ib * ((size_t)it * n + i), ps[i]->P, ps[i]->S, prm->precision,
-                      std::sqrt(prm->tau) * eta * eta / 4.0, i);
-    }
-  CS_CUDA(cudaMemcpyAsync(d_insts, hinst.data(), hinst.size(), cudaMemcpyHostToDevice, stream), "copy descriptors");
-  // Every outer iteration (batched Euler launch + refit) and the objective are
-  // captured into one CUDA graph and submitted as a single launch.
+  long long timeout_ms = 0;
+  for (int i = 0; i < n; ++i) timeout_ms = std::max<long long>(timeout_ms, prms[i]->timeout_ms);
+  const long long timeout_cycles = timeout_ms * (long long)(khz > 0 ? khz : 2000000);
+  for (size_t g = 0; g < groups.size(); ++g)
+    CS_CUDA(launch_init_R(d_jobs + job_off[g], (int)groups[g].idx.size(), groups[g].T, P0.num_sms, stream), "init R");
+  // Every outer iteration of every group (batched Euler launch + refit) and the
+  // objective are captured into one CUDA graph and submitted as a single launch.
   // (captured on a private stream: the problems' stream may be the legacy
   // default stream, which cannot be captured; the graph then runs on theirs)
   reap_batch_graphs();
@@ -477,27 +540,33 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   }
   cudaError_t e = cudaSuccess;
   const char* where = "";
-  for (int it = 0; it < prm->n_outer && e == cudaSuccess; ++it) {
-    BatchLaunch L;
-    L.insts = static_cast<unsigned char*>(d_insts) + ib * (size_t)n * it;
-    L.order = d_order;
-    L.n = n;
-    L.T = trials;
-    L.prm = prm;
-    L.queue = d_queue;
-    L.outer = it;
-    L.err = d_err;
-    L.timeout_cycles = timeout_cycles;
-    L.ctas = prm->max_ctas > 0 ? std::min(prm->max_ctas, P0.num_sms) : P0.num_sms;
-    e = launch_euler_batch(L, cap);
-    where = "batched euler launch";
-    if (e == cudaSuccess) {
-      e = launch_refit(d_jobs, n, trials, pool, stride, pool_blocks, it, cap);
-      where = "batched refit launch";
+  for (int it = 0; it < n_outer_max && e == cudaSuccess; ++it) {
+    for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+      const int na = inst_cnt[it][g];
+      if (na == 0) continue;
+      const cs_params& gp = *prms[groups[g].idx[0]];
+      BatchLaunch L;
+      L.insts = static_cast<unsigned char*>(d_insts) + inst_off[it][g];
+      L.order = d_order;
+      L.n = na;
+      L.T = groups[g].T;
+      L.prm = &gp;
+      L.queue = d_queue;
+      L.outer = it;
+      L.err = d_err;
+      L.timeout_cycles = timeout_cycles;
+      L.ctas = gp.max_ctas > 0 ? std::min(gp.max_ctas, P0.num_sms) : P0.num_sms;
+      e = launch_euler_batch(L, cap);
+      where = "batched euler launch";
+      if (e == cudaSuccess) {
+        e = launch_refit(d_jobs + job_off[g], na, groups[g].T, pool, stride, pool_blocks, it, cap);
+        where = "batched refit launch";
+      }
     }
   }
-  if (e == cudaSuccess) {
-    e = launch_finish(d_jobs, n, trials, P0.num_sms, cap);
+  for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+    e = launch_finish(d_jobs + job_off[g], (int)groups[g].idx.size(), groups[g].T, P0.num_sms, cap,
+                      d_err4 + 4 * job_off[g]);
     where = "batched finish launch";
   }
   const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
@@ -523,12 +592,14 @@ cs_status cs_solve_batch(cs_problem* const* ps, int32_t n, const cs_params* prm,
   dev_free(d_err, stream);
   dev_free(d_jobs, stream);
   dev_free(pool, stream);
-  for (int i = 0; i < n; ++i) {
-    ps[i]->S.done = true;
-    ps[i]->S.plan_cluster = 0;
-    ps[i]->S.plan_ctas = std::min(n, P0.num_sms);
-    ps[i]->S.plan_form = btc ? 4 : 3;
-  }
+  dev_free(d_err4, stream);
+  for (size_t g = 0; g < groups.size(); ++g)
+    for (int i : groups[g].idx) {
+      ps[i]->S.done = true;
+      ps[i]->S.plan_cluster = 0;
+      ps[i]->S.plan_ctas = std::min((int)groups[g].idx.size(), P0.num_sms);
+      ps[i]->S.plan_form = groups[g].btc ? 4 : 3;
+    }
   return CS_OK;
 }
 
@@ -537,7 +608,7 @@ static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   if (!p->S.done) return fail(CS_ENOTREADY, "no solve queued on this problem");
   CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
   double st[CS_STATS_LEN];
-  CS_CUDA(cudaMemcpy(st, p->S.stats, 8 * sizeof(double), cudaMemcpyDeviceToHost), "copy stats");
+  CS_CUDA(cudaMemcpy(st, p->S.stats, CS_STATS_LEN * sizeof(double), cudaMemcpyDeviceToHost), "copy stats");
   st[8] = p->S.plan_cluster;
   st[9] = p->S.plan_ctas;
   st[10] = p->S.plan_form;

@@ -82,6 +82,10 @@ struct BInst {
   uint8_t* sigma;          // N x T
   double theta;            // sqrt(tau) eta^2 / 4 of this problem
   int inst;                // instance number of the initial-amplitude key
+  // this problem's run parameters (cs_params)
+  int n_steps, pump_kind, field, init_kind;
+  double dt, p0, p1, p_thr, d, t0, width, beta, tau, Kj, init_scale;
+  uint64_t seed;
 };
 
 template <typename CT>
@@ -92,14 +96,6 @@ struct BArgs {
   int T, twp, slots;
   int tps;          // column tiles per ring slot (1, 2 or 4)
   int* queue;
-  int n_steps;
-  double dt;
-  int pump_kind;
-  double p0, p1, p_thr, d, t0, width;
-  double beta, tau, Kj;
-  int field, init_kind;
-  double init_scale;
-  uint64_t seed;
   int outer;
   int* err;
   long long timeout_cycles;
@@ -491,11 +487,11 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   CT* c = I.state;
   CT* e = I.state + NT;
   CT* b = I.state + 2 * NT;
-  const double st = sqrt(a.tau);
-  const CT wcoef = (a.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
+  const double st = sqrt(I.tau);
+  const CT wcoef = (I.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
   bool ok = true;
   // ---- prologue
-  if (a.field == CS_FIELD_CN) {
+  if (I.field == CS_FIELD_CN) {
     for (size_t idx = threadIdx.x; idx < NT; idx += kBThreads) {
       const int r = (int)(idx / T), t = (int)(idx % T);
       bxput<GT, CT, PAIR, TC>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
@@ -522,22 +518,22 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   }
   for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
     const int r = (int)(o / T), t = (int)(o % T);
-    const uint64_t key = run_key(a.seed, (uint64_t)I.inst, (uint64_t)t, (uint64_t)a.outer);
-    const CT c0 = CT(initial_amplitude(key, (uint64_t)r, a.init_kind, a.init_scale));
+    const uint64_t key = run_key(I.seed, (uint64_t)I.inst, (uint64_t)t, (uint64_t)a.outer);
+    const CT c0 = CT(initial_amplitude(key, (uint64_t)r, I.init_kind, I.init_scale));
     c[o] = c0;
     e[o] = CT(1);
     const CT Rr = CT(I.R[o]);
-    bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp, ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
+    bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp, ((I.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
   }
   fence_proxy_async_global();
   __syncthreads();
   // ---- Euler steps
-  const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
+  const CT dt = CT(I.dt), beta = CT(I.beta), tau = CT(I.tau), Kj = CT(I.Kj);
   CT* Xc = I.X1;
   CT* Xn = I.X0;
-  for (int n = 0; n < a.n_steps && ok; ++n) {
-    const CT p = pump_at<CT>(n, a.n_steps, a.pump_kind, a.p0, a.p1, a.p_thr, a.d, a.dt, a.t0, a.width);
-    const bool last = (n + 1 == a.n_steps);
+  for (int n = 0; n < I.n_steps && ok; ++n) {
+    const CT p = pump_at<CT>(n, I.n_steps, I.pump_kind, I.p0, I.p1, I.p_thr, I.d, I.dt, I.t0, I.width);
+    const bool last = (n + 1 == I.n_steps);
     for (int rt = 0; rt < I.nrt && ok; ++rt) {
       constexpr int kU = 8;
       const int ne = kRT * T;
@@ -585,7 +581,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
               c[o] = cn;
               e[o] = en;
               bxput<GT, CT, PAIR, TC>(Xn, r, t, twp,
-                                      ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
+                                      ((I.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
               if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
             }
           }
@@ -629,7 +625,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
             c[o] = cn;
             e[o] = en;
             bxput<GT, CT, PAIR, TC>(Xn, r, t, twp,
-                                    ((a.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
+                                    ((I.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
             if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
           }
         }
@@ -717,14 +713,6 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.slots = slots;
   a.tps = tps;
   a.queue = L.queue;
-  a.n_steps = L.prm->n_steps;
-  a.dt = L.prm->dt;
-  a.pump_kind = L.prm->pump_kind;
-  a.p0 = L.prm->p0; a.p1 = L.prm->p1; a.p_thr = L.prm->p_thr; a.d = L.prm->d; a.t0 = L.prm->t0;
-  a.width = L.prm->width;
-  a.beta = L.prm->beta; a.tau = L.prm->tau; a.Kj = L.prm->K * L.prm->j;
-  a.field = L.prm->field; a.init_kind = L.prm->init_kind; a.init_scale = L.prm->init_scale;
-  a.seed = L.prm->seed;
   a.outer = L.outer;
   a.err = L.err;
   a.timeout_cycles = L.timeout_cycles;
@@ -809,21 +797,30 @@ cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag) {
 }
 
 // Host description of one problem for the batched kernel, written into `dst`
-// (a BInst of the precision's compute type).
-void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst) {
-  if (precision == CS_P_FP64) {
+// (a BInst of the precision's compute type): its buffers, its threshold term
+// theta of this outer iteration, its instance number and its run parameters.
+template <typename CT>
+static void fill_inst(BInst<CT>& I, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
+                      int inst) {
+  I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
+  I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
+  I.X0 = (CT*)S.X0; I.X1 = (CT*)S.X1; I.state = (CT*)S.state; I.sigma = S.sigma;
+  I.theta = theta; I.inst = inst;
+  I.n_steps = prm.n_steps; I.pump_kind = prm.pump_kind; I.field = prm.field; I.init_kind = prm.init_kind;
+  I.dt = prm.dt; I.p0 = prm.p0; I.p1 = prm.p1; I.p_thr = prm.p_thr; I.d = prm.d; I.t0 = prm.t0;
+  I.width = prm.width; I.beta = prm.beta; I.tau = prm.tau; I.Kj = prm.K * prm.j; I.init_scale = prm.init_scale;
+  I.seed = prm.seed;
+}
+
+void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
+                     int inst) {
+  if (prm.precision == CS_P_FP64) {
     BInst<double> I;
-    I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
-    I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
-    I.X0 = (double*)S.X0; I.X1 = (double*)S.X1; I.state = (double*)S.state; I.sigma = S.sigma;
-    I.theta = theta; I.inst = inst;
+    fill_inst(I, P, S, prm, theta, inst);
     *reinterpret_cast<BInst<double>*>(dst) = I;
   } else {
     BInst<float> I;
-    I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
-    I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
-    I.X0 = (float*)S.X0; I.X1 = (float*)S.X1; I.state = (float*)S.state; I.sigma = S.sigma;
-    I.theta = theta; I.inst = inst;
+    fill_inst(I, P, S, prm, theta, inst);
     *reinterpret_cast<BInst<float>*>(dst) = I;
   }
 }

@@ -74,6 +74,8 @@ struct RefitJob {
   int refit;             // CS_REFIT_EXACT or CS_REFIT_JACOBI
   int jacobi_iters;      // damped Jacobi sweeps per outer iteration
   double jacobi_dt;      // damped Jacobi step
+  int precision;         // CS_P_*: storage precision of G_off in the Euler kernels
+  const float* gscale;   // FP8 row scales of G_off (NULL unless FP8)
 };
 
 // Per-solve device state, sized by (N, trials).
@@ -100,6 +102,7 @@ struct SolveDev {
   unsigned* bar = nullptr;      // Euler kernel: per-CTA X publication flags (kMaxEulerCtas + 1 words)
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
+  double* err4 = nullptr;       // 4 doubles: scratch of the error against FP64 (launch_finish)
   RefitJob* job = nullptr;      // this problem's refit job (device copy)
   bool done = false;
   int plan_cluster = 0, plan_ctas = 0, plan_form = 0;  // work split of the last Euler launch
@@ -107,12 +110,19 @@ struct SolveDev {
 
 RefitJob make_job(const ProblemDev& P, const SolveDev& S);
 
+// The stream a problem queues its work on, and its sizes (for the server, which
+// runs a caller's problem on one of its own streams for the length of a request).
+cudaStream_t problem_stream(const cs_problem* p);
+void set_problem_stream(cs_problem* p, cudaStream_t s);
+int64_t problem_N(const cs_problem* p);
+int64_t problem_M(const cs_problem* p);
+
 // One outer iteration of a batch of problems in one launch (batch.cu).
 struct BatchLaunch {
   const void* insts;   // device array of per-problem descriptors (fill_batch_inst)
   const int* order;    // device array: processing order, largest first
-  int n, T;
-  const cs_params* prm;
+  int n, T;            // problems of this launch and their (common) trial count
+  const cs_params* prm;  // precision and tensor_form of the launch (common to its problems)
   int* queue;          // device work counter
   int outer;
   int* err;
@@ -120,7 +130,8 @@ struct BatchLaunch {
   int ctas;            // CTAs to launch (one per SM)
 };
 size_t batch_inst_bytes();
-void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, int precision, double theta, int inst);
+void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
+                     int inst);
 cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag);
 // Whether a batch of this precision and trial count runs the batched kernel's
 // tensor-core form (BF16 / FP16 storage, 8 or 16 trials, tensor_form != 1).
@@ -138,6 +149,8 @@ const char* euler_last_call();  // the CUDA call the last failing Euler launch s
 cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
                          int outer, cudaStream_t st);
-cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
+// Objective per trial, kept trial, and the kept result's error against FP64
+// (stats[11], stats[12]); err4 is 4 doubles of scratch per job.
+cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st, double* err4);
 
 }  // namespace cs

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "kernels_common.cuh"
 #include "refit_core.cuh"
 
 namespace cs {
@@ -522,6 +523,77 @@ __global__ void select_kernel(const RefitJob* __restrict__ jobs, int T) {
   }
 }
 
+// G_rk rounded to the storage precision the Euler kernels used for G_off (with
+// the row's scale for FP8), widened back to FP64.
+__device__ __forceinline__ double stored_value(double v, int precision, const float* gscale, int r) {
+  switch (precision) {
+    case CS_P_FP32: return (double)to_storage<float>(v);
+    case CS_P_BF16: return (double)__bfloat162float(to_storage<__nv_bfloat16>(v));
+    case CS_P_FP16: return (double)__half2float(to_storage<__half>(v));
+    case CS_P_FP8: {
+      const double sc = (double)gscale[r];
+      return sc > 0.0 ? (double)float(to_storage<__nv_fp8_e4m3>(v / sc)) * sc : 0.0;
+    }
+    default: return v;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
+// Error of the kept result against FP64, per problem (after select_kernel):
+//  err[0] = max_r |U^s_r - U_r|, err[1] = max_r |U_r|  with U = G_off x_hat in
+//           FP64 and U^s the same product with G_off rounded to its storage
+//           precision (the coupling the Euler kernels used); U^s - U is summed
+//           directly as sum_k (G^s_rk - G_rk) x_k (exactly zero for FP64);
+//  err[2] = max over the support of |h^z_r - (G x_hat)_r|, err[3] = max over the
+//           support of |h^z_r|: the FP64 residual of the refit's normal equations.
+// One warp per row, FP64 throughout; maxima are order independent.
+__global__ void error_kernel(const RefitJob* __restrict__ jobs, double* __restrict__ err4) {
+  const RefitJob& J = jobs[blockIdx.y];
+  double* e = err4 + 4 * (size_t)blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < J.N; r += gridDim.x * wpb) {
+    const double* Gr = J.G + (size_t)r * J.N;
+    double u = 0.0, du = 0.0, gx = 0.0;
+    for (int k = lane; k < J.N; k += 32) {
+      const double xk = J.x_hat[k];
+      if (xk == 0.0) continue;
+      const double v = Gr[k];
+      gx += v * xk;
+      if (k != r) {
+        u += v * xk;
+        du += (stored_value(v, J.precision, J.gscale, r) - v) * xk;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      u += __shfl_xor_sync(0xffffffffu, u, o);
+      du += __shfl_xor_sync(0xffffffffu, du, o);
+      gx += __shfl_xor_sync(0xffffffffu, gx, o);
+    }
+    if (lane == 0) {
+      atomic_max_nonneg(e + 0, fabs(du));
+      atomic_max_nonneg(e + 1, fabs(u));
+      if (J.sigma_hat[r]) {
+        atomic_max_nonneg(e + 2, fabs(J.hz[r] - gx));
+        atomic_max_nonneg(e + 3, fabs(J.hz[r]));
+      }
+    }
+  }
+}
+
+// stats[11] = err[0] / err[1] (0 when U = 0), stats[12] = err[2] / err[3].
+__global__ void error_stats_kernel(const RefitJob* __restrict__ jobs, const double* __restrict__ err4, int njobs) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += gridDim.x * blockDim.x) {
+    const double* e = err4 + 4 * (size_t)j;
+    jobs[j].stats[11] = e[1] > 0.0 ? e[0] / e[1] : 0.0;
+    jobs[j].stats[12] = e[3] > 0.0 ? e[2] / e[3] : 0.0;
+  }
+}
+
 // Initial R of every trial: the Jacobi fixed point of the empty support, h^z / g.
 __global__ void init_R_kernel(const RefitJob* __restrict__ jobs, int T, int njobs) {
   for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
@@ -568,12 +640,21 @@ cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, s
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st) {
+cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st, double* err4) {
   const int items = njobs * T;
   energy_kernel<<<std::min(items, 8 * num_sms), kRefitThreads, 0, st>>>(jobs, T, items);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   select_kernel<<<njobs, 256, 0, st>>>(jobs, T);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(err4, 0, sizeof(double) * 4 * (size_t)njobs, st);
+  if (e != cudaSuccess) return e;
+  const int gx = std::max(1, std::min(4 * num_sms / std::max(1, std::min(njobs, 65535)), 4 * num_sms));
+  error_kernel<<<dim3(gx, njobs), 256, 0, st>>>(jobs, err4);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  error_stats_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, err4, njobs);
   return cudaGetLastError();
 }
 

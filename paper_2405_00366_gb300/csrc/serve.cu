@@ -46,6 +46,8 @@ struct Request {
   int state = RQ_QUEUED;
   int slot = -1;
   cs_problem* p = nullptr;
+  cs_problem* user = nullptr;       // the caller's problem (submitted by problem), else NULL
+  cudaStream_t user_stream = nullptr;  // its own stream, restored when the request ends
   cudaEvent_t ev = nullptr;
   std::vector<double> x_hat;
   std::vector<uint8_t> sigma_hat;
@@ -57,13 +59,14 @@ struct Request {
 };
 
 // Device bytes a request holds while it runs (problem, coupling copy, solve state,
-// refit workspace), rounded up generously.
-size_t request_bytes(int64_t M, int64_t N, int trials, int precision) {
+// refit workspace), rounded up generously; without A and G when the problem is
+// the caller's (already on the device).
+size_t request_bytes(int64_t M, int64_t N, int trials, int precision, bool own_problem = true) {
   const size_t n = (size_t)N, m = (size_t)M, T = (size_t)trials;
   const size_t np = (n + cs::kPadN - 1) / cs::kPadN * cs::kPadN;
   const size_t gb = cs::storage_bytes(precision);
   const size_t cb = precision == CS_P_FP64 ? 8 : 4;
-  size_t b = m * n * 8 + n * n * 8 + np * np * gb;          // A, G, G_off
+  size_t b = (own_problem ? m * n * 8 + n * n * 8 : 0) + np * np * gb;  // A, G, G_off
   b += n * T * (8 + 3 * cb + 1 + 4) + 2 * np * ((T + 3) / 4 * 4) * cb;  // R, state, sigma, sidx, X
   b += std::min<size_t>(T, 152) * (n * n + 2 * n) * 8;      // refit workspace
   return b + (1u << 20);
@@ -92,6 +95,7 @@ struct cs_server {
   std::deque<Request*> queue;
   std::vector<Request*> running;
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::map<cs_problem*, int> busy;  // caller's problems with a request running (one at a time each)
   uint64_t next_ticket = 1;
   std::mutex mu;
   std::condition_variable cv;
@@ -101,8 +105,7 @@ struct cs_server {
   void finish(Request* r) {
     r->status = cs_result(r->p, r->x_hat.data(), r->sigma_hat.data(), &r->energy, r->stats);
     if (r->status != CS_OK && r->status != CS_ESINGULAR) r->error = cs_last_error();
-    cs_problem_destroy(r->p);
-    r->p = nullptr;
+    release_problem(r);
     cudaEventDestroy(r->ev);
     r->ev = nullptr;
     r->state = (r->status == CS_OK || r->status == CS_ESINGULAR) ? RQ_DONE : RQ_FAILED;
@@ -116,7 +119,22 @@ struct cs_server {
     r->y.shrink_to_fit();
   }
 
-  // Admit r on slot s: form its problem and queue its solve (caller holds mu).
+  // The request's problem is done with: a problem the server formed is freed; a
+  // caller's problem goes back to its own stream (its solve has completed, so
+  // nothing is left on the server's stream) and is free for its next request.
+  void release_problem(Request* r) {
+    if (r->user) {
+      cs::set_problem_stream(r->user, r->user_stream);
+      busy.erase(r->user);
+    } else if (r->p) {
+      cs_problem_destroy(r->p);
+    }
+    r->p = nullptr;
+  }
+
+  // Admit r on slot s: form its problem (or take the caller's, moved onto the
+  // slot's stream behind the work already queued on its own) and queue its solve
+  // (caller holds mu).
   void start(Request* r, int s) {
     r->slot = s;
     slot_busy[s] = 1;
@@ -125,15 +143,31 @@ struct cs_server {
     r->t_start = now_s();
     r->x_hat.resize((size_t)r->N);
     r->sigma_hat.resize((size_t)r->N);
-    cs_status st = cs_problem_create(r->A.data(), r->y.data(), r->M, r->N, r->lambda, 0, streams[s], &r->p);
+    cs_status st = CS_OK;
+    if (r->user) {
+      busy[r->user] = 1;
+      r->p = r->user;
+      r->user_stream = cs::problem_stream(r->user);
+      cudaEvent_t before = nullptr;
+      if (cudaEventCreateWithFlags(&before, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(before, r->user_stream) != cudaSuccess ||
+          cudaStreamWaitEvent(streams[s], before, 0) != cudaSuccess) {
+        cs::set_last_error("cannot order the request behind the problem's stream");
+        st = CS_ECUDA;
+      }
+      if (before) cudaEventDestroy(before);
+      if (st == CS_OK) cs::set_problem_stream(r->user, streams[s]);
+    } else {
+      st = cs_problem_create(r->A.data(), r->y.data(), r->M, r->N, r->lambda, 0, streams[s], &r->p);
+    }
     if (st == CS_OK) st = cs_solve(r->p, &r->prm, r->trials);
     if (st == CS_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) st = CS_ECUDA;
     if (st == CS_OK && cudaEventRecord(r->ev, streams[s]) != cudaSuccess) st = CS_ECUDA;
     if (st != CS_OK) {
       r->status = st;
       r->error = cs_last_error();
-      if (r->p) cs_problem_destroy(r->p);
-      r->p = nullptr;
+      if (r->user) cudaStreamSynchronize(streams[s]);
+      release_problem(r);
       if (r->ev) cudaEventDestroy(r->ev);
       r->ev = nullptr;
       r->state = RQ_FAILED;
@@ -168,7 +202,7 @@ struct cs_server {
         for (int i = 0; i < max_slots; ++i)
           if (!slot_busy[i]) { s = i; break; }
         if (s < 0) break;
-        if (in_use + r->bytes > budget || sms_in_use + r->prm.max_ctas > num_sms) {
+        if (in_use + r->bytes > budget || sms_in_use + r->prm.max_ctas > num_sms || (r->user && busy.count(r->user))) {
           ++it;
           continue;
         }
@@ -224,8 +258,52 @@ cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server
   return CS_OK;
 }
 
-cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,
-                           const cs_params* prm, int32_t trials, uint64_t* ticket) {
+// The server's share of the GPU for a request: a grid sized to the work, cluster
+// size 1 and cooperative launches (which keep every CTA of a grid resident while
+// grids share SMs).
+static void server_params(const cs_server* sv, const cs_params* prm, int64_t N, int trials, cs_params* out) {
+  *out = *prm;
+  if (out->max_ctas <= 0) out->max_ctas = server_grid(sv->num_sms, N, trials, prm->precision);
+  out->max_ctas = std::min(out->max_ctas, sv->num_sms);
+  out->cluster_size = 1;
+}
+
+static cs_status enqueue(cs_server* sv, std::unique_ptr<Request> r, uint64_t* ticket) {
+  if (r->bytes > sv->budget) {
+    cs::set_last_error("the request needs more device memory than the server's whole budget");
+    return CS_ENOMEM;
+  }
+  r->t_submit = now_s();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  r->ticket = sv->next_ticket++;
+  *ticket = r->ticket;
+  sv->queue.push_back(r.get());
+  sv->reqs[r->ticket] = std::move(r);
+  sv->cv.notify_all();
+  return CS_OK;
+}
+
+cs_status cs_server_submit(cs_server* sv, cs_problem* p, const cs_params* prm, int32_t trials, uint64_t* ticket) {
+  if (!sv || !p || !prm || !ticket) {
+    cs::set_last_error("NULL argument");
+    return CS_EINVAL;
+  }
+  if (trials < 1) {
+    cs::set_last_error("trials must be >= 1");
+    return CS_EINVAL;
+  }
+  std::unique_ptr<Request> r(new Request());
+  r->user = p;
+  r->M = cs::problem_M(p);
+  r->N = cs::problem_N(p);
+  server_params(sv, prm, r->N, trials, &r->prm);
+  r->trials = trials;
+  r->bytes = request_bytes(r->M, r->N, trials, prm->precision, false);
+  return enqueue(sv, std::move(r), ticket);
+}
+
+cs_status cs_server_submit_host(cs_server* sv, const double* A, const double* y, int64_t M, int64_t N, double lambda,
+                                const cs_params* prm, int32_t trials, uint64_t* ticket) {
   if (!sv || !A || !y || !prm || !ticket) {
     cs::set_last_error("NULL argument");
     return CS_EINVAL;
@@ -238,28 +316,14 @@ cs_status cs_server_submit(cs_server* sv, const double* A, const double* y, int6
   r->M = M;
   r->N = N;
   r->lambda = lambda;
-  r->prm = *prm;
-  // solves of a server share the GPU: a grid sized to the work and cooperative
-  // launches (which keep every CTA of a grid resident while grids share SMs)
-  if (r->prm.max_ctas <= 0) r->prm.max_ctas = server_grid(sv->num_sms, N, trials, prm->precision);
-  r->prm.max_ctas = std::min(r->prm.max_ctas, sv->num_sms);
-  r->prm.cluster_size = 1;
+  server_params(sv, prm, N, trials, &r->prm);
   r->trials = trials;
   r->bytes = request_bytes(M, N, trials, prm->precision);
-  if (r->bytes > sv->budget) {
-    cs::set_last_error("the request needs more device memory than the server's whole budget");
-    return CS_ENOMEM;
+  if (r->bytes <= sv->budget) {
+    r->A.assign(A, A + (size_t)M * N);
+    r->y.assign(y, y + (size_t)M);
   }
-  r->A.assign(A, A + (size_t)M * N);
-  r->y.assign(y, y + (size_t)M);
-  r->t_submit = now_s();
-  std::lock_guard<std::mutex> lk(sv->mu);
-  r->ticket = sv->next_ticket++;
-  *ticket = r->ticket;
-  sv->queue.push_back(r.get());
-  sv->reqs[r->ticket] = std::move(r);
-  sv->cv.notify_all();
-  return CS_OK;
+  return enqueue(sv, std::move(r), ticket);
 }
 
 cs_status cs_server_poll(cs_server* sv, uint64_t ticket, int32_t* done) {

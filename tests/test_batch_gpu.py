@@ -228,3 +228,47 @@ def test_fp8_row_scaled_error_bounds(capsys):
         assert es == pytest.approx(0.5 * resid @ resid + inst.lam * S.size, rel=1e-10)
         if 0 < S.size < inst.M:
             assert np.abs(inst.A[:, S].T @ resid).max() <= 1e-8 * np.linalg.norm(inst.A.T @ inst.y)
+
+
+def test_batch_per_problem_params_and_trials():
+    """cs_solve_batch with one cs_params and one trial count per problem: FP64 and
+    FP32 storage, 3 / 5 / 2 / 4 trials, 2 or 3 outer iterations, both fields and
+    different seeds in one batch (four groups, one graph); each problem matches the
+    oracle run with its own parameters (instance number = its index)."""
+    insts = uneven([150, 97, 260, 64], seed=31)
+    base = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_steps=500)
+    ws = [dict(base, precision="fp64", n_outer=3, field="cn", seed=1),
+          dict(base, precision="fp32", n_outer=2, field="bn", seed=2),
+          dict(base, precision="fp64", n_outer=2, field="bn", seed=3),
+          dict(base, precision="fp32", n_outer=3, field="cn", seed=4)]
+    trials = [3, 5, 2, 4]
+    hs = [cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam) for i in insts]
+    try:
+        cs.cs_solve_batch(hs, [cs.params_from_workload(w) for w in ws], trials)
+        for i, (h, inst, w, T) in enumerate(zip(hs, insts, ws, trials)):
+            x, s, E, st, status = cs.cs_result(h)
+            R, sig, Es, ss = cs.cs_result_trials(h, T, w["n_outer"])
+            r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)
+            np.testing.assert_array_equal(ss, r["support_sizes"])
+            np.testing.assert_array_equal(sig, r["sigmas"])
+            tol = 1e-9 if w["precision"] == "fp64" else 1e-5
+            np.testing.assert_allclose(x, r["x_hat"], rtol=0, atol=tol)
+            assert int(st[0]) == r["best_trial"] and st[4] == T
+    finally:
+        for h in hs:
+            cs.cs_problem_destroy(h)
+
+
+def test_batch_argument_checks():
+    """A problem given twice, or a per-problem list of the wrong length, is refused."""
+    inst = uneven([40], seed=2)[0]
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        prm = cs.params_from_workload(dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=10))
+        with pytest.raises(cs.CSError) as ei:
+            cs.cs_solve_batch([h, h], prm, 2)
+        assert ei.value.status == cs.CS_EINVAL
+        with pytest.raises(ValueError):
+            cs.cs_solve_batch([h], [prm, prm], 2)
+    finally:
+        cs.cs_problem_destroy(h)

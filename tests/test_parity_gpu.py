@@ -313,3 +313,39 @@ def test_barrier_timeout_is_reported_and_context_survives():
     finally:
         cs.cs_problem_destroy(h)
     torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------------ s2: error against FP64 per result
+@pytest.mark.parametrize("precision,refit", [("fp64", "exact"), ("fp32", "exact"), ("bf16", "exact"),
+                                             ("fp16", "exact"), ("fp32", "jacobi")])
+def test_error_against_fp64_is_reported_per_result(precision, refit):
+    """stats[11]: relative error of G_off x_hat with G_off in its storage precision
+    against FP64; stats[12]: FP64 relative residual of the refit's normal equations on
+    the kept support.  Both recomputed here from the returned x_hat (storage rounding
+    by the helper pinned in test_storage_rounding_cpu.py)."""
+    from storage_rounding import round_to_storage
+    inst = cs_inputs.random_instance(300, 180, 30, 0.01, 0.03, seed=17)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=600, precision=precision, refit=refit)
+    g = gpu_solve(inst, w, 4)
+    G, hz, gd = oracle.gram(inst.A, inst.y)
+    Goff = G - np.diag(gd)
+    x = g["x_hat"]
+    if precision == "fp64":
+        Gs = Goff
+    elif precision == "fp32":
+        Gs = Goff.astype(np.float32).astype(np.float64)
+    else:
+        Gs = round_to_storage(Goff, precision)
+    U = Goff @ x
+    e11 = np.abs((Gs - Goff) @ x).max() / np.abs(U).max()
+    S = np.flatnonzero(g["sigma"])
+    e12 = np.abs(hz[S] - G[S] @ x).max() / np.abs(hz[S]).max()
+    if precision == "fp64":
+        assert g["stats"][11] == 0.0
+    else:
+        assert g["stats"][11] == pytest.approx(e11, rel=1e-6)
+        assert 0.0 < g["stats"][11] < {"fp32": 1e-6, "fp16": 1e-2, "bf16": 1e-1}[precision]
+    if refit == "exact":
+        assert g["stats"][12] <= 1e-12 and e12 <= 1e-12
+    else:
+        assert g["stats"][12] == pytest.approx(e12, rel=1e-6)

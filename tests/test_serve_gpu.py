@@ -30,7 +30,7 @@ def _requests():
 def _serve(reqs, slots=3, budget=8 << 30):
     sv = cs.cs_server_create(budget, slots)
     try:
-        tickets = [cs.cs_server_submit(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
+        tickets = [cs.cs_server_submit_host(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
                    for inst, w, T in reqs]
         out = []
         for (inst, w, T), t in zip(reqs, tickets):
@@ -67,9 +67,9 @@ def test_budget_admission_and_ticket_lifecycle():
     try:
         with pytest.raises(cs.CSError) as ei:  # can never fit
             big = cs_inputs.random_instance(4000, 100, 10, 0.0, 0.1, seed=9)
-            cs.cs_server_submit(sv, big.A, big.y, big.lam, cs.cs_params_default(), 64)
+            cs.cs_server_submit_host(sv, big.A, big.y, big.lam, cs.cs_params_default(), 64)
         assert ei.value.status == cs.CS_ENOMEM
-        tickets = [cs.cs_server_submit(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in reqs]
+        tickets = [cs.cs_server_submit_host(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in reqs]
         times = []
         for (inst, w, T), t in zip(reqs, tickets):
             cs.cs_server_wait(sv, t)
@@ -89,6 +89,9 @@ def test_server_argument_checks_need_no_gpu():
     assert cs.lib().cs_server_create(1 << 30, 0, ctypes.byref(h)) == cs.CS_EINVAL
     d = ctypes.c_int32()
     assert cs.lib().cs_server_poll(None, 1, ctypes.byref(d)) == cs.CS_EINVAL
+    t = ctypes.c_uint64()
+    p = cs.cs_params_default()
+    assert cs.lib().cs_server_submit(None, None, ctypes.byref(p), 1, ctypes.byref(t)) == cs.CS_EINVAL
 
 
 @pytest.mark.gpu
@@ -102,7 +105,7 @@ def test_small_requests_backfill_beside_a_large_one():
     sv = cs.cs_server_create(8 << 30, 8)
     try:
         order = [big, small, small, big]
-        tickets = [cs.cs_server_submit(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in order]
+        tickets = [cs.cs_server_submit_host(sv, i.A, i.y, i.lam, cs.params_from_workload(w), T) for i, w, T in order]
         times = []
         for (inst, w, T), t in zip(order, tickets):
             cs.cs_server_wait(sv, t)
@@ -112,3 +115,43 @@ def test_small_requests_backfill_beside_a_large_one():
     b1, s1, s2, b2 = times
     assert s1[1] < b1[2] and s2[1] < b1[2]  # the small ones started before the first large one finished
     assert b2[1] >= b1[2] - 1e-3            # the second large one waited for the SMs
+
+
+@pytest.mark.gpu
+def test_requests_on_a_cached_problem():
+    """cs_server_submit on a problem made once by cs_problem_create: two requests
+    with different seeds (and a third with more trials) reuse its Gram, run one
+    after the other on it, and each matches the oracle with its own parameters;
+    afterwards the problem is back on its own stream and solves directly."""
+    import torch
+    inst = cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=0)
+    base = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=500)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    G0 = cs.cs_problem_gram(h)[0]
+    sv = cs.cs_server_create(8 << 30, 4)
+    reqs = [(dict(base, seed=1), 1), (dict(base, seed=2), 1), (dict(base, seed=3), 3)]
+    try:
+        tickets = [cs.cs_server_submit(sv, h, cs.params_from_workload(w), T) for w, T in reqs]
+        results = []
+        for t in tickets:
+            cs.cs_server_wait(sv, t)
+            results.append(cs.cs_server_result(sv, t, inst.N))
+    finally:
+        cs.cs_server_destroy(sv)
+    try:
+        for (w, T), res in zip(reqs, results):
+            r = oracle.solve(inst.A, inst.y, inst.lam,
+                             oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS}), trials=T)
+            np.testing.assert_array_equal(res[1], r["sigma"])
+            np.testing.assert_allclose(res[0], r["x_hat"], rtol=0, atol=1e-9)
+            assert res[5] == cs.CS_OK
+        # the requests ran one after the other on the one problem
+        times = [res[4] for res in results]
+        assert times[1][1] >= times[0][2] - 1e-3 and times[2][1] >= times[1][2] - 1e-3
+        # its Gram is untouched and it is usable directly again
+        np.testing.assert_array_equal(cs.cs_problem_gram(h)[0], G0)
+        cs.cs_solve(h, cs.params_from_workload(reqs[0][0]), 1)
+        x, s, E, st, status = cs.cs_result(h)
+        np.testing.assert_allclose(x, results[0][0], rtol=0, atol=1e-9)
+    finally:
+        cs.cs_problem_destroy(h)
