@@ -49,6 +49,7 @@ enum { CS_FIELD_CN = 0, CS_FIELD_BN = 1 };          /* Eq. localfieldMFZ / Eq. l
 enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1 };   /* normal equations / damped Jacobi */
 enum { CS_PUMP_LINEAR = 0, CS_PUMP_SIGMOID = 1 };   /* p0 -> p1 ramp / Eq. pumprateGACS */
 enum { CS_INIT_UNIFORM = 0, CS_INIT_NORMAL = 1 };   /* U(-s, s) / N(0, s^2) */
+enum { CS_READOUT_FINAL = 0, CS_READOUT_BEST = 1 }; /* sigma of a CIM run: last / best visited */
 /* Storage precision of the coupling matrix G and arithmetic of the Euler loop:
  * FP64 keeps G and the amplitudes in double; the others accumulate in float.
  * FP8 is E4M3 with one FP32 scale per row of G_off (its largest magnitude / 448). */
@@ -106,6 +107,18 @@ typedef struct {
                            2: tensor-core forms only; 3: mma.sync tensor-core forms only;
                            4: the tcgen05 form only (resident FP32 G_off).  2, 3 and 4 make
                            the solve fail with CS_EINVAL where no such form applies */
+  int32_t self_term;    /* 0: the injection of Eq. MFZlocalfieldmain as written (its Hamiltonian,
+                           Eq. l0Hamiltonian, has no self-term, so a spin at its refit value turns
+                           on when G_rr R_r^2 > lambda); 1: corrected mode, the injection also
+                           subtracts (sqrt tau / 4) G_rr R_r^2, so that it turns on when
+                           1/2 G_rr R_r^2 > lambda, the single-spin decision of Eq. doublel0 */
+  int32_t readout;      /* CS_READOUT_FINAL: sigma = H(c) at the end of each CIM run (the paper);
+                           CS_READOUT_BEST: the first configuration H(c_n), n = 1 .. n_steps, of
+                           lowest objective (Eq. doublel0 at the run's R, lambda = eta^2 / 2), the
+                           readout the paper's discussion proposes.  BEST needs the binarised field
+                           (its product is the configuration's coupling term) and single solves;
+                           each run then keeps a history of (n_steps + 1) x N x trials bytes and
+                           (n_steps + 1) x CTAs x trials doubles on the device */
 } cs_params;
 
 typedef struct cs_problem cs_problem;

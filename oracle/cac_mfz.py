@@ -48,7 +48,10 @@ step, the symmetry and zero diagonal of J, the published SplitMix64 outputs,
 the moments of the initial-amplitude distributions, the pump and eta
 schedules at closed-form points, the Gram matrix by brute force, the
 recomputed objective, the zero gradient of the exact refit, the ridge on a
-singular support, and the damped Jacobi refit converging to the exact one;
+singular support, the damped Jacobi refit (two sweeps worked by hand, and its
+convergence to the exact refit), the corrected self-term (hand-worked step,
+separable case, brute force against Eq. doublel0) and the best-configuration
+readout (against the recorded trajectory scored by objective());
 tests/test_oracle_mutations.py plants mistakes in it and checks that a pin
 fails for each.
 """
@@ -64,7 +67,8 @@ import scipy.linalg
 __all__ = [
     "Params", "splitmix64_mix", "counter_uniform", "initial_amplitudes", "gram",
     "coupling_J", "pump", "eta_at", "local_field_cn", "local_field_bn", "injection",
-    "euler_step", "cim_run", "refit_exact", "refit_jacobi", "objective", "rmse",
+    "euler_step", "self_term_correction", "readout_energy", "cim_run", "refit_exact", "refit_jacobi",
+    "objective", "rmse",
     "hamming_loss", "solve",
 ]
 
@@ -104,6 +108,8 @@ class Params:
     jacobi_dt: float = 0.1
     jacobi_iters: int = 100
     seed: int = 0
+    self_term: bool = False      # corrected mode: the injection also subtracts (sqrt tau / 4) G_rr R_r^2
+    readout: str = "final"       # "final": H(c) at the end of each run; "best": the best configuration visited
 
 
 # ---------------------------------------------------------------- random numbers
@@ -226,6 +232,26 @@ def injection(j, e, R, h, eta, tau):
     return j * e * (R * h - (eta * eta / 4.0) * math.sqrt(tau))
 
 
+def self_term_correction(g, R, tau):
+    """(sqrt tau / 4) G_rr R_r^2, subtracted inside the injection in corrected mode.
+
+    The Hamiltonian of Eq. l0Hamiltonian has no self-term 1/2 G_rr R_r^2 sigma_r,
+    so with R_r at its Jacobi fixed point the injection switches spin r on when
+    G_rr R_r^2 > eta^2 / 2 = lambda, while Eq. doublel0 is lowered by it only
+    when 1/2 G_rr R_r^2 > lambda.  Subtracting this term restores the objective's
+    own single-spin decision (the discussion of Eq. MFZlocalfieldmain gives the
+    field at the stationary amplitudes c = +-sqrt(tau))."""
+    return (math.sqrt(tau) / 4.0) * g[:, None] * R * R
+
+
+def readout_energy(Goff, g, hz, R, sigma, lam):
+    """Eq. doublel0 at (R, sigma) less the constant 1/2 y^T y, per trial (columns):
+    1/2 x^T G x - (A^T y)^T x + lam |sigma| with x = sigma o R and G = G_off + diag(g)."""
+    x = sigma * R
+    return 0.5 * np.sum(x * (Goff @ x), axis=0) + 0.5 * np.sum(g[:, None] * x * x, axis=0) \
+        - hz @ x + lam * np.sum(sigma, axis=0)
+
+
 def euler_step(c, e, p, inj, prm: Params):
     """One explicit Euler step of Eq. mfeq1 and Eq. GMFZEC5, both from the old (c, e)."""
     dc = (-1.0 + p - c * c) * c + prm.K * inj
@@ -234,13 +260,17 @@ def euler_step(c, e, p, inj, prm: Params):
 
 
 def cim_run(Goff, hz, R, eta, prm: Params, outer: int, inst: int = 0,
-            record_steps: int = 0, max_steps: Optional[int] = None):
+            record_steps: int = 0, max_steps: Optional[int] = None, g=None):
     """One CIM run (support estimation of Algorithm 1) for all trials (columns of R).
 
     Returns sigma (N, T) uint8, the final (c, e) and, if record_steps > 0, the
     amplitudes c and e after each of the first record_steps steps
     (shape (record_steps, N, T)).  max_steps stops the run early (a bounded
     sample for tests and timing; the schedules still refer to prm.n_steps).
+    g = diag(G) is needed by the corrected mode and the "best" readout: the
+    latter (the paper's future-work readout: compare the configurations visited
+    rather than take the last) returns, per trial, the first of H(c_1), ...,
+    H(c_S) with the lowest readout_energy at lambda = eta^2 / 2.
     """
     N, T = R.shape
     c = np.stack([initial_amplitudes(prm.seed, inst, t, outer, N, prm.init_kind, prm.init_scale)
@@ -249,15 +279,28 @@ def cim_run(Goff, hz, R, eta, prm: Params, outer: int, inst: int = 0,
     rec_c = np.zeros((record_steps, N, T)) if record_steps else None
     rec_e = np.zeros((record_steps, N, T)) if record_steps else None
     field = local_field_cn if prm.field == "cn" else local_field_bn
+    corr = self_term_correction(g, R, prm.tau) if prm.self_term else None
+    best_E = np.full(T, np.inf)
+    best_s = np.zeros((N, T), dtype=np.uint8)
     for n in range(prm.n_steps if max_steps is None else min(max_steps, prm.n_steps)):
         p = pump(n, prm)
         h = field(Goff, R, c, hz, prm.tau)
         inj = injection(prm.j, e, R, h, eta, prm.tau)
+        if corr is not None:
+            inj = inj - prm.j * e * corr
         c, e = euler_step(c, e, p, inj, prm)
         if n < record_steps:
             rec_c[n] = c
             rec_e[n] = e
+        if prm.readout == "best":
+            s = (c > 0.0).astype(np.uint8)
+            E = readout_energy(Goff, g, hz, R, s, eta * eta / 2.0)
+            better = E < best_E  # strict: the first configuration of the lowest energy is kept
+            best_E = np.where(better, E, best_E)
+            best_s[:, better] = s[:, better]
     sigma = (c > 0.0).astype(np.uint8)  # H(c), H(0) = 0
+    if prm.readout == "best":
+        sigma = best_s
     return sigma, c, e, rec_c, rec_e
 
 
@@ -362,7 +405,7 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
         eta = eta_at(i, prm, lam)
         sigma, c, e, rc, re = cim_run(Goff, hz, R, eta, prm, outer=i, inst=inst,
                                       record_steps=record_steps if i == 0 else 0,
-                                      max_steps=max_steps)
+                                      max_steps=max_steps, g=g)
         if i == 0 and record_steps:
             rec = (rc, re)
         for t in range(trials):

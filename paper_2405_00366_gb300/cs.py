@@ -32,6 +32,8 @@ FIELDS = {"cn": CS_FIELD_CN, "bn": CS_FIELD_BN}
 PUMPS = {"linear": CS_PUMP_LINEAR, "sigmoid": CS_PUMP_SIGMOID}
 INITS = {"uniform": CS_INIT_UNIFORM, "normal": CS_INIT_NORMAL}
 REFITS = {"exact": CS_REFIT_EXACT, "jacobi": CS_REFIT_JACOBI}
+CS_READOUT_FINAL, CS_READOUT_BEST = 0, 1
+READOUTS = {"final": CS_READOUT_FINAL, "best": CS_READOUT_BEST}
 
 
 class cs_params(ctypes.Structure):
@@ -49,6 +51,7 @@ class cs_params(ctypes.Structure):
         ("instance", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
         ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
         ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32), ("tensor_form", ctypes.c_int32),
+        ("self_term", ctypes.c_int32), ("readout", ctypes.c_int32),
     ]
 
 
@@ -119,13 +122,16 @@ def _check(status: int, allow=(CS_OK,)) -> int:
 
 def cs_params_default(**overrides) -> cs_params:
     """cs_params filled by the library's defaults, then `overrides` (names as in cs.h;
-    the string forms 'fp32', 'cn', 'linear', 'uniform', 'exact' are accepted)."""
+    the string forms 'fp32', 'cn', 'linear', 'uniform', 'exact', 'best' are accepted)."""
     p = cs_params()
     lib().cs_params_default(ctypes.byref(p))
-    maps = {"precision": PRECISIONS, "field": FIELDS, "pump_kind": PUMPS, "init_kind": INITS, "refit": REFITS}
+    maps = {"precision": PRECISIONS, "field": FIELDS, "pump_kind": PUMPS, "init_kind": INITS, "refit": REFITS,
+            "readout": READOUTS}
     for k, v in overrides.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]
+        if isinstance(v, bool):
+            v = int(v)
         if not hasattr(p, k):
             raise KeyError(k)
         setattr(p, k, v)

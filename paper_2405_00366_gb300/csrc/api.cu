@@ -77,7 +77,7 @@ cudaError_t alloc(T** p, size_t elems) {
 
 void free_solve(SolveDev& S, cudaStream_t st) {
   void* ptrs[] = {S.R, S.X0, S.X1, S.state, S.lead, S.job, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
-                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular, S.err4};
+                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular, S.err4, S.e_hist, S.s_hist};
   for (void* q : ptrs) dev_free(q, st);
   S = SolveDev();
 }
@@ -138,6 +138,24 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
   S.n_outer = prm.n_outer;
   S.record_steps = rec;
   S.precision = prm.precision;
+  if (prm.readout == CS_READOUT_BEST) {
+    // history of the best-configuration readout: per step the configuration
+    // (N x T bytes) and each CTA's energy partials (T doubles)
+    const size_t steps = (size_t)prm.n_steps + 1;
+    const size_t ne = steps * (size_t)P.num_sms * trials, ns = steps * (size_t)P.N * trials;
+    if (!S.e_hist || S.cap_e_hist < ne || S.cap_s_hist < ns) {
+      dev_free(S.e_hist, P.stream);
+      dev_free(S.s_hist, P.stream);
+      S.e_hist = nullptr;
+      S.s_hist = nullptr;
+      S.cap_e_hist = S.cap_s_hist = 0;
+      g_alloc_stream = P.stream;
+      CS_CUDA(alloc(&S.e_hist, ne), "cudaMalloc readout energies");
+      CS_CUDA(alloc(&S.s_hist, ns), "cudaMalloc readout configurations");
+      S.cap_e_hist = ne;
+      S.cap_s_hist = ns;
+    }
+  }
   return CS_OK;
 }
 
@@ -171,6 +189,10 @@ cs_status check_params(const cs_params* p, int trials) {
     return fail(CS_EINVAL, "tensor_form >= 2: no tensor-core form for FP64 or FP8 storage");
   if (p->tensor_form == 4 && (p->precision != CS_P_FP32 || p->stream_g == 1))
     return fail(CS_EINVAL, "tensor_form = 4: the tcgen05 form is built for resident FP32 G_off only");
+  if (p->self_term != 0 && p->self_term != 1) return fail(CS_EINVAL, "self_term must be 0 or 1");
+  if (p->readout != CS_READOUT_FINAL && p->readout != CS_READOUT_BEST) return fail(CS_EINVAL, "bad readout");
+  if (p->readout == CS_READOUT_BEST && p->field != CS_FIELD_BN)
+    return fail(CS_EINVAL, "readout = CS_READOUT_BEST needs the binarised field (CS_FIELD_BN)");
   const double vals[] = {p->p0, p->p1, p->p_thr, p->d, p->t0, p->width, p->beta, p->K, p->j,
                          p->eta_init, p->eta_end, p->velo, p->init_scale};
   for (double v : vals)
@@ -387,6 +409,11 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
                                  : "N too large for the on-chip Euler kernel at this precision");
     if (e != cudaSuccess)
       return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
+    if (prm->readout == CS_READOUT_BEST) {
+      CS_CUDA(launch_readout(S.e_hist, S.s_hist, S.sigma, (int)P.N, S.trials, prm->n_steps, S.plan_ctas, P.stream),
+              "readout launch");
+      P.launches += 1;
+    }
     CS_CUDA(mark(p, TM_EULER, false), "event");
     CS_CUDA(mark(p, TM_REFIT, true), "event");
     CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream), "refit launch");
@@ -410,6 +437,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     if (trials[i] > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials per problem");
     if (prms[i]->record_steps != 0) return fail(CS_EINVAL, "a batched solve does not record trajectories");
     if (prms[i]->tensor_form == 4) return fail(CS_EINVAL, "tensor_form = 4: the batched kernel has no tcgen05 form");
+    if (prms[i]->readout != CS_READOUT_FINAL)
+      return fail(CS_EINVAL, "a batched solve reads out the final configuration only (readout = CS_READOUT_FINAL)");
     if (ps[i]->P.stream != ps[0]->P.stream || ps[i]->P.device != ps[0]->P.device)
       return fail(CS_EINVAL, "the problems of a batch must share one stream and device");
     for (int k = 0; k < i; ++k)

@@ -76,6 +76,7 @@ struct BInst {
   const float* gscale;     // row scales (FP8 storage)
   const double* R;         // N x T
   const double* hz;        // N
+  const double* g;         // N, diag G (the corrected mode's self-term)
   CT* X0;                  // Npad x twp, rows >= N zero
   CT* X1;
   CT* state;               // c, e, b: 3 x N x T
@@ -83,7 +84,7 @@ struct BInst {
   double theta;            // sqrt(tau) eta^2 / 4 of this problem
   int inst;                // instance number of the initial-amplitude key
   // this problem's run parameters (cs_params)
-  int n_steps, pump_kind, field, init_kind;
+  int n_steps, pump_kind, field, init_kind, self_term;
   double dt, p0, p1, p_thr, d, t0, width, beta, tau, Kj, init_scale;
   uint64_t seed;
 };
@@ -506,14 +507,16 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
         if (r >= N) continue;
         const double v = (double)(tile_sum<CT, PAIR>(P, idx / T, t, twp) * row_scale<GT, CT>(I.gscale, r));
         const size_t o = (size_t)r * T + t;
-        b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta);
+        const double corr = I.self_term ? (st / 4.0) * I.g[r] * I.R[o] * I.R[o] : 0.0;
+        b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta - corr);
       }
       __syncthreads();
     }
   } else {
     for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
       const int r = (int)(o / T);
-      b[o] = CT((st / 2.0) * I.R[o] * I.hz[r] - I.theta);
+      const double corr = I.self_term ? (st / 4.0) * I.g[r] * I.R[o] * I.R[o] : 0.0;
+      b[o] = CT((st / 2.0) * I.R[o] * I.hz[r] - I.theta - corr);
     }
   }
   for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
@@ -803,10 +806,11 @@ template <typename CT>
 static void fill_inst(BInst<CT>& I, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
                       int inst) {
   I.N = (int)P.N; I.nrt = (int)((P.N + kRT - 1) / kRT); I.nkc = (int)(P.Npad / kKC);
-  I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz;
+  I.Gt = P.Gt; I.gscale = P.gscale; I.R = S.R; I.hz = P.hz; I.g = P.g;
   I.X0 = (CT*)S.X0; I.X1 = (CT*)S.X1; I.state = (CT*)S.state; I.sigma = S.sigma;
   I.theta = theta; I.inst = inst;
   I.n_steps = prm.n_steps; I.pump_kind = prm.pump_kind; I.field = prm.field; I.init_kind = prm.init_kind;
+  I.self_term = prm.self_term;
   I.dt = prm.dt; I.p0 = prm.p0; I.p1 = prm.p1; I.p_thr = prm.p_thr; I.d = prm.d; I.t0 = prm.t0;
   I.width = prm.width; I.beta = prm.beta; I.tau = prm.tau; I.Kj = prm.K * prm.j; I.init_scale = prm.init_scale;
   I.seed = prm.seed;

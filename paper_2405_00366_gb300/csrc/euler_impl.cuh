@@ -109,7 +109,8 @@ EulerFn<CT> kernel_for(int MR, bool stream, bool wide, bool tc, bool tc5 = false
 // what this model resolves.
 template <typename GT, typename CT>
 cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool force_stream, int tensor_form, Plan* out,
-                      std::vector<std::pair<double, Plan>>* cands = nullptr, bool single_cluster = false) {
+                      std::vector<std::pair<double, Plan>>* cands = nullptr, bool single_cluster = false,
+                      int nst = 4) {
   const int N = (int)P.N, nq = (int)(P.Npad / 4);
   const int sms = max_ctas > 0 ? std::min(max_ctas, P.num_sms) : P.num_sms;
   const int twmax = round4(std::min(T, kTChunk));
@@ -235,7 +236,8 @@ cudaError_t make_plan(const ProblemDev& P, int T, int hint, int max_ctas, bool f
             const int min_slots = (stream && tps > 1) ? 3 : ((stream || tc5) ? 2 : 3);
             for (int slots = 8; slots >= min_slots; --slots) {
               if ((size_t)slots * pl.slot_bytes < kpart) break;  // the ring holds the k-warp partials
-              pl.smem = smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT)).total;
+              pl.smem =
+                  smem_layout(gblock, pl.slot_bytes, slots, pl.RPC_pad, twmax, pl.ORW, T, sizeof(CT), nst).total;
               if (pl.smem <= cap) { pl.slots = slots; break; }
             }
           }
@@ -389,6 +391,12 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
   a.field = prm.field; a.init_kind = prm.init_kind; a.init_scale = prm.init_scale;
   a.seed = prm.seed; a.instance = prm.instance; a.outer = outer;
   a.flags = S.bar; a.err = S.err; a.timeout_cycles = timeout_cycles;
+  a.g = P.g;
+  a.self_term = prm.self_term;
+  a.readout = prm.readout;
+  a.lam_read = eta * eta / 2.0;
+  a.e_hist = S.e_hist;
+  a.s_hist = S.s_hist;
   a.phantom = (unsigned)prm.test_phantom_ctas;
   S.plan_cluster = pl.C;
   S.plan_ctas = pl.C * pl.NC;
@@ -480,16 +488,16 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   // cache per process (so every thread and every solve of a shape agrees)
   struct Key {
     int64_t N;
-    int T, hint, cap, strm, dev, tune, notc;
+    int T, hint, cap, strm, dev, tune, notc, best;
     bool operator<(const Key& o) const {
-      return std::tie(N, T, hint, cap, strm, dev, tune, notc) <
-             std::tie(o.N, o.T, o.hint, o.cap, o.strm, o.dev, o.tune, o.notc);
+      return std::tie(N, T, hint, cap, strm, dev, tune, notc, best) <
+             std::tie(o.N, o.T, o.hint, o.cap, o.strm, o.dev, o.tune, o.notc, o.best);
     }
   };
   static std::mutex mu;
   static std::map<Key, Plan> cache;
   const Key key{P.N, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g, P.device, prm.autotune,
-                prm.tensor_form};
+                prm.tensor_form, prm.readout};
   Plan pl;
   bool hit = false;
   {
@@ -500,8 +508,8 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
   if (!hit) {
     std::vector<std::pair<double, Plan>> cands;
     cudaError_t e = make_plan<GT, CT>(P, S.trials, prm.cluster_size, prm.max_ctas, prm.stream_g == 1,
-                                      prm.tensor_form, &pl, &cands,
-                                      prm.autotune != 0);
+                                      prm.tensor_form, &pl, &cands, prm.autotune != 0,
+                                      prm.readout == CS_READOUT_BEST ? 5 : 4);
     if (e != cudaSuccess) return e;
     if (prm.autotune && cands.size() > 1) {
       e = autotune_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands, &pl);

@@ -104,6 +104,12 @@ struct EulerArgs {
   double init_scale;
   uint64_t seed;
   int instance, outer;
+  const double* g;   // diag G (FP64): the corrected mode's self-term and the readout energy
+  int self_term;     // 1: the injection also subtracts (sqrt tau / 4) G_rr R_r^2 (folded into b)
+  int readout;       // CS_READOUT_BEST: record per step the configuration and the CTA's energy partials
+  double lam_read;   // lambda of the readout energy, eta^2 / 2
+  double* e_hist;    // (n_steps + 1) x gridDim.x x T energy partials
+  uint8_t* s_hist;   // (n_steps + 1) x N x T configurations
   unsigned* flags;  // per CTA: X publications so far (gridDim.x words, then one word never written)
   int* err;
   long long timeout_cycles;
@@ -131,14 +137,16 @@ constexpr int kMiscWords = 2 + kMaxSlots;
 struct Smem {
   size_t g, ring, part, st, bars, total;
 };
+// The owned state: c, e, b, R and, for the best-configuration readout, the
+// coupling term of each owned element (nst = 5).
 __host__ __device__ __forceinline__ Smem smem_layout(size_t gbytes_block, size_t slot_bytes, int slots, int prows,
-                                                     int twmax, int ORW, int T, size_t cbytes) {
+                                                     int twmax, int ORW, int T, size_t cbytes, int nst = 4) {
   Smem s;
   s.g = 0;
   s.ring = align128(gbytes_block);
   s.part = s.ring + align128((size_t)slots * slot_bytes);
   s.st = s.part + align128((size_t)prows * twmax * cbytes);
-  s.bars = s.st + align128((size_t)4 * ORW * T * cbytes);
+  s.bars = s.st + align128((size_t)nst * ORW * T * cbytes);
   // full[slots], empty[slots], the accumulator barrier of the tcgen05 form, then
   // kMiscWords 32-bit words (TMEM address, barrier outcomes, last ring uses)
   s.total = s.bars + (2 * (size_t)slots + 1) * sizeof(uint64_t) + kMiscWords * sizeof(uint32_t);
@@ -1114,8 +1122,9 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   const int own0 = j * a.ORW;                      // first owned row (cluster-local)
   const int nown = max(0, min(a.ORW, nrows - own0));
   const int twmax = round4(min(T, kTChunk));
+  const bool best = a.readout == CS_READOUT_BEST;
   const Smem L = smem_layout(STREAM ? 0 : (size_t)a.RPC_pad * a.ldg * sizeof(GT), a.slot_bytes, a.slots,
-                             a.RPC_pad, twmax, a.ORW, T, sizeof(CT));
+                             a.RPC_pad, twmax, a.ORW, T, sizeof(CT), best ? 5 : 4);
   GT* Gsm = reinterpret_cast<GT*>(smem_raw + L.g);
   unsigned char* ring = smem_raw + L.ring;
   CT* P = reinterpret_cast<CT*>(smem_raw + L.part);
@@ -1123,6 +1132,7 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
   CT* e_s = c_s + (size_t)a.ORW * T;
   CT* b_s = e_s + (size_t)a.ORW * T;
   CT* R_s = b_s + (size_t)a.ORW * T;
+  CT* u_s = R_s + (size_t)a.ORW * T;  // readout: coupling term of the configuration at this step
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
   uint64_t* empty = full + a.slots;
   uint64_t* accbar = empty + a.slots;
@@ -1257,7 +1267,8 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         const CT v = sum_partials(cluster, P, (size_t)pidx<TC5>(own0 + r, tt, twp), C) *
                      row_scale<GT, CT>(a.gscale, gr) * xsi;
         const double Rr = a.R[(size_t)gr * T + t0 + tt];
-        b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta);
+        const double corr = a.self_term ? (st / 4.0) * a.g[gr] * Rr * Rr : 0.0;
+        b_s[(size_t)r * T + t0 + tt] = CT(Rr * (-(st / 4.0) * (double)v + (st / 2.0) * a.hz[gr]) - a.theta - corr);
       }
       cluster.sync();
     }
@@ -1265,7 +1276,9 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
     for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
       const int r = idx / T, t = idx % T;
       const int gr = row0 + own0 + r;
-      b_s[idx] = CT((st / 2.0) * a.R[(size_t)gr * T + t] * a.hz[gr] - a.theta);
+      const double Rr = a.R[(size_t)gr * T + t];
+      const double corr = a.self_term ? (st / 4.0) * a.g[gr] * Rr * Rr : 0.0;
+      b_s[idx] = CT((st / 2.0) * Rr * a.hz[gr] - a.theta - corr);
     }
   }
   for (int idx = threadIdx.x; idx < nown * T; idx += kThreads) {
@@ -1281,6 +1294,24 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
                                 ((a.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
   }
   publish();
+
+  // Best-configuration readout: this CTA's share of the objective (less
+  // 1/2 y^T y) of the configuration recorded for step m, per trial, in FP64:
+  // sum over owned r on it of R_r (1/2 U_r + 1/2 G_rr R_r - h^z_r) + lambda.
+  auto energy_pass = [&](int m) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += kThreads) {
+      double E = 0.0;
+      for (int r = 0; r < nown; ++r) {
+        const int gr = row0 + own0 + r;
+        if (a.s_hist[((size_t)m * N + gr) * T + t]) {
+          const double Rr = a.R[(size_t)gr * T + t];
+          E += Rr * (0.5 * (double)u_s[(size_t)r * T + t] + 0.5 * a.g[gr] * Rr - a.hz[gr]) + a.lam_read;
+        }
+      }
+      a.e_hist[((size_t)m * gridDim.x + blockIdx.x) * T + t] = E;
+    }
+  };
 
   // ---- Euler steps
   const CT dt = CT(a.dt), beta = CT(a.beta), tau = CT(a.tau), Kj = CT(a.Kj);
@@ -1319,6 +1350,11 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
         const CT Rr = R_s[so];
         const CT f = wcoef * Rr * U + b_s[so];
         const CT cc = c_s[so], ee = e_s[so];
+        if (best) {  // the configuration c_n whose coupling term U this step's product formed
+          const bool sg = cc > CT(0);
+          u_s[so] = sg ? U : CT(0);
+          a.s_hist[((size_t)n * N + gr) * T + t0 + tt] = sg ? 1 : 0;
+        }
         const CT c2 = cc * cc;
         const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
         const CT en = ee + dt * (-beta * (c2 - tau) * ee);
@@ -1338,9 +1374,46 @@ __global__ void __launch_bounds__(kThreads, 1) euler_kernel(EulerArgs<CT> a) {
       // every CTA of the cluster has read this CTA's partials before they are rewritten
       if (t0 + kTChunk < T) cluster.sync();
     }
+    if (best) energy_pass(n);
     if (last_step) break;
     publish();  // the next X, read by bulk copies (async proxy) of the CTAs whose k range holds these rows
     CT* tmp = Xc; Xc = Xn; Xn = tmp;
+  }
+  if (best) {
+    // the final configuration c_S: one more product (of the X the last step wrote), no update
+    publish();
+    for (int t0 = 0; t0 < T; t0 += kTChunk) {
+      const int tw = min(kTChunk, T - t0), twp = round4(tw);
+      block_partials<GT, CT, MR, STREAM, WIDE, TC, TC5>(a, Gsm, Xn + xblock(t0, Npad), twp, k0, klen, nrows, cl, ring,
+                                                         P, full, empty, accbar, rs, gsi, last, tmem);
+      cluster.sync();
+      const int nel = nown * tw;
+      for (int base = threadIdx.x; base < nel; base += kUpd * kThreads) {
+        int off[kUpd];
+        bool val[kUpd];
+        CT Us[kUpd];
+#pragma unroll
+        for (int k = 0; k < kUpd; ++k) {
+          const int idx = base + k * kThreads;
+          val[k] = idx < nel;
+          off[k] = val[k] ? pidx<TC5>(own0 + idx / tw, idx % tw, twp) : 0;
+        }
+        gather_sums_c(cluster, P, C, off, val, Us);
+#pragma unroll
+        for (int k = 0; k < kUpd; ++k) {
+          const int idx = base + k * kThreads;
+          if (!val[k]) continue;
+          const int r = idx / tw, tt = idx % tw;
+          const int gr = row0 + own0 + r;
+          const size_t so = (size_t)r * T + t0 + tt;
+          const bool sg = c_s[so] > CT(0);
+          u_s[so] = sg ? Us[k] * row_scale<GT, CT>(a.gscale, gr) * xsi : CT(0);
+          a.s_hist[((size_t)a.n_steps * N + gr) * T + t0 + tt] = sg ? 1 : 0;
+        }
+      }
+      if (t0 + kTChunk < T) cluster.sync();
+    }
+    energy_pass(a.n_steps);
   }
   leave();  // peers may still read this CTA's partials until the cluster leaves together
 }

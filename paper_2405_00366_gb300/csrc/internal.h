@@ -103,6 +103,9 @@ struct SolveDev {
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
   double* err4 = nullptr;       // 4 doubles: scratch of the error against FP64 (launch_finish)
+  double* e_hist = nullptr;     // best-configuration readout: (n_steps + 1) x CTAs x T energy partials
+  uint8_t* s_hist = nullptr;    // and (n_steps + 1) x N x T configurations
+  size_t cap_e_hist = 0, cap_s_hist = 0;
   RefitJob* job = nullptr;      // this problem's refit job (device copy)
   bool done = false;
   int plan_cluster = 0, plan_ctas = 0, plan_form = 0;  // work split of the last Euler launch
@@ -152,5 +155,10 @@ cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, s
 // Objective per trial, kept trial, and the kept result's error against FP64
 // (stats[11], stats[12]); err4 is 4 doubles of scratch per job.
 cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st, double* err4);
+// Best-configuration readout of one CIM run (euler.cu): per trial the first
+// step n in 1 .. S whose summed energy (CTA partials in fixed order) is lowest;
+// sigma (N x T) takes that step's configuration.
+cudaError_t launch_readout(const double* e_hist, const uint8_t* s_hist, uint8_t* sigma, int N, int T, int S,
+                           int ctas, cudaStream_t st);
 
 }  // namespace cs

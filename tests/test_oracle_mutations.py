@@ -7,6 +7,8 @@ mistakes they are meant to notice.  Everything here runs on the CPU.
 """
 import math
 
+import numpy as np
+
 import pytest
 
 import oracle
@@ -137,3 +139,28 @@ def test_planted_jacobi_mistake_is_caught(monkeypatch, fake):
     monkeypatch.setattr(om, "refit_jacobi", fake)
     monkeypatch.setattr(oracle, "refit_jacobi", fake)
     assert _fails(pins.test_damped_jacobi_two_sweeps_hand_worked)
+
+
+def _corr_half(g, R, tau):
+    return (math.sqrt(tau) / 2.0) * g[:, None] * R * R
+
+
+def _readout_no_diagonal(Goff, g, hz, R, sigma, lam):
+    x = sigma * R
+    return 0.5 * np.sum(x * (Goff @ x), axis=0) - hz @ x + lam * np.sum(sigma, axis=0)
+
+
+def test_planted_self_term_mistake_is_caught(monkeypatch):
+    """The correction with 1/2 in place of 1/4 fails the hand-worked step and the
+    separable case of the corrected mode."""
+    monkeypatch.setattr(om, "self_term_correction", _corr_half)
+    monkeypatch.setattr(oracle, "self_term_correction", _corr_half)
+    assert _fails(pins.test_three_spin_hand_worked_step)
+    assert _fails(pins.test_separable_case_corrected_mode_is_the_objective_threshold, "cn")
+
+
+def test_planted_readout_mistake_is_caught(monkeypatch):
+    """A readout energy without the diagonal term fails the trajectory pin."""
+    monkeypatch.setattr(om, "readout_energy", _readout_no_diagonal)
+    monkeypatch.setattr(oracle, "readout_energy", _readout_no_diagonal)
+    assert _fails(pins.test_best_readout_is_the_first_lowest_objective_on_the_trajectory, "bn")

@@ -5,6 +5,7 @@ the mathematics fixes: published generator outputs, a hand-worked Euler step,
 closed forms (the separable case reduces to hard thresholding), brute force over
 every support, a library least-squares solver, and algebraic identities.
 """
+import dataclasses
 import itertools
 import math
 import os
@@ -130,6 +131,13 @@ def test_three_spin_hand_worked_step():
         c1, e1 = oracle.euler_step(c, e, p, inj, prm)
         np.testing.assert_allclose(c1[:, 0], gold["c_" + field], rtol=0, atol=1e-15)
         np.testing.assert_allclose(e1[:, 0], gold["e_next"], rtol=0, atol=1e-15)
+        # corrected mode: the self-term restored inside the injection
+        corr = oracle.self_term_correction(np.diag(G), R, 1.0)
+        np.testing.assert_allclose(corr[:, 0], gold["corr"], rtol=0, atol=1e-15)
+        inj_c = inj - 1.0 * e * corr
+        np.testing.assert_allclose(inj_c[:, 0], gold["inj_" + field + "_corr"], rtol=0, atol=1e-15)
+        c2, _ = oracle.euler_step(c, e, p, inj_c, prm)
+        np.testing.assert_allclose(c2[:, 0], gold["c_" + field + "_corr"], rtol=0, atol=1e-15)
 
 
 # ------------------------------------------------------------------ refit
@@ -245,6 +253,21 @@ def _separable(N, lam, seed):
 
 
 @pytest.mark.parametrize("field", ["cn", "bn"])
+def test_separable_case_corrected_mode_is_the_objective_threshold(field):
+    """Corrected mode (self-term restored): with G = I the support is the hard
+    threshold of Eq. doublel0 itself, {r : |(A^T y)_r| > sqrt(2 lambda)} (the L0
+    proximal operator), and R = A^T y."""
+    lam = 0.05
+    A, y, hz = _separable(60, lam, seed=4)
+    prm = Params(n_outer=2, n_steps=1000, dt=0.01, field=field, seed=1, self_term=True)
+    res = oracle.solve(A, y, lam, prm, trials=2)
+    expect = (hz ** 2 > 2 * lam).astype(np.uint8)
+    for t in range(2):
+        np.testing.assert_array_equal(res["sigmas"][:, t], expect)
+        np.testing.assert_allclose(res["R"][:, t], hz, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("field", ["cn", "bn"])
 def test_separable_case_is_hard_threshold(field):
     """With G = I the dynamics reduce to one scalar ODE per spin whose injection has
     the sign of hz_r^2 - lambda (paper-literal Hamiltonian without the self-term),
@@ -306,6 +329,61 @@ def test_brute_force_minimum_over_all_supports():
     seeds (8 of 12 with these seeds; planted mistakes in the field or the
     injection drop this to 6 or fewer)."""
     assert brute_force_hits() >= 7
+
+
+def brute_force_hits_corrected(n_seeds=12, trials=4):
+    """As brute_force_hits in corrected mode, against Eq. doublel0 itself (lambda,
+    not lambda / 2): never below the minimum; the number of seeds that reach it."""
+    hits = 0
+    for seed in range(n_seeds):
+        inst = cs_inputs.random_instance(12, 8, 3, 0.05, 0.04, seed=100 + seed)
+        prm = Params(n_outer=12, n_steps=1000, dt=0.02, pump_kind="sigmoid", eta_init=0.8,
+                     eta_end=math.sqrt(2 * inst.lam), velo=8, seed=seed, self_term=True)
+        res = oracle.solve(inst.A, inst.y, inst.lam, prm, trials=trials)
+        best, arg = _all_supports_min(inst.A, inst.y, inst.lam)
+        for t in range(trials):
+            S = np.flatnonzero(res["sigmas"][:, t])
+            r = inst.y - inst.A[:, S] @ res["R"][S, t]
+            assert 0.5 * float(r @ r) + inst.lam * len(S) >= best - 1e-10
+        hits += tuple(np.flatnonzero(res["sigma"])) == arg
+    return hits
+
+
+def test_brute_force_minimum_corrected_mode():
+    """Corrected mode minimises Eq. doublel0 with the user's lambda: never below the
+    brute-force minimum over all 2^12 supports (asserted per trial), and equal to
+    it on half of these seeds (6 of 12; the method is a heuristic, and the formula
+    of the correction itself is pinned by the three-spin step and the separable
+    case)."""
+    assert brute_force_hits_corrected() >= 5
+
+
+@pytest.mark.parametrize("field", ["cn", "bn"])
+def test_best_readout_is_the_first_lowest_objective_on_the_trajectory(field):
+    """readout = "best": the configuration returned is, per trial, the first of
+    H(c_1) .. H(c_S) of lowest objective.  Checked against the recorded trajectory of
+    the same run, each configuration scored with objective() from A and y."""
+    inst = cs_inputs.random_instance(30, 18, 4, 0.05, 0.03, seed=6)
+    G, hz, g = oracle.gram(inst.A, inst.y)
+    Goff = G - np.diag(g)
+    T, S = 3, 300
+    R = np.repeat((hz / g)[:, None], T, axis=1)
+    eta = math.sqrt(2 * inst.lam)
+    base = Params(n_steps=S, dt=0.02, field=field, seed=2)
+    _, _, _, rc, _ = oracle.cim_run(Goff, hz, R, eta, base, outer=0, record_steps=S, g=g)
+    best = oracle.cim_run(Goff, hz, R, eta, dataclasses.replace(base, readout="best"), outer=0, g=g)[0]
+    yy = 0.5 * float(inst.y @ inst.y)
+    for t in range(T):
+        E = []
+        for n in range(S):
+            s = (rc[n][:, t] > 0).astype(np.uint8)
+            E.append(oracle.objective(inst.A, inst.y, s * R[:, t], s, inst.lam) - yy)
+        n_star = int(np.argmin(E))
+        np.testing.assert_array_equal(best[:, t], (rc[n_star][:, t] > 0).astype(np.uint8))
+        # and the readout energy is the objective less 1/2 y^T y
+        s = best[:, t:t + 1]
+        assert oracle.readout_energy(Goff, g, hz, R[:, t:t + 1], s, inst.lam)[0] == pytest.approx(E[n_star],
+                                                                                                 abs=1e-12)
 
 
 def test_noise_free_exact_recovery():

@@ -349,3 +349,72 @@ def test_error_against_fp64_is_reported_per_result(precision, refit):
         assert g["stats"][12] <= 1e-12 and e12 <= 1e-12
     else:
         assert g["stats"][12] == pytest.approx(e12, rel=1e-6)
+
+
+# ------------------------------------------------------------------ f4: corrected self-term, best readout
+ORACLE_KEYS_F4 = ORACLE_KEYS | {"self_term", "readout"}
+
+
+def oracle_params_f4(w):
+    return oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS_F4})
+
+
+@pytest.mark.parametrize("precision,field", [("fp64", "cn"), ("fp64", "bn"), ("fp32", "cn")])
+def test_corrected_self_term_matches_oracle(precision, field):
+    """self_term = 1: the injection restores the self-term (the single-spin decision of
+    Eq. doublel0); whole solves against the oracle in the same mode."""
+    inst = cs_inputs.random_instance(250, 150, 25, 0.01, 0.03, seed=23)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=700, precision=precision, field=field,
+             self_term=True, seed=6)
+    g = gpu_solve(inst, w, 4)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params_f4(w), trials=4)
+    _compare_solve(g, r, inst, 4, 1e-9 if precision == "fp64" else 1e-5, precision == "fp64")
+    # a different dynamics than the paper-literal mode on this instance
+    plain = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=4)
+    assert not np.array_equal(plain["sigmas"], r["sigmas"])
+
+
+def test_corrected_self_term_in_a_batch():
+    """The batched kernel folds the same correction into its prologue."""
+    from test_batch_gpu import run_batch
+    insts = [cs_inputs.random_instance(N, int(0.6 * N), N // 10, 0.01, 0.03, seed=40 + N) for N in (120, 77, 200)]
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=500, precision="fp64", self_term=True)
+    out = run_batch(insts, w, 2)
+    for i, (inst, res) in enumerate(zip(insts, out)):
+        r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params_f4(w), trials=2, inst=i)
+        np.testing.assert_array_equal(res["sigmas"], r["sigmas"])
+        np.testing.assert_allclose(res["x_hat"], r["x_hat"], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision,form,cluster", [("fp64", 0, 0), ("fp64", 0, 2), ("fp32", 1, 0), ("fp32", 4, 0)])
+def test_best_readout_matches_oracle(precision, form, cluster):
+    """readout = best (binarised field): each CIM run returns the first configuration
+    of lowest objective among those it visited.  FP64 (two cluster shapes) and FP32
+    (FMAs, tcgen05) against the oracle: supports and R per trial."""
+    inst = cs_inputs.random_instance(240, 140, 24, 0.01, 0.03, seed=29)
+    T = 16 if form == 4 else 4
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=600, precision=precision, field="bn",
+             readout="best", seed=8, tensor_form=form, cluster_size=cluster)
+    g = gpu_solve(inst, w, T)
+    if form == 4:
+        assert g["stats"][10] == 5
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params_f4(w), trials=T)
+    _compare_solve(g, r, inst, T, 1e-9 if precision == "fp64" else 1e-5, precision == "fp64")
+    final = oracle.solve(inst.A, inst.y, inst.lam, oracle_params_f4(dict(w, readout="final")), trials=T)
+    assert r["energy"] <= final["energy"] + 1e-12
+
+
+def test_best_readout_argument_checks():
+    """The best readout needs the binarised field and a single solve."""
+    inst = cs_inputs.random_instance(64, 40, 6, 0.0, 0.05, seed=1)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=10, readout="best")
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        with pytest.raises(cs.CSError) as ei:
+            cs.cs_solve(h, cs.params_from_workload(w, field="cn"), 2)
+        assert ei.value.status == cs.CS_EINVAL
+        with pytest.raises(cs.CSError) as ei:
+            cs.cs_solve_batch([h], cs.params_from_workload(w, field="bn"), 2)
+        assert ei.value.status == cs.CS_EINVAL
+    finally:
+        cs.cs_problem_destroy(h)
