@@ -20,7 +20,10 @@ Two further workloads print their own line (not the default):
   --workload serve_mix           a Poisson stream (200 requests/s) of 40 requests
       mixing the single FP64 N=200 shape, the 64-trial N=2000 shape and the
       uneven BF16 shape 60/30/10, through the continuous-batching server, against
-      the same requests as plain FP32 solves one at a time; p50/p99 latency.
+      the same requests as plain FP32 solves one at a time; p50/p99 latency;
+  --workload sweep_random        the paper's random-data experiment: final RMSE
+      against sparsity for alpha in {0.6, 0.8} and two noise levels, and the
+      RMSE and Hamming loss after every outer iteration, both local fields.
 """
 from __future__ import annotations
 
@@ -487,6 +490,75 @@ def run_serve(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def run_sweep(args):
+    """The paper's random-data experiment (its RMSE-against-sparsity figure and its
+    per-iteration RMSE and Hamming-loss figure), on synthetic data of the same
+    shape: N = 2000, alpha in {0.6, 0.8}, (nu, eta_end) in {(0.05, 0.18),
+    (0.1, 0.35)}, a in {0.1, 0.2, 0.3, 0.4}, both local fields, `--sweep-datasets`
+    random datasets per point, one trial each, the paper's schedules (workload
+    paper_random_n2000: sigmoid pump, eta from 0.8 over 52 outer iterations,
+    damped Jacobi CDP), FP32.  Prints one JSON line: reconstructions/s over the
+    whole sweep, the final RMSE per point, and the mean RMSE and Hamming loss
+    after every outer iteration at alpha = 0.6, a = 0.2, nu = 0.05."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2405_00366_gb300 import build, cs
+
+    if not os.path.exists(cs.LIB_PATH):
+        build.build()
+    torch.cuda.set_device(0)
+    base = cs_inputs.WORKLOADS["paper_random_n2000"]
+    N, n_outer = base["N"], base["n_outer"]
+    alphas, noise, avals = [0.6, 0.8], [(0.05, 0.18), (0.1, 0.35)], [0.1, 0.2, 0.3, 0.4]
+    fields = ["cn", "bn"]
+    final, curves = {}, {}
+    solves, t_gpu = 0, 0.0
+    stream = torch.cuda.Stream()
+    for field in fields:
+        for alpha in alphas:
+            for nu, eta_end in noise:
+                for a in avals:
+                    rm, hm = [], []
+                    for ds in range(args.sweep_datasets):
+                        lam = eta_end ** 2 / 2
+                        inst = cs_inputs.random_instance(N, int(alpha * N), int(a * N), nu, lam,
+                                                         seed=7919 * ds + int(1000 * a) + int(100 * alpha))
+                        w = dict(base, field=field, eta_end=eta_end, lam=lam)
+                        prm = cs.params_from_workload(w, record_outer=1)
+                        A_d = torch.from_numpy(inst.A).cuda()
+                        y_d = torch.from_numpy(inst.y).cuda()
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        h = cs.cs_problem_create(A_d, y_d, lam, stream=stream)
+                        cs.cs_solve(h, prm, 1)
+                        cs.cs_result(h)
+                        t_gpu += time.perf_counter() - t0
+                        solves += 1
+                        sig, R = cs.cs_outer_history(h, n_outer, N, 1)
+                        cs.cs_problem_destroy(h)
+                        rm.append([oracle.rmse(sig[i, :, 0] * R[i, :, 0], inst.x0) for i in range(n_outer)])
+                        hm.append([oracle.hamming_loss(sig[i, :, 0], inst.xi) for i in range(n_outer)])
+                    key = f"{field}/alpha={alpha}/nu={nu}/a={a}"
+                    final[key] = {"rmse": float(np.mean([r[-1] for r in rm])),
+                                  "hamming": float(np.mean([h[-1] for h in hm]))}
+                    if alpha == 0.6 and nu == 0.05 and a == 0.2:
+                        curves[field] = {"rmse": np.mean(rm, axis=0).tolist(), "hamming": np.mean(hm, axis=0).tolist()}
+    line = {
+        "metric": METRIC, "value": solves / t_gpu, "unit": "reconstructions/s", "n_gpus": 1, "steps": solves,
+        "warmup": 0, "ms_per_step": 1e3 * t_gpu / solves, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sweep_random", "N": N, "alphas": alphas, "nu_eta_end": noise, "a": avals,
+                   "fields": fields, "datasets_per_point": args.sweep_datasets, "trials": 1, "n_outer": n_outer,
+                   "n_steps": base["n_steps"], "dt": base["dt"], "pump": "sigmoid d=0.4", "refit": "jacobi 0.1 x 100",
+                   "timing": "host clock around create + solve + result of each solve"},
+        "sweep": {"final": final, "per_iteration_alpha0.6_a0.2_nu0.05": curves},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,7 +573,9 @@ def main():
                     help="override the workload's outer iterations (short runs for profiling only)")
     ap.add_argument("--n-steps", type=int, default=None,
                     help="override the workload's Euler steps per run (short runs for profiling only)")
-    ap.add_argument("--workload", choices=SINGLE_WORKLOADS + ["batch_uneven_bf16", "serve_mix"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=SINGLE_WORKLOADS + ["batch_uneven_bf16", "serve_mix", "sweep_random"],
+                    default=WORKLOAD)
+    ap.add_argument("--sweep-datasets", type=int, default=2, help="random datasets per point of the sweep workload")
     ap.add_argument("--batch-instances", type=int, default=None,
                     help="instances of the batched workload (smaller batches for profiling only)")
     args = ap.parse_args()
@@ -517,6 +591,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve_mix":
         return run_serve(args)
+    if args.workload == "sweep_random":
+        return run_sweep(args)
 
     import numpy as np
     import torch

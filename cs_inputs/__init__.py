@@ -119,6 +119,18 @@ WORKLOADS = {
     "mri_n16384_fp16": dict(
         mri_side=128, N=16384, M=4915, nnz=1638, nu=0.0, lam=0.1, seed=0, trials=8,
         n_outer=40, n_steps=3000, precision="fp16", **dict(_COMMON, K=0.1)),
+    # the paper's random-data experiments (Numerical experiments): N = 2000,
+    # alpha = 0.6, a = 0.2, nu = 0.05; sigmoid pump (Eq. pumprateGACS, p_thr = 1,
+    # d = 0.4), dt = 0.02 up to 20 photon lifetimes, eta from 0.8 down to
+    # eta_end = 0.18 (0.35 for nu = 0.1) with velo = 51, i.e. 52 outer
+    # iterations (Eq. etaSchedulling), damped Jacobi CDP (0.1, 100 sweeps),
+    # N(0, 1e-4) initial amplitudes, K = 1; the objective's lambda eta_end^2 / 2
+    "paper_random_n2000": dict(
+        N=2000, M=1200, nnz=400, nu=0.05, lam=0.18 ** 2 / 2, seed=0, trials=1,
+        n_outer=52, n_steps=1000, precision="fp32",
+        **dict(_COMMON, dt=0.02, pump_kind="sigmoid", p_thr=1.0, d=0.4, t0=4.0, width=2.0, eta_init=0.8,
+               eta_end=0.18, velo=51.0, init_kind="normal", init_scale=0.01, refit="jacobi", jacobi_dt=0.1,
+               jacobi_iters=100)),
 }
 
 

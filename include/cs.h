@@ -46,7 +46,8 @@ typedef enum {
 } cs_status;
 
 enum { CS_FIELD_CN = 0, CS_FIELD_BN = 1 };          /* Eq. localfieldMFZ / Eq. localfieldMFZBN */
-enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1 };   /* normal equations / damped Jacobi */
+enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1, CS_REFIT_CG = 2 }; /* normal equations / damped Jacobi /
+                                                                       conjugate gradient */
 enum { CS_PUMP_LINEAR = 0, CS_PUMP_SIGMOID = 1 };   /* p0 -> p1 ramp / Eq. pumprateGACS */
 enum { CS_INIT_UNIFORM = 0, CS_INIT_NORMAL = 1 };   /* U(-s, s) / N(0, s^2) */
 enum { CS_READOUT_FINAL = 0, CS_READOUT_BEST = 1 }; /* sigma of a CIM run: last / best visited */
@@ -119,13 +120,21 @@ typedef struct {
                            (its product is the configuration's coupling term) and single solves;
                            each run then keeps a history of (n_steps + 1) x N x trials bytes and
                            (n_steps + 1) x CTAs x trials doubles on the device */
+  int32_t cg_iters;     /* CS_REFIT_CG (the paper's CDP for MRI data): conjugate gradient on
+                           G_SS R_S = (A^T y)_S in FP64, warm started from the trial's R, at most
+                           cg_iters iterations (paper: 10000) ... */
+  double cg_tol;        /* ... and until ||(A^T y)_S - G_SS R_S||_2 <= cg_tol ||(A^T y)_S||_2; off
+                           the support R is the Jacobi fixed point, as for the exact refit */
+  int32_t record_outer; /* 1: keep sigma and R after every outer iteration (single solves; read
+                           with cs_outer_history): n_outer x N x trials bytes and doubles */
 } cs_params;
 
 typedef struct cs_problem cs_problem;
 
 /* Defaults: 20 x 1000 steps, dt 0.01, linear pump 0 -> 1.5, beta 0.2, tau 1,
  * K = j = 1, fixed eta, U(-0.01, 0.01) initial amplitudes, continuous field,
- * exact refit, FP32, seed 0, no recording, 10 s timeout. */
+ * exact refit (damped Jacobi: step 0.1, 100 sweeps; conjugate gradient: 10000
+ * iterations, tolerance 1e-10), FP32, seed 0, no recording, 10 s timeout. */
 void cs_params_default(cs_params* p);
 
 /* Create a problem from A (M x N, row-major, float64) and y (M, float64) and
@@ -203,6 +212,12 @@ cs_status cs_result_trials(cs_problem* p, double* R, uint8_t* sigma, double* ene
  * params.record_steps Euler steps of outer iteration 0, as doubles laid out
  * [step][r][t] (record_steps x N x trials).  Host pointers. */
 cs_status cs_trajectory(cs_problem* p, double* c, double* e);
+
+/* sigma and R of every trial after each outer iteration of the last solve
+ * (params.record_outer = 1), laid out [outer][r][t]: n_outer x N x trials bytes
+ * and doubles.  Host pointers, either may be NULL.  CS_EINVAL if the solve did
+ * not record them. */
+cs_status cs_outer_history(cs_problem* p, uint8_t* sigma, double* R);
 
 /* Copy the FP64 Gram data formed by cs_problem_create to host buffers
  * (any may be NULL): G (N x N), h^z = A^T y (N), g = diag G (N). */

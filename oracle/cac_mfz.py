@@ -49,7 +49,8 @@ the moments of the initial-amplitude distributions, the pump and eta
 schedules at closed-form points, the Gram matrix by brute force, the
 recomputed objective, the zero gradient of the exact refit, the ridge on a
 singular support, the damped Jacobi refit (two sweeps worked by hand, and its
-convergence to the exact refit), the corrected self-term (hand-worked step,
+convergence to the exact refit), the conjugate-gradient refit (two iterations
+worked by hand, convergence to the exact refit), the corrected self-term (hand-worked step,
 separable case, brute force against Eq. doublel0) and the best-configuration
 readout (against the recorded trajectory scored by objective());
 tests/test_oracle_mutations.py plants mistakes in it and checks that a pin
@@ -67,7 +68,7 @@ import scipy.linalg
 __all__ = [
     "Params", "splitmix64_mix", "counter_uniform", "initial_amplitudes", "gram",
     "coupling_J", "pump", "eta_at", "local_field_cn", "local_field_bn", "injection",
-    "euler_step", "self_term_correction", "readout_energy", "cim_run", "refit_exact", "refit_jacobi",
+    "euler_step", "self_term_correction", "readout_energy", "cim_run", "refit_exact", "refit_jacobi", "refit_cg",
     "objective", "rmse",
     "hamming_loss", "solve",
 ]
@@ -104,9 +105,11 @@ class Params:
     init_kind: str = "uniform"   # "uniform": U(-s, s); "normal": N(0, s^2)
     init_scale: float = 0.01
     field: str = "cn"            # "cn" continuous (Eq. localfieldMFZ), "bn" binarised
-    refit: str = "exact"         # "exact" normal equations, "jacobi" damped Jacobi
+    refit: str = "exact"         # "exact" normal equations, "jacobi" damped Jacobi, "cg" conjugate gradient
     jacobi_dt: float = 0.1
     jacobi_iters: int = 100
+    cg_iters: int = 10000        # conjugate-gradient refit: at most this many iterations (paper: 10000)
+    cg_tol: float = 1e-10        # and until ||h^z_S - G_SS R_S||_2 <= cg_tol ||h^z_S||_2
     seed: int = 0
     self_term: bool = False      # corrected mode: the injection also subtracts (sqrt tau / 4) G_rr R_r^2
     readout: str = "final"       # "final": H(c) at the end of each run; "best": the best configuration visited
@@ -359,6 +362,41 @@ def refit_jacobi(Goff, hz, g, sigma, R, dtc, iters):
     return R
 
 
+def refit_cg(G, hz, g, sigma, R, iters, tol):
+    """CDP by conjugate gradient (paper, MRI data): the normal equations of the
+    support, G_SS R_S = (A^T y)_S, by conjugate gradient warm started from the
+    trial's R_S, at most `iters` iterations and until the residual is at most
+    tol ||(A^T y)_S||; off the support R_r is the Jacobi fixed point, as for the
+    exact refit."""
+    S = np.flatnonzero(sigma)
+    R = np.array(R, dtype=np.float64, copy=True)
+    if S.size == 0:
+        return hz / g
+    Gss = G[np.ix_(S, S)]
+    b = hz[S]
+    x = R[S].copy()
+    r = b - Gss @ x
+    p = r.copy()
+    rr = float(r @ r)
+    bnorm = math.sqrt(float(b @ b))
+    for _ in range(iters):
+        if math.sqrt(rr) <= tol * bnorm:
+            break
+        q = Gss @ p
+        alpha = rr / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(r @ r)
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+    R[S] = x
+    off = np.ones(hz.size, dtype=bool)
+    off[S] = False
+    R[off] = (hz[off] - G[np.ix_(off, S)] @ x) / g[off]
+    return R
+
+
 # ---------------------------------------------------------------- metrics
 def objective(A, y, x_hat, sigma, lam):
     """Eq. doublel0 at (R, sigma): 1/2 ||y - A x_hat||^2 + lambda |sigma|, x_hat = sigma o R."""
@@ -384,9 +422,10 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
     """Alternating minimisation (Algorithm 1) for `trials` independent trials.
 
     Returns a dict with the kept (lowest-energy) trial's x_hat, sigma, energy and
-    index, every trial's R, sigma and energy, per-outer support sizes, a flag
-    for ridge use and, with record_steps, the first steps' (c, e) of outer
-    iteration 0.  max_steps truncates every CIM run (bounded samples only).
+    index, every trial's R, sigma and energy, per-outer support sizes, every
+    trial's sigma and R after each outer iteration (sigma_outer, R_outer:
+    n_outer x N x T), a flag for ridge use and, with record_steps, the first
+    steps' (c, e) of outer iteration 0.  max_steps truncates every CIM run (bounded samples only).
     """
     A = np.asarray(A, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -400,6 +439,7 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
     sigma = np.zeros((N, trials), dtype=np.uint8)
     singular = False
     support_sizes = []
+    sigma_outer, R_outer = [], []
     rec = None
     for i in range(prm.n_outer):
         eta = eta_at(i, prm, lam)
@@ -412,10 +452,14 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
             if prm.refit == "exact":
                 R[:, t], sing = refit_exact(G, hz, g, sigma[:, t])
                 singular |= sing
+            elif prm.refit == "cg":
+                R[:, t] = refit_cg(G, hz, g, sigma[:, t], R[:, t], prm.cg_iters, prm.cg_tol)
             else:
                 R[:, t] = refit_jacobi(Goff, hz, g, sigma[:, t], R[:, t],
                                        prm.jacobi_dt, prm.jacobi_iters)
         support_sizes.append(sigma.sum(axis=0).astype(np.int64))
+        sigma_outer.append(sigma.copy())
+        R_outer.append(R.copy())
     x_hats = sigma * R
     energies = np.array([objective(A, y, x_hats[:, t], sigma[:, t], lam) for t in range(trials)])
     best = int(np.argmin(energies))  # first index among equal minima
@@ -423,5 +467,6 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
         x_hat=x_hats[:, best].copy(), sigma=sigma[:, best].copy(), energy=float(energies[best]),
         best_trial=best, energies=energies, R=R, sigmas=sigma,
         support_sizes=np.array(support_sizes), singular=singular,
+        sigma_outer=np.array(sigma_outer), R_outer=np.array(R_outer),
         trajectory=rec, G=G, hz=hz, g=g,
     )

@@ -21,7 +21,7 @@ CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTREADY, CS_ESINGULAR =
 STATUS_NAMES = {0: "CS_OK", 1: "CS_EINVAL", 2: "CS_ENOMEM", 3: "CS_ECUDA", 4: "CS_ETIMEOUT",
                 5: "CS_ENOTREADY", 6: "CS_ESINGULAR"}
 CS_FIELD_CN, CS_FIELD_BN = 0, 1
-CS_REFIT_EXACT, CS_REFIT_JACOBI = 0, 1
+CS_REFIT_EXACT, CS_REFIT_JACOBI, CS_REFIT_CG = 0, 1, 2
 CS_PUMP_LINEAR, CS_PUMP_SIGMOID = 0, 1
 CS_INIT_UNIFORM, CS_INIT_NORMAL = 0, 1
 CS_P_FP64, CS_P_FP32, CS_P_BF16, CS_P_FP16, CS_P_FP8 = 0, 1, 2, 3, 4
@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": CS_P_FP64, "fp32": CS_P_FP32, "bf16": CS_P_BF16, "fp16": C
 FIELDS = {"cn": CS_FIELD_CN, "bn": CS_FIELD_BN}
 PUMPS = {"linear": CS_PUMP_LINEAR, "sigmoid": CS_PUMP_SIGMOID}
 INITS = {"uniform": CS_INIT_UNIFORM, "normal": CS_INIT_NORMAL}
-REFITS = {"exact": CS_REFIT_EXACT, "jacobi": CS_REFIT_JACOBI}
+REFITS = {"exact": CS_REFIT_EXACT, "jacobi": CS_REFIT_JACOBI, "cg": CS_REFIT_CG}
 CS_READOUT_FINAL, CS_READOUT_BEST = 0, 1
 READOUTS = {"final": CS_READOUT_FINAL, "best": CS_READOUT_BEST}
 
@@ -52,6 +52,7 @@ class cs_params(ctypes.Structure):
         ("test_phantom_ctas", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
         ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32), ("tensor_form", ctypes.c_int32),
         ("self_term", ctypes.c_int32), ("readout", ctypes.c_int32),
+        ("cg_iters", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("record_outer", ctypes.c_int32),
     ]
 
 
@@ -83,6 +84,7 @@ def lib():
         L.cs_result_trials.argtypes = [P, P, P, P, P]
         L.cs_trajectory.argtypes = [P, P, P]
         L.cs_problem_gram.argtypes = [P, P, P, P]
+        L.cs_outer_history.argtypes = [P, P, P]
         L.cs_problem_timing.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
         L.cs_objective_static.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_double, P, P]
@@ -102,6 +104,7 @@ def lib():
         L.cs_last_error.argtypes = []
         L.cs_last_error.restype = ctypes.c_char_p
         for name in ["cs_problem_create", "cs_solve", "cs_solve_batch", "cs_result", "cs_result_trials", "cs_trajectory",
+                     "cs_outer_history",
                      "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static",
                      "cs_server_create", "cs_server_submit", "cs_server_submit_host", "cs_server_poll",
                      "cs_server_wait", "cs_server_result"]:
@@ -306,6 +309,15 @@ def cs_server_result(server, ticket: int, N: int):
 def cs_server_destroy(server) -> None:
     if server:
         lib().cs_server_destroy(server)
+
+
+def cs_outer_history(problem, n_outer: int, N: int, trials: int):
+    """(sigma, R) after each outer iteration of the last solve (record_outer = 1):
+    arrays of shape (n_outer, N, trials), uint8 and float64."""
+    s = np.empty((n_outer, N, trials), dtype=np.uint8)
+    R = np.empty((n_outer, N, trials))
+    _check(lib().cs_outer_history(problem, s.ctypes.data, R.ctypes.data), allow=(CS_OK, CS_ESINGULAR))
+    return s, R
 
 
 def cs_problem_shape(problem):

@@ -77,7 +77,8 @@ cudaError_t alloc(T** p, size_t elems) {
 
 void free_solve(SolveDev& S, cudaStream_t st) {
   void* ptrs[] = {S.R, S.X0, S.X1, S.state, S.lead, S.job, S.sigma, S.energy, S.ssize, S.sidx, S.work, S.rec_c,
-                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular, S.err4, S.e_hist, S.s_hist};
+                  S.rec_e, S.x_hat, S.sigma_hat, S.stats, S.bar, S.err, S.singular, S.err4, S.e_hist, S.s_hist,
+                  S.sig_outer, S.R_outer};
   for (void* q : ptrs) dev_free(q, st);
   S = SolveDev();
 }
@@ -95,6 +96,7 @@ size_t compute_bytes(int precision) { return precision == CS_P_FP64 ? 8 : 4; }
 cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int trials, bool pool = true) {
   const int rec = prm.record_steps > 0 ? std::min(prm.record_steps, prm.n_steps) : 0;
   const bool fits = S.R && trials <= S.cap_trials && prm.n_outer <= S.cap_outer && rec <= S.cap_record &&
+                    (prm.record_outer == 0 || S.sig_outer) &&
                     compute_bytes(prm.precision) <= compute_bytes(S.cap_prec < 0 ? 0 : S.cap_prec) &&
                     (!pool || S.work);
   if (!fits) {
@@ -117,8 +119,12 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     CS_CUDA(dev_alloc(&S.state, 3 * N * T * cb, P.stream), "cudaMalloc state");
     if (pool) {
       S.work_blocks = (int)std::min<size_t>(T, (size_t)P.num_sms);
-      S.work_stride = N * N + 2 * N;
+      S.work_stride = N * N + 4 * N;  // the refit's matrix and four vectors
       CS_CUDA(alloc(&S.work, (size_t)S.work_blocks * S.work_stride), "cudaMalloc refit workspace");
+    }
+    if (prm.record_outer) {
+      CS_CUDA(alloc(&S.sig_outer, (size_t)prm.n_outer * N * T), "cudaMalloc outer supports");
+      CS_CUDA(alloc(&S.R_outer, (size_t)prm.n_outer * N * T), "cudaMalloc outer signals");
     }
     CS_CUDA(alloc(&S.rec_c, (size_t)rec * N * T), "cudaMalloc rec_c");
     CS_CUDA(alloc(&S.rec_e, (size_t)rec * N * T), "cudaMalloc rec_e");
@@ -169,12 +175,16 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->pump_kind == CS_PUMP_SIGMOID && !(p->width > 0.0)) return fail(CS_EINVAL, "sigmoid width must be > 0");
   if (p->init_kind != CS_INIT_UNIFORM && p->init_kind != CS_INIT_NORMAL) return fail(CS_EINVAL, "bad init_kind");
   if (p->field != CS_FIELD_CN && p->field != CS_FIELD_BN) return fail(CS_EINVAL, "bad field");
-  if (p->refit != CS_REFIT_EXACT && p->refit != CS_REFIT_JACOBI) return fail(CS_EINVAL, "bad refit");
+  if (p->refit != CS_REFIT_EXACT && p->refit != CS_REFIT_JACOBI && p->refit != CS_REFIT_CG)
+    return fail(CS_EINVAL, "bad refit");
+  if (p->refit == CS_REFIT_CG && (p->cg_iters < 1 || !(p->cg_tol >= 0.0) || !std::isfinite(p->cg_tol)))
+    return fail(CS_EINVAL, "the conjugate-gradient refit needs cg_iters >= 1 and cg_tol >= 0");
   if (p->refit == CS_REFIT_JACOBI && (!(p->jacobi_dt > 0.0) || !std::isfinite(p->jacobi_dt) || p->jacobi_iters < 1))
     return fail(CS_EINVAL, "the damped Jacobi refit needs jacobi_dt > 0 and jacobi_iters >= 1");
   if (p->precision < CS_P_FP64 || p->precision > CS_P_FP8) return fail(CS_EINVAL, "bad precision");
   if (p->eta_init > 0.0 && !(p->velo > 0.0)) return fail(CS_EINVAL, "velo must be > 0 with an eta schedule");
   if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
+  if (p->record_outer != 0 && p->record_outer != 1) return fail(CS_EINVAL, "record_outer must be 0 or 1");
   if (p->timeout_ms <= 0) return fail(CS_EINVAL, "timeout_ms must be > 0");
   if (p->test_phantom_ctas < 0 || p->test_phantom_ctas > 1024) return fail(CS_EINVAL, "bad test_phantom_ctas");
   if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
@@ -255,6 +265,8 @@ RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) 
   J.refit = prm.refit;
   J.jacobi_iters = prm.jacobi_iters;
   J.jacobi_dt = prm.jacobi_dt;
+  J.cg_iters = prm.cg_iters;
+  J.cg_tol = prm.cg_tol;
   J.precision = prm.precision;
   J.gscale = prm.precision == CS_P_FP8 ? P.gscale : nullptr;
   return J;
@@ -318,6 +330,8 @@ void cs_params_default(cs_params* p) {
   p->refit = CS_REFIT_EXACT;
   p->jacobi_dt = 0.1;
   p->jacobi_iters = 100;
+  p->cg_iters = 10000;
+  p->cg_tol = 1e-10;
   p->precision = CS_P_FP32;
   p->seed = 0;
   p->instance = 0;
@@ -416,7 +430,18 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     }
     CS_CUDA(mark(p, TM_EULER, false), "event");
     CS_CUDA(mark(p, TM_REFIT, true), "event");
-    CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream), "refit launch");
+    const RefitPlan rplan{prm->refit, prm->jacobi_iters, (int)P.N, P.num_sms, S.R};
+    CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream, &rplan),
+            "refit launch");
+    if (refit_grid_wide(&rplan, 1, S.trials, S.work_blocks, S.work_stride)) P.launches += prm->jacobi_iters - 1;
+    if (prm->record_outer) {
+      const size_t nt = (size_t)P.N * S.trials;
+      CS_CUDA(cudaMemcpyAsync(S.sig_outer + (size_t)i * nt, S.sigma, nt, cudaMemcpyDeviceToDevice, P.stream),
+              "record outer support");
+      CS_CUDA(cudaMemcpyAsync(S.R_outer + (size_t)i * nt, S.R, nt * sizeof(double), cudaMemcpyDeviceToDevice,
+                              P.stream),
+              "record outer signal");
+    }
     CS_CUDA(mark(p, TM_REFIT, false), "event");
     P.launches += 2;
   }
@@ -424,6 +449,7 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream, S.err4), "finish launch");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
   P.launches += 4;  // energy, selection, error against FP64 and its ratio
+  S.has_outer = prm->record_outer != 0;
   S.done = true;
   return CS_OK;
 }
@@ -435,7 +461,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     cs_status st = check_params(prms[i], trials[i]);
     if (st != CS_OK) return st;
     if (trials[i] > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials per problem");
-    if (prms[i]->record_steps != 0) return fail(CS_EINVAL, "a batched solve does not record trajectories");
+    if (prms[i]->record_steps != 0 || prms[i]->record_outer != 0)
+      return fail(CS_EINVAL, "a batched solve does not record trajectories or outer histories");
     if (prms[i]->tensor_form == 4) return fail(CS_EINVAL, "tensor_form = 4: the batched kernel has no tcgen05 form");
     if (prms[i]->readout != CS_READOUT_FINAL)
       return fail(CS_EINVAL, "a batched solve reads out the final configuration only (readout = CS_READOUT_FINAL)");
@@ -530,7 +557,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
       jobs.back().err = d_err;
     }
   }
-  const size_t stride = (size_t)nmax * nmax + 2 * (size_t)nmax;
+  const size_t stride = (size_t)nmax * nmax + 4 * (size_t)nmax;
   int pool_blocks = std::min(refit_items_max, P0.num_sms);
   while (pool_blocks > 1 && (double)pool_blocks * stride * 8.0 > 16e9) --pool_blocks;
   CS_CUDA(dev_alloc(&d_insts, std::max<size_t>(hinst.size(), 1), stream), "cudaMalloc batch descriptors");
@@ -625,6 +652,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   for (size_t g = 0; g < groups.size(); ++g)
     for (int i : groups[g].idx) {
       ps[i]->S.done = true;
+      ps[i]->S.has_outer = false;
       ps[i]->S.plan_cluster = 0;
       ps[i]->S.plan_ctas = std::min((int)groups[g].idx.size(), P0.num_sms);
       ps[i]->S.plan_form = groups[g].btc ? 4 : 3;
@@ -681,6 +709,16 @@ cs_status cs_trajectory(cs_problem* p, double* c, double* e) {
   const size_t n = (size_t)p->S.record_steps * p->P.N * p->S.trials;
   if (c) CS_CUDA(cudaMemcpy(c, p->S.rec_c, n * sizeof(double), cudaMemcpyDeviceToHost), "copy rec_c");
   if (e) CS_CUDA(cudaMemcpy(e, p->S.rec_e, n * sizeof(double), cudaMemcpyDeviceToHost), "copy rec_e");
+  return s;
+}
+
+cs_status cs_outer_history(cs_problem* p, uint8_t* sigma, double* R) {
+  cs_status s = wait_and_check(p, nullptr);
+  if (s != CS_OK && s != CS_ESINGULAR) return s;
+  if (!p->S.has_outer) return fail(CS_EINVAL, "the last solve did not record its outer iterations (record_outer)");
+  const size_t n = (size_t)p->S.n_outer * p->P.N * p->S.trials;
+  if (sigma) CS_CUDA(cudaMemcpy(sigma, p->S.sig_outer, n, cudaMemcpyDeviceToHost), "copy outer supports");
+  if (R) CS_CUDA(cudaMemcpy(R, p->S.R_outer, n * sizeof(double), cudaMemcpyDeviceToHost), "copy outer signals");
   return s;
 }
 

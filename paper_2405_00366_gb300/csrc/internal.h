@@ -74,6 +74,8 @@ struct RefitJob {
   int refit;             // CS_REFIT_EXACT or CS_REFIT_JACOBI
   int jacobi_iters;      // damped Jacobi sweeps per outer iteration
   double jacobi_dt;      // damped Jacobi step
+  int cg_iters;          // conjugate-gradient refit: most iterations
+  double cg_tol;         // and relative residual
   int precision;         // CS_P_*: storage precision of G_off in the Euler kernels
   const float* gscale;   // FP8 row scales of G_off (NULL unless FP8)
 };
@@ -103,6 +105,9 @@ struct SolveDev {
   int* err = nullptr;           // device error word
   int* singular = nullptr;      // set when a refit used the ridge
   double* err4 = nullptr;       // 4 doubles: scratch of the error against FP64 (launch_finish)
+  uint8_t* sig_outer = nullptr; // record_outer: n_outer x N x T supports after each outer iteration
+  double* R_outer = nullptr;    // and n_outer x N x T signals
+  bool has_outer = false;       // the last solve recorded them
   double* e_hist = nullptr;     // best-configuration readout: (n_steps + 1) x CTAs x T energy partials
   uint8_t* s_hist = nullptr;    // and (n_steps + 1) x N x T configurations
   size_t cap_e_hist = 0, cap_s_hist = 0;
@@ -150,8 +155,18 @@ cudaError_t launch_euler(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
                          double eta, long long timeout_cycles);
 const char* euler_last_call();  // the CUDA call the last failing Euler launch stopped at
 cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
+// What the host knows of a single problem's refit, for launch_refit to pick
+// the grid-wide damped Jacobi (few trials of one problem); NULL: one block per
+// (problem, trial).
+struct RefitPlan {
+  int refit, jacobi_iters, N, num_sms;
+  double* R;  // the problem's R (N x T)
+};
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
-                         int outer, cudaStream_t st);
+                         int outer, cudaStream_t st, const RefitPlan* plan = nullptr);
+// Whether launch_refit takes the grid-wide damped Jacobi (1 + jacobi_iters
+// launches instead of 2).
+bool refit_grid_wide(const RefitPlan* plan, int njobs, int T, int pool_blocks, size_t pool_stride);
 // Objective per trial, kept trial, and the kept result's error against FP64
 // (stats[11], stats[12]); err4 is 4 doubles of scratch per job.
 cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st, double* err4);

@@ -325,7 +325,7 @@ __device__ bool solve_mixed_blocked(const RefitJob& J, const int* idx, int n, do
   return prev <= 1e-12 * rn0;
 }
 
-// Refit of trial t of job J.  W is this block's global workspace (n^2 + 2n
+// Refit of trial t of job J.  W is this block's global workspace (n^2 + 4n
 // doubles); `smem` (smem_bytes) holds the FP32 factor of the mixed-precision
 // path, taken when it fits and succeeds; otherwise the FP64 factorisation.
 __device__ void refit_one(const RefitJob& J, int t, const int* idx, int n, double* W, float* smem,
@@ -421,6 +421,86 @@ __device__ void jacobi_one(const RefitJob& J, int t, const int* idx, int n, doub
   }
 }
 
+// Conjugate-gradient CDP of trial t (the paper's iteration for MRI data) in
+// FP64: G_SS is gathered once into W (row-major, n x n); from x = R_S of the
+// trial, r = h^z_S - G_SS x, p = r, and for at most cg_iters iterations, until
+// ||r|| <= cg_tol ||h^z_S||: q = G_SS p (one warp per row), alpha = r.r / p.q,
+// x += alpha p, r -= alpha q, beta = r'.r' / r.r, p = r + beta p.  Dot products
+// are fixed-order block sums, so the iteration is deterministic.  Then R_S = x
+// and off the support the Jacobi fixed point, as for the exact refit.
+__device__ void cg_one(const RefitJob& J, int t, const int* idx, int n, double* W) {
+  const int N = J.N, T = J.T, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __shared__ double red_s[kRefitThreads / 32];
+  if (n == 0) {
+    for (int r = threadIdx.x; r < N; r += kRefitThreads) J.R[(size_t)r * T + t] = J.hz[r] / J.g[r];
+    __syncthreads();
+    return;
+  }
+  double* Gs = W;
+  double* x = W + (size_t)n * n;
+  double* rv = x + n;
+  double* pv = rv + n;
+  double* qv = pv + n;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += kRefitThreads) {
+    const int i = (int)(e / n), k = (int)(e % n);
+    Gs[e] = J.G[(size_t)idx[i] * N + idx[k]];
+  }
+  for (int i = threadIdx.x; i < n; i += kRefitThreads) x[i] = J.R[(size_t)idx[i] * T + t];
+  __syncthreads();
+  // q = G_SS v, one warp per row, lanes over the columns, shuffle sum
+  auto matvec = [&](const double* v, double* q) {
+    for (int i = w; i < n; i += kRefitThreads / 32) {
+      const double* Gi = Gs + (size_t)i * n;
+      double s = 0.0;
+      for (int k = l; k < n; k += 32) s = fma(Gi[k], v[k], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) q[i] = s;
+    }
+    __syncthreads();
+  };
+  auto dot = [&](const double* a, const double* b) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) s = fma(a[i], b[i], s);
+    return block_sum(s, red_s);
+  };
+  matvec(x, qv);
+  double bb = 0.0;
+  for (int i = threadIdx.x; i < n; i += kRefitThreads) {
+    const double b = J.hz[idx[i]];
+    rv[i] = b - qv[i];
+    pv[i] = rv[i];
+    bb = fma(b, b, bb);
+  }
+  const double bnorm = sqrt(block_sum(bb, red_s));
+  double rr = dot(rv, rv);
+  for (int it = 0; it < J.cg_iters; ++it) {
+    if (!(sqrt(rr) > J.cg_tol * bnorm)) break;
+    matvec(pv, qv);
+    const double alpha = rr / dot(pv, qv);
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) {
+      x[i] = fma(alpha, pv[i], x[i]);
+      rv[i] = fma(-alpha, qv[i], rv[i]);
+    }
+    __syncthreads();
+    const double rr_new = dot(rv, rv);
+    const double beta = rr_new / rr;
+    for (int i = threadIdx.x; i < n; i += kRefitThreads) pv[i] = fma(beta, pv[i], rv[i]);
+    __syncthreads();
+    rr = rr_new;
+  }
+  for (int i = threadIdx.x; i < n; i += kRefitThreads) J.R[(size_t)idx[i] * T + t] = x[i];
+  // off the support: one warp per row r
+  for (int r = w; r < N; r += kRefitThreads / 32) {
+    if (J.sigma[(size_t)r * T + t]) continue;
+    const double* Gr = J.G + (size_t)r * N;
+    double s = 0.0;
+    for (int i = l; i < n; i += 32) s = fma(Gr[idx[i]], x[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) J.R[(size_t)r * T + t] = (J.hz[r] - s) / J.g[r];
+  }
+  __syncthreads();
+}
+
 // Refit of every (job, trial) item whose support is not a copy of an earlier
 // trial's; items are spread over the grid, block b owns workspace b of the pool.
 __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __restrict__ jobs, int T, int items,
@@ -444,6 +524,14 @@ __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __
       __syncthreads();
       continue;
     }
+    if (J.refit == CS_REFIT_CG) {  // warm started from the trial's own R: no sharing
+      if (threadIdx.x == 0) {
+        J.ssize[(size_t)outer * T + t] = n;
+        J.lead[t] = t;
+      }
+      cg_one(J, t, idx, n, pool + (size_t)blockIdx.x * pool_stride);
+      continue;
+    }
     int lead = t;
     for (int u = 0; u < t; ++u)
       if (same_support(J.sigma, J.N, T, t, u)) { lead = u; break; }
@@ -453,6 +541,45 @@ __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __
     }
     if (lead == t) refit_one(J, t, idx, n, pool + (size_t)blockIdx.x * pool_stride, refit_smem, smem_bytes);
     __syncthreads();
+  }
+}
+
+// Support lists of every trial for the grid-wide damped Jacobi refit (one
+// block per trial): sidx, the support size of this outer iteration, no leader.
+__global__ void __launch_bounds__(kRefitThreads) support_kernel(const RefitJob* __restrict__ jobs, int T, int outer) {
+  const RefitJob& J = jobs[0];
+  const int t = blockIdx.x;
+  const int n = support_list(J.sigma, J.N, T, t, J.sidx + (size_t)t * J.N);
+  if (threadIdx.x == 0) {
+    J.ssize[(size_t)outer * T + t] = n;
+    J.lead[t] = t;
+  }
+}
+
+// One damped Jacobi sweep of every trial of one problem over the whole grid:
+// Rb_r = Ra_r + jacobi_dt (R~_r - Ra_r), R~_r = (h^z_r - sum_{r' in S, r' != r}
+// G_rr' Ra_r') / G_rr, one warp per (row, trial), the same arithmetic and
+// summation order as jacobi_one.  Ra and Rb are N x T ([r][t]).
+__global__ void jacobi_sweep_kernel(const RefitJob* __restrict__ jobs, int T, int outer, const double* __restrict__ Ra,
+                                    double* __restrict__ Rb) {
+  const RefitJob& J = jobs[0];
+  const int t = blockIdx.y;
+  const int n = J.ssize[(size_t)outer * T + t];
+  const int* idx = J.sidx + (size_t)t * J.N;
+  const int l = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < J.N; r += gridDim.x * wpb) {
+    const double* Gr = J.G + (size_t)r * J.N;
+    double s = 0.0;
+    for (int i = l; i < n; i += 32) {
+      const int c = idx[i];
+      if (c != r) s = fma(Gr[c], Ra[(size_t)c * T + t], s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) {
+      const double Rr = Ra[(size_t)r * T + t];
+      const double Rt = (J.hz[r] - s) / J.g[r];
+      Rb[(size_t)r * T + t] = Rr + J.jacobi_dt * (Rt - Rr);
+    }
   }
 }
 
@@ -615,9 +742,34 @@ cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, c
   return cudaGetLastError();
 }
 
+bool refit_grid_wide(const RefitPlan* plan, int njobs, int T, int pool_blocks, size_t pool_stride) {
+  return plan && plan->refit == CS_REFIT_JACOBI && njobs == 1 && T * 8 <= plan->num_sms &&
+         (size_t)pool_blocks * pool_stride >= (size_t)plan->N * T;
+}
+
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
-                         int outer, cudaStream_t st) {
+                         int outer, cudaStream_t st, const RefitPlan* plan) {
   const int items = njobs * T;
+  if (refit_grid_wide(plan, njobs, T, pool_blocks, pool_stride)) {
+    // a few trials of one problem: the sweeps spread over the whole GPU, R
+    // alternating between the problem's R and the workspace
+    support_kernel<<<T, kRefitThreads, 0, st>>>(jobs, T, outer);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int wpb = 8;
+    const dim3 grid(std::max(1, std::min((plan->N + wpb - 1) / wpb, 4 * plan->num_sms / T)), T);
+    double* Ra = plan->R;
+    double* Rb = pool;
+    for (int sw = 0; sw < plan->jacobi_iters; ++sw) {
+      jacobi_sweep_kernel<<<grid, 32 * wpb, 0, st>>>(jobs, T, outer, Ra, Rb);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      std::swap(Ra, Rb);
+    }
+    if (Ra != plan->R)
+      return cudaMemcpyAsync(plan->R, Ra, sizeof(double) * plan->N * T, cudaMemcpyDeviceToDevice, st);
+    return cudaSuccess;
+  }
   // shared memory for the FP32 factor of the mixed-precision refit (|S| up to about 310)
   static thread_local size_t smem = 0;
   if (smem == 0) {

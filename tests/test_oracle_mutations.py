@@ -164,3 +164,37 @@ def test_planted_readout_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(om, "readout_energy", _readout_no_diagonal)
     monkeypatch.setattr(oracle, "readout_energy", _readout_no_diagonal)
     assert _fails(pins.test_best_readout_is_the_first_lowest_objective_on_the_trajectory, "bn")
+
+
+def _cg_beta_inverted(G, hz, g, sigma, R, iters, tol):
+    S = np.flatnonzero(sigma)
+    R = np.array(R, dtype=float)
+    Gss, b, x = G[np.ix_(S, S)], hz[S], R[S].copy()
+    r = b - Gss @ x
+    p, rr = r.copy(), float(r @ r)
+    for _ in range(iters):
+        q = Gss @ p
+        a = rr / float(p @ q)
+        x, r = x + a * p, r - a * q
+        rn = float(r @ r)
+        p, rr = r + (rr / rn) * p, rn
+    R[S] = x
+    off = sigma == 0
+    R[off] = (hz[off] - G[np.ix_(off, S)] @ x) / g[off]
+    return R
+
+
+def _cg_cold_start(G, hz, g, sigma, R, iters, tol):
+    return om_refit_cg_orig(G, hz, g, sigma, np.zeros_like(R), iters, tol)
+
+
+om_refit_cg_orig = om.refit_cg
+
+
+@pytest.mark.parametrize("fake", [_cg_beta_inverted, _cg_cold_start])
+def test_planted_cg_mistake_is_caught(monkeypatch, fake):
+    """An inverted beta and a start from zero instead of the trial's R fail the
+    hand-worked two-step pin."""
+    monkeypatch.setattr(om, "refit_cg", fake)
+    monkeypatch.setattr(oracle, "refit_cg", fake)
+    assert _fails(pins.test_cg_refit_two_steps_hand_worked)

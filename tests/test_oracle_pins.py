@@ -198,6 +198,37 @@ def test_damped_jacobi_two_sweeps_hand_worked():
         np.testing.assert_allclose(R, gold[key], rtol=0, atol=1e-15)
 
 
+def test_cg_refit_two_steps_hand_worked():
+    """Conjugate gradient on a 2 x 2 support from the trial's R: the first iterate
+    and the exact second one (tests/golden/cg_two_steps.txt); spin 3 is off the
+    support and takes the Jacobi fixed point."""
+    gold = {k: np.array([float(v) for v in vals]) for k, vals in _read_golden("cg_two_steps.txt").items()}
+    G = np.array([[4.0, 1.0, 0.5], [1.0, 3.0, -1.0], [0.5, -1.0, 2.0]])
+    g = np.diag(G).copy()
+    hz = np.array([1.0, 2.0, 0.25])
+    sigma = np.array([1, 1, 0], dtype=np.uint8)
+    R0 = np.array([2.0, 1.0, 7.0])
+    for iters, key in ((1, "x1"), (2, "x2")):
+        R = oracle.refit_cg(G, hz, g, sigma, R0, iters, 0.0)
+        np.testing.assert_allclose(R[:2], gold[key], rtol=0, atol=1e-15)
+        assert R[2] == pytest.approx((0.25 - 0.5 * R[0] + 1.0 * R[1]) / 2.0, abs=1e-15)
+    # the iteration stops once the residual meets the tolerance: a third step changes nothing
+    R3 = oracle.refit_cg(G, hz, g, sigma, R0, 3, 1e-12)
+    np.testing.assert_allclose(R3[:2], gold["x2"], rtol=0, atol=1e-15)
+
+
+def test_cg_refit_converges_to_exact():
+    inst = cs_inputs.random_instance(150, 90, 15, 0.05, 0.1, seed=8)
+    G, hz, g = oracle.gram(inst.A, inst.y)
+    rng = np.random.default_rng(3)
+    for size in (1, 10, 40, 80):
+        sigma = np.zeros(150, dtype=np.uint8)
+        sigma[rng.choice(150, size, replace=False)] = 1
+        exact, _ = oracle.refit_exact(G, hz, g, sigma)
+        R = oracle.refit_cg(G, hz, g, sigma, hz / g, 10000, 1e-12)
+        np.testing.assert_allclose(R, exact, rtol=0, atol=1e-8 * np.abs(exact).max())
+
+
 def test_jacobi_refit_converges_to_exact():
     inst = cs_inputs.random_instance(100, 70, 10, 0.05, 0.1, seed=8)
     G, hz, g = oracle.gram(inst.A, inst.y)

@@ -418,3 +418,68 @@ def test_best_readout_argument_checks():
         assert ei.value.status == cs.CS_EINVAL
     finally:
         cs.cs_problem_destroy(h)
+
+
+# ------------------------------------------------------------------ f2: conjugate-gradient refit
+@pytest.mark.parametrize("precision,trials", [("fp64", 1), ("fp64", 3), ("fp32", 4)])
+def test_cg_refit_matches_oracle(precision, trials):
+    """refit = cg (the paper's CDP for MRI data): FP64 conjugate gradient on the
+    support's normal equations, warm started from each trial's R, against the oracle:
+    supports identical, R (on and off the support) to 1e-7 relative to max |R|."""
+    inst = cs_inputs.random_instance(300, 180, 30, 0.01, 0.03, seed=19)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=700, precision=precision, refit="cg",
+             cg_iters=10000, cg_tol=1e-10)
+    g = gpu_solve(inst, w, trials)
+    keys = ORACLE_KEYS | {"cg_iters", "cg_tol"}
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle.Params(**{k: v for k, v in w.items() if k in keys}),
+                     trials=trials)
+    np.testing.assert_array_equal(g["support_sizes"], r["support_sizes"])
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_allclose(g["R"], r["R"], rtol=0, atol=1e-7 * np.abs(r["R"]).max())
+    # the refit's FP64 residual is within the tolerance asked for
+    assert g["stats"][12] <= 1e-9
+
+
+def test_cg_refit_mri_shaped():
+    """32 x 32 MRI-shaped problem (orthonormal rows of a subsampled 2-D DCT over Haar
+    coefficients): the conjugate-gradient refit agrees with the oracle's, and with
+    the exact refit's solution (supports identical, x_hat to 1e-7 relative)."""
+    w = cs_inputs.workload("mri_n16384_fp16", mri_side=32, N=1024, M=307, nnz=102, n_outer=3, n_steps=800,
+                           precision="fp32", refit="cg")
+    inst = cs_inputs.workload_instance(w)
+    g = gpu_solve(inst, w, 2)
+    keys = ORACLE_KEYS | {"cg_iters", "cg_tol"}
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle.Params(**{k: v for k, v in w.items() if k in keys}), trials=2)
+    np.testing.assert_array_equal(g["sigmas"], r["sigmas"])
+    np.testing.assert_allclose(g["x_hat"], r["x_hat"], rtol=0, atol=1e-7 * np.abs(r["x_hat"]).max())
+    e = gpu_solve(inst, dict(w, refit="exact"), 2)
+    np.testing.assert_array_equal(g["sigmas"], e["sigmas"])
+    np.testing.assert_allclose(g["x_hat"], e["x_hat"], rtol=0, atol=1e-7 * np.abs(e["x_hat"]).max())
+
+
+# ------------------------------------------------------------------ f1: the paper's random-data schedule
+@pytest.mark.parametrize("field", ["cn", "bn"])
+def test_paper_schedule_outer_history_matches_oracle(field):
+    """The paper's random-data settings (sigmoid pump d = 0.4, dt = 0.02 x 1000,
+    eta schedule from 0.8, damped Jacobi CDP, N(0, 1e-4) amplitudes) scaled to
+    N = 200, twelve outer iterations (velo = 11), FP64: the support and R of every
+    trial after EVERY outer iteration (record_outer, cs_outer_history) equal the
+    oracle's, so per-iteration RMSE and Hamming curves are the oracle's too."""
+    w = cs_inputs.workload("paper_random_n2000", N=200, M=120, nnz=40, n_outer=12, velo=11.0, precision="fp64",
+                           field=field, seed=4)
+    inst = cs_inputs.workload_instance(w)
+    T = 2
+    prm = cs.params_from_workload(w, record_outer=1)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        cs.cs_solve(h, prm, T)
+        cs.cs_result(h)
+        sig_h, R_h = cs.cs_outer_history(h, w["n_outer"], inst.N, T)
+    finally:
+        cs.cs_problem_destroy(h)
+    keys = ORACLE_KEYS | {"jacobi_dt", "jacobi_iters"}
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle.Params(**{k: v for k, v in w.items() if k in keys}), trials=T)
+    np.testing.assert_array_equal(sig_h, r["sigma_outer"])
+    np.testing.assert_allclose(R_h, r["R_outer"], rtol=0, atol=1e-9)
+    ham = [oracle.hamming_loss(sig_h[i, :, 0], inst.xi) for i in range(w["n_outer"])]
+    assert ham[-1] < ham[0]  # the alternation improves the support estimate on this instance
