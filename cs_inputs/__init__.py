@@ -21,6 +21,7 @@ import numpy as np
 __all__ = [
     "Instance",
     "random_instance",
+    "mri_full_instance",
     "uneven_batch",
     "WORKLOADS",
     "workload",
@@ -125,6 +126,17 @@ WORKLOADS = {
     # eta_end = 0.18 (0.35 for nu = 0.1) with velo = 51, i.e. 52 outer
     # iterations (Eq. etaSchedulling), damped Jacobi CDP (0.1, 100 sweeps),
     # N(0, 1e-4) initial amplitudes, K = 1; the objective's lambda eta_end^2 / 2
+    # the paper's MRI problem on a synthetic 128 x 128 image (mri_full_instance):
+    # complex DFT observation (M_obs = 4915 points, compression 0.3), the
+    # gamma = 1e-4 second-difference terms, the LASSO solution as the initial R,
+    # sigmoid pump d = 0.6, fixed eta (eta_init = eta_end), 11 outer iterations
+    # (velo), K = 0.1, the conjugate-gradient CDP; FP16 storage, 8 trials
+    "mri_full_n16384": dict(
+        mri_side=128, mri_gamma=1e-4, N=16384, M_obs=4915, M=2 * 4915 + 2 * 16384, nnz=1638, nu=0.0,
+        lam=0.022 ** 2 / 2, seed=0, trials=8, n_outer=11, n_steps=1000, precision="fp16",
+        **dict(_COMMON, dt=0.02, pump_kind="sigmoid", p_thr=1.0, d=0.6, t0=4.0, width=2.0, eta_init=0.022,
+               eta_end=0.022, velo=11.0, init_kind="normal", init_scale=0.01, K=0.1, refit="cg",
+               init_R="lasso", lasso_lambda=3e-4, lasso_iters=300)),
     "paper_random_n2000": dict(
         N=2000, M=1200, nnz=400, nu=0.05, lam=0.18 ** 2 / 2, seed=0, trials=1,
         n_outer=52, n_steps=1000, precision="fp32",
@@ -143,6 +155,9 @@ def workload(name: str, **overrides):
 
 def workload_instance(w) -> Instance:
     """The seeded instance of a workload dict."""
+    if "mri_gamma" in w:
+        return mri_full_instance(w["mri_side"], w["nnz"] / w["N"], w["M_obs"] / w["N"], w["mri_gamma"], w["lam"],
+                                 w["seed"])
     if "mri_side" in w:
         return mri_instance(w["mri_side"], w["nnz"] / w["N"], w["M"] / w["N"], w["lam"], w["seed"])
     return random_instance(w["N"], w["M"], w["nnz"], w["nu"], w["lam"], w["seed"])
@@ -216,4 +231,58 @@ def mri_instance(n_side: int = 128, sparsity: float = 0.1, alpha: float = 0.3, l
     fu, fv = freq // n, freq % n
     A = np.einsum("mi,mj->mij", B[:, fu].T, B[:, fv].T).reshape(M, N)
     y = A @ x0
+    return Instance(A=np.ascontiguousarray(A), y=y, x0=x0, xi=xi, lam=float(lam))
+
+def second_difference_matrix(n: int) -> np.ndarray:
+    """Second-order difference along one axis of length n with zero padding outside
+    the image: (D v)_i = v_{i-1} - 2 v_i + v_{i+1}, v_{-1} = v_n = 0."""
+    return -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+
+
+def mri_full_instance(n_side: int = 128, sparsity: float = 0.1, alpha: float = 0.3, gamma: float = 1e-4,
+                      lam: float = 0.01, seed: int = 0) -> Instance:
+    """The paper's MRI reconstruction problem (Eq. MRIl0init1 - MRIJMatrix1) on a
+    synthetic image, as one real least-squares system the solver takes unchanged.
+
+    The image x = Haar^T r is sparse in the 2-D Haar domain (a fraction `sparsity`
+    of the N = n^2 coefficients r nonzero, Laplace(0, 1) values).  It is observed
+    through M = round(alpha N) points of its orthonormal complex 2-D DFT, drawn
+    without replacement with density ~ max(0.02, (1 - |f| / (sqrt(2) n / 2))^2)
+    over the wrapped frequencies |f| = |(min(u, n-u), min(v, n-v))|, DC kept:
+    y = S F Haar^T r (noise-free).  The objective 1/2 ||y - S F x||^2
+    + gamma/2 ||Delta_v x||^2 + gamma/2 ||Delta_h x||^2 + lambda ||Haar x||_0 has,
+    over r, the coupling G = Haar F^H S^T S F Haar^T + gamma Haar Delta_v^T Delta_v
+    Haar^T + gamma Haar Delta_h^T Delta_h Haar^T (Eq. MRIJMatrix1; its real part,
+    the image being real) and Zeeman term A^T y; both are the Gram data of
+    A = [Re(S F Haar^T); Im(S F Haar^T); sqrt(gamma) Delta_v Haar^T;
+    sqrt(gamma) Delta_h Haar^T] with y = [Re y; Im y; 0; 0] (2M + 2N rows).
+    Delta_v, Delta_h: second differences along the image's rows and columns,
+    zero padded.  Draw order: support, values, frequencies."""
+    n = n_side
+    N = n * n
+    M = int(round(alpha * N))
+    K = int(round(sparsity * N))
+    rng = np.random.default_rng(seed)
+    xi = np.zeros(N, dtype=np.uint8)
+    xi[rng.choice(N, size=K, replace=False)] = 1
+    x0 = np.zeros(N)
+    x0[xi == 1] = rng.laplace(0.0, 1.0, size=K)
+    u = np.arange(n)
+    wu = np.minimum(u, n - u)
+    rad = np.sqrt(wu[:, None] ** 2 + wu[None, :] ** 2).reshape(N)
+    dens = np.maximum(0.02, (1.0 - rad / (math.sqrt(2.0) * n / 2.0)) ** 2)
+    dens[0] = 0.0
+    dens /= dens.sum()
+    freq = np.concatenate([[0], rng.choice(N, size=M - 1, replace=False, p=dens)])
+    H1 = haar_1d_matrix(n)
+    F1 = np.exp(-2j * math.pi * np.outer(u, u) / n) / math.sqrt(n)
+    B = H1 @ F1.T  # column u = H1 f_u (the DFT basis row f_u through the inverse Haar)
+    fu, fv = freq // n, freq % n
+    Ac = np.einsum("mi,mj->mij", B[:, fu].T, B[:, fv].T).reshape(M, N)
+    D = second_difference_matrix(n)
+    DH = D @ H1.T
+    sg = math.sqrt(gamma)
+    A = np.concatenate([Ac.real, Ac.imag, sg * np.kron(DH, H1.T), sg * np.kron(H1.T, DH)], axis=0)
+    yc = Ac @ x0
+    y = np.concatenate([yc.real, yc.imag, np.zeros(2 * N)])
     return Instance(A=np.ascontiguousarray(A), y=y, x0=x0, xi=xi, lam=float(lam))

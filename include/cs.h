@@ -51,6 +51,7 @@ enum { CS_REFIT_EXACT = 0, CS_REFIT_JACOBI = 1, CS_REFIT_CG = 2 }; /* normal equ
 enum { CS_PUMP_LINEAR = 0, CS_PUMP_SIGMOID = 1 };   /* p0 -> p1 ramp / Eq. pumprateGACS */
 enum { CS_INIT_UNIFORM = 0, CS_INIT_NORMAL = 1 };   /* U(-s, s) / N(0, s^2) */
 enum { CS_READOUT_FINAL = 0, CS_READOUT_BEST = 1 }; /* sigma of a CIM run: last / best visited */
+enum { CS_INIT_R_ZEEMAN = 0, CS_INIT_R_LASSO = 1 }; /* initial R: h^z / diag G / the LASSO solution */
 /* Storage precision of the coupling matrix G and arithmetic of the Euler loop:
  * FP64 keeps G and the amplitudes in double; the others accumulate in float.
  * FP8 is E4M3 with one FP32 scale per row of G_off (its largest magnitude / 448). */
@@ -127,6 +128,13 @@ typedef struct {
                            the support R is the Jacobi fixed point, as for the exact refit */
   int32_t record_outer; /* 1: keep sigma and R after every outer iteration (single solves; read
                            with cs_outer_history): n_outer x N x trials bytes and doubles */
+  int32_t init_R;       /* R before the first CIM run: CS_INIT_R_ZEEMAN, h^z / diag G (the refit of
+                           the empty support); CS_INIT_R_LASSO, the LASSO solution (the paper's
+                           initial condition for its MRI runs), argmin 1/2 ||y - A x||^2 +
+                           lasso_lambda ||x||_1 by lasso_iters FISTA iterations from 0 in FP64
+                           (step 1 / the largest absolute row sum of G); single solves */
+  int32_t lasso_iters;
+  double lasso_lambda;
 } cs_params;
 
 typedef struct cs_problem cs_problem;

@@ -50,7 +50,9 @@ schedules at closed-form points, the Gram matrix by brute force, the
 recomputed objective, the zero gradient of the exact refit, the ridge on a
 singular support, the damped Jacobi refit (two sweeps worked by hand, and its
 convergence to the exact refit), the conjugate-gradient refit (two iterations
-worked by hand, convergence to the exact refit), the corrected self-term (hand-worked step,
+worked by hand, convergence to the exact refit), the LASSO initial R (three
+FISTA iterations worked by hand, the soft threshold of the separable case, the
+optimality conditions at convergence), the corrected self-term (hand-worked step,
 separable case, brute force against Eq. doublel0) and the best-configuration
 readout (against the recorded trajectory scored by objective());
 tests/test_oracle_mutations.py plants mistakes in it and checks that a pin
@@ -69,6 +71,7 @@ __all__ = [
     "Params", "splitmix64_mix", "counter_uniform", "initial_amplitudes", "gram",
     "coupling_J", "pump", "eta_at", "local_field_cn", "local_field_bn", "injection",
     "euler_step", "self_term_correction", "readout_energy", "cim_run", "refit_exact", "refit_jacobi", "refit_cg",
+    "lasso_fista",
     "objective", "rmse",
     "hamming_loss", "solve",
 ]
@@ -110,6 +113,9 @@ class Params:
     jacobi_iters: int = 100
     cg_iters: int = 10000        # conjugate-gradient refit: at most this many iterations (paper: 10000)
     cg_tol: float = 1e-10        # and until ||h^z_S - G_SS R_S||_2 <= cg_tol ||h^z_S||_2
+    init_R: str = "zeeman"       # initial R: "zeeman" h^z / diag(G); "lasso" the LASSO solution (FISTA)
+    lasso_lambda: float = 1e-3   # the LASSO's L1 weight
+    lasso_iters: int = 500       # FISTA iterations
     seed: int = 0
     self_term: bool = False      # corrected mode: the injection also subtracts (sqrt tau / 4) G_rr R_r^2
     readout: str = "final"       # "final": H(c) at the end of each run; "best": the best configuration visited
@@ -397,6 +403,25 @@ def refit_cg(G, hz, g, sigma, R, iters, tol):
     return R
 
 
+def lasso_fista(G, hz, lam1, iters):
+    """The LASSO solution used as the initial R of the paper's MRI runs:
+    argmin 1/2 x^T G x - (A^T y)^T x + lam1 ||x||_1 (= 1/2 ||y - A x||^2 + lam1 ||x||_1
+    up to a constant) by FISTA (Beck & Teboulle 2009) from x = 0, `iters`
+    iterations, step 1/L with L the largest absolute row sum of G (an upper
+    bound of its largest eigenvalue)."""
+    L = float(np.max(np.sum(np.abs(G), axis=1)))
+    x = np.zeros_like(hz)
+    z = x.copy()
+    t = 1.0
+    for _ in range(iters):
+        v = z - (G @ z - hz) / L
+        xn = np.sign(v) * np.maximum(np.abs(v) - lam1 / L, 0.0)
+        tn = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        z = xn + ((t - 1.0) / tn) * (xn - x)
+        x, t = xn, tn
+    return x
+
+
 # ---------------------------------------------------------------- metrics
 def objective(A, y, x_hat, sigma, lam):
     """Eq. doublel0 at (R, sigma): 1/2 ||y - A x_hat||^2 + lambda |sigma|, x_hat = sigma o R."""
@@ -432,6 +457,8 @@ def solve(A, y, lam, prm: Params, trials: int = 1, inst: int = 0,
     G, hz, g = gram(A, y)
     Goff = G - np.diag(g)
     N = G.shape[0]
+    if R_init is None and prm.init_R == "lasso":
+        R_init = lasso_fista(G, hz, prm.lasso_lambda, prm.lasso_iters)
     if R_init is None:
         R = np.repeat((hz / g)[:, None], trials, axis=1)
     else:

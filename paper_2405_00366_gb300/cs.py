@@ -34,6 +34,8 @@ INITS = {"uniform": CS_INIT_UNIFORM, "normal": CS_INIT_NORMAL}
 REFITS = {"exact": CS_REFIT_EXACT, "jacobi": CS_REFIT_JACOBI, "cg": CS_REFIT_CG}
 CS_READOUT_FINAL, CS_READOUT_BEST = 0, 1
 READOUTS = {"final": CS_READOUT_FINAL, "best": CS_READOUT_BEST}
+CS_INIT_R_ZEEMAN, CS_INIT_R_LASSO = 0, 1
+INIT_RS = {"zeeman": CS_INIT_R_ZEEMAN, "lasso": CS_INIT_R_LASSO}
 
 
 class cs_params(ctypes.Structure):
@@ -53,6 +55,7 @@ class cs_params(ctypes.Structure):
         ("stream_g", ctypes.c_int32), ("autotune", ctypes.c_int32), ("tensor_form", ctypes.c_int32),
         ("self_term", ctypes.c_int32), ("readout", ctypes.c_int32),
         ("cg_iters", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("record_outer", ctypes.c_int32),
+        ("init_R", ctypes.c_int32), ("lasso_iters", ctypes.c_int32), ("lasso_lambda", ctypes.c_double),
     ]
 
 
@@ -129,7 +132,7 @@ def cs_params_default(**overrides) -> cs_params:
     p = cs_params()
     lib().cs_params_default(ctypes.byref(p))
     maps = {"precision": PRECISIONS, "field": FIELDS, "pump_kind": PUMPS, "init_kind": INITS, "refit": REFITS,
-            "readout": READOUTS}
+            "readout": READOUTS, "init_R": INIT_RS}
     for k, v in overrides.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]

@@ -185,6 +185,10 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->eta_init > 0.0 && !(p->velo > 0.0)) return fail(CS_EINVAL, "velo must be > 0 with an eta schedule");
   if (p->record_steps < 0) return fail(CS_EINVAL, "record_steps must be >= 0");
   if (p->record_outer != 0 && p->record_outer != 1) return fail(CS_EINVAL, "record_outer must be 0 or 1");
+  if (p->init_R != CS_INIT_R_ZEEMAN && p->init_R != CS_INIT_R_LASSO) return fail(CS_EINVAL, "bad init_R");
+  if (p->init_R == CS_INIT_R_LASSO &&
+      (p->lasso_iters < 1 || !(p->lasso_lambda >= 0.0) || !std::isfinite(p->lasso_lambda)))
+    return fail(CS_EINVAL, "the LASSO initial R needs lasso_iters >= 1 and lasso_lambda >= 0");
   if (p->timeout_ms <= 0) return fail(CS_EINVAL, "timeout_ms must be > 0");
   if (p->test_phantom_ctas < 0 || p->test_phantom_ctas > 1024) return fail(CS_EINVAL, "bad test_phantom_ctas");
   if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
@@ -332,6 +336,9 @@ void cs_params_default(cs_params* p) {
   p->jacobi_iters = 100;
   p->cg_iters = 10000;
   p->cg_tol = 1e-10;
+  p->init_R = CS_INIT_R_ZEEMAN;
+  p->lasso_iters = 500;
+  p->lasso_lambda = 1e-3;
   p->precision = CS_P_FP32;
   p->seed = 0;
   p->instance = 0;
@@ -410,9 +417,16 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   const long long timeout_cycles = (long long)prm->timeout_ms * (long long)(khz > 0 ? khz : 2000000);
   const RefitJob hjob = make_job(P, S, *prm);
   CS_CUDA(cudaMemcpyAsync(S.job, &hjob, sizeof(hjob), cudaMemcpyHostToDevice, P.stream), "copy job");
-  CS_CUDA(launch_init_R(S.job, 1, S.trials, P.num_sms, P.stream), "init R");
+  if (prm->init_R == CS_INIT_R_LASSO) {
+    CS_CUDA(launch_lasso(P.G, P.hz, (int)P.N, S.trials, prm->lasso_lambda, prm->lasso_iters, S.work, S.R,
+                         P.num_sms, P.stream),
+            "LASSO initial R");
+    P.launches += 2 * prm->lasso_iters + 2;
+  } else {
+    CS_CUDA(launch_init_R(S.job, 1, S.trials, P.num_sms, P.stream), "init R");
+    P.launches += 1;
+  }
   CS_CUDA(mark(p, TM_OTHER, false), "event");
-  P.launches += 1;
   for (int i = 0; i < prm->n_outer; ++i) {
     const double eta = eta_at(i, *prm, P.lambda);
     CS_CUDA(mark(p, TM_EULER, true), "event");
@@ -464,6 +478,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     if (prms[i]->record_steps != 0 || prms[i]->record_outer != 0)
       return fail(CS_EINVAL, "a batched solve does not record trajectories or outer histories");
     if (prms[i]->tensor_form == 4) return fail(CS_EINVAL, "tensor_form = 4: the batched kernel has no tcgen05 form");
+    if (prms[i]->init_R != CS_INIT_R_ZEEMAN)
+      return fail(CS_EINVAL, "a batched solve starts from R = h^z / diag G (init_R = CS_INIT_R_ZEEMAN)");
     if (prms[i]->readout != CS_READOUT_FINAL)
       return fail(CS_EINVAL, "a batched solve reads out the final configuration only (readout = CS_READOUT_FINAL)");
     if (ps[i]->P.stream != ps[0]->P.stream || ps[i]->P.device != ps[0]->P.device)

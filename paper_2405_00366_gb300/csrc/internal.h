@@ -170,6 +170,11 @@ bool refit_grid_wide(const RefitPlan* plan, int njobs, int T, int pool_blocks, s
 // Objective per trial, kept trial, and the kept result's error against FP64
 // (stats[11], stats[12]); err4 is 4 doubles of scratch per job.
 cudaError_t launch_finish(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st, double* err4);
+// The LASSO initial R (refit.cu): argmin 1/2 x^T G x - h^z.x + lam1 ||x||_1 by
+// `iters` FISTA iterations from 0 (step 1 / the largest absolute row sum of G),
+// copied to every trial's column of R (N x T).  work: at least 4 N + 1 doubles.
+cudaError_t launch_lasso(const double* G, const double* hz, int N, int T, double lam1, int iters, double* work,
+                         double* R, int num_sms, cudaStream_t st);
 // Best-configuration readout of one CIM run (euler.cu): per trial the first
 // step n in 1 .. S whose summed energy (CTA partials in fixed order) is lowest;
 // sigma (N x T) takes that step's configuration.

@@ -733,7 +733,83 @@ __global__ void init_R_kernel(const RefitJob* __restrict__ jobs, int T, int njob
   }
 }
 
+// Largest absolute row sum of G (N x N, FP64) into *L: one warp per row,
+// the maximum by an order-independent atomic (L zeroed beforehand).
+__global__ void row_abs_max_kernel(const double* __restrict__ G, int N, double* L) {
+  const int l = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < N; r += gridDim.x * wpb) {
+    const double* Gr = G + (size_t)r * N;
+    double s = 0.0;
+    for (int k = l; k < N; k += 32) s += fabs(Gr[k]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) atomic_max_nonneg(L, s);
+  }
+}
+
+// q = G z - h^z, one warp per row (fixed summation order).
+__global__ void fista_grad_kernel(const double* __restrict__ G, const double* __restrict__ hz,
+                                  const double* __restrict__ z, double* __restrict__ q, int N) {
+  const int l = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < N; r += gridDim.x * wpb) {
+    const double* Gr = G + (size_t)r * N;
+    double s = 0.0;
+    for (int k = l; k < N; k += 32) s = fma(Gr[k], z[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) q[r] = s - hz[r];
+  }
+}
+
+// xn = soft(z - q / L, lam1 / L); z = xn + c (xn - x)   (c = (t_k - 1) / t_{k+1}).
+__global__ void fista_step_kernel(const double* __restrict__ x, double* __restrict__ xn, double* __restrict__ z,
+                                  const double* __restrict__ q, const double* __restrict__ L, double lam1, double c,
+                                  int N) {
+  const double Lv = *L;
+  const double thr = lam1 / Lv;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+    const double v = z[r] - q[r] / Lv;
+    const double a = fabs(v) - thr;
+    const double xr = a > 0.0 ? copysign(a, v) : 0.0;
+    xn[r] = xr;
+    z[r] = xr + c * (xr - x[r]);
+  }
+}
+
+// R[r][t] = x[r] for every trial.
+__global__ void broadcast_R_kernel(const double* __restrict__ x, double* __restrict__ R, int N, int T) {
+  const size_t total = (size_t)N * T;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < total; o += (size_t)gridDim.x * blockDim.x)
+    R[o] = x[o / T];
+}
+
 }  // namespace
+
+cudaError_t launch_lasso(const double* G, const double* hz, int N, int T, double lam1, int iters, double* work,
+                         double* R, int num_sms, cudaStream_t st) {
+  double* xa = work;
+  double* xb = work + N;
+  double* z = work + 2 * (size_t)N;
+  double* q = work + 3 * (size_t)N;
+  double* L = work + 4 * (size_t)N;
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * (4 * (size_t)N + 1), st);
+  if (e != cudaSuccess) return e;
+  const int rows_grid = std::max(1, std::min((N + 7) / 8, 8 * num_sms));
+  row_abs_max_kernel<<<rows_grid, 256, 0, st>>>(G, N, L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int vec_grid = std::max(1, std::min((N + 255) / 256, 4 * num_sms));
+  double t = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    fista_grad_kernel<<<rows_grid, 256, 0, st>>>(G, hz, z, q, N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    fista_step_kernel<<<vec_grid, 256, 0, st>>>(xa, xb, z, q, L, lam1, (t - 1.0) / tn, N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(xa, xb);
+    t = tn;
+  }
+  broadcast_R_kernel<<<std::max(1, std::min((int)(((size_t)N * T + 255) / 256), 4 * num_sms)), 256, 0, st>>>(xa, R, N,
+                                                                                                          T);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st) {
   const int gy = std::min(njobs, 65535);

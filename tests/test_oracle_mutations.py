@@ -198,3 +198,32 @@ def test_planted_cg_mistake_is_caught(monkeypatch, fake):
     monkeypatch.setattr(om, "refit_cg", fake)
     monkeypatch.setattr(oracle, "refit_cg", fake)
     assert _fails(pins.test_cg_refit_two_steps_hand_worked)
+
+
+def _fista_no_momentum(G, hz, lam1, iters):
+    L = float(np.max(np.sum(np.abs(G), axis=1)))
+    x = np.zeros_like(hz)
+    for _ in range(iters):
+        v = x - (G @ x - hz) / L
+        x = np.sign(v) * np.maximum(np.abs(v) - lam1 / L, 0.0)
+    return x
+
+
+def _fista_threshold_unscaled(G, hz, lam1, iters):
+    L = float(np.max(np.sum(np.abs(G), axis=1)))
+    x = np.zeros_like(hz)
+    z, t = x.copy(), 1.0
+    for _ in range(iters):
+        v = z - (G @ z - hz) / L
+        xn = np.sign(v) * np.maximum(np.abs(v) - lam1, 0.0)
+        tn = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        z, x, t = xn + ((t - 1.0) / tn) * (xn - x), xn, tn
+    return x
+
+
+@pytest.mark.parametrize("fake", [_fista_no_momentum, _fista_threshold_unscaled])
+def test_planted_fista_mistake_is_caught(monkeypatch, fake):
+    """Plain ISTA (no momentum) and a threshold not divided by L fail the three-step pin."""
+    monkeypatch.setattr(om, "lasso_fista", fake)
+    monkeypatch.setattr(oracle, "lasso_fista", fake)
+    assert _fails(pins.test_fista_three_steps_hand_worked)

@@ -229,6 +229,39 @@ def test_cg_refit_converges_to_exact():
         np.testing.assert_allclose(R, exact, rtol=0, atol=1e-8 * np.abs(exact).max())
 
 
+def test_fista_three_steps_hand_worked():
+    """Three FISTA iterations of the LASSO on a 2 x 2 problem (tests/golden/fista_three_steps.txt)."""
+    gold = {k: np.array([float(v) for v in vals]) for k, vals in _read_golden("fista_three_steps.txt").items()}
+    G = np.array([[2.0, 1.0], [1.0, 2.0]])
+    hz = np.array([3.0, 1.0])
+    for iters, key in ((1, "x1"), (2, "x2"), (3, "x3")):
+        np.testing.assert_allclose(oracle.lasso_fista(G, hz, 0.5, iters), gold[key], rtol=0, atol=1e-15)
+
+
+def test_fista_separable_case_is_the_soft_threshold():
+    """G = I: the LASSO solution is the soft threshold of A^T y by lam1, reached
+    after one iteration (L = 1) and kept."""
+    rng = np.random.default_rng(12)
+    hz = rng.standard_normal(40)
+    for iters in (1, 5):
+        x = oracle.lasso_fista(np.eye(40), hz, 0.3, iters)
+        np.testing.assert_allclose(x, np.sign(hz) * np.maximum(np.abs(hz) - 0.3, 0.0), rtol=0, atol=1e-15)
+
+
+def test_fista_meets_the_lasso_optimality_conditions():
+    """At convergence the subgradient conditions hold: (A^T y - G x)_r = lam1 sign(x_r)
+    on the support and |(A^T y - G x)_r| <= lam1 off it."""
+    inst = cs_inputs.random_instance(120, 80, 12, 0.05, 0.1, seed=13)
+    G, hz, g = oracle.gram(inst.A, inst.y)
+    lam1 = 0.05
+    x = oracle.lasso_fista(G, hz, lam1, 20000)
+    grad = hz - G @ x
+    on = x != 0
+    assert on.any() and (~on).any()
+    np.testing.assert_allclose(grad[on], lam1 * np.sign(x[on]), rtol=0, atol=1e-8)
+    assert np.abs(grad[~on]).max() <= lam1 + 1e-8
+
+
 def test_jacobi_refit_converges_to_exact():
     inst = cs_inputs.random_instance(100, 70, 10, 0.05, 0.1, seed=8)
     G, hz, g = oracle.gram(inst.A, inst.y)

@@ -483,3 +483,38 @@ def test_paper_schedule_outer_history_matches_oracle(field):
     np.testing.assert_allclose(R_h, r["R_outer"], rtol=0, atol=1e-9)
     ham = [oracle.hamming_loss(sig_h[i, :, 0], inst.xi) for i in range(w["n_outer"])]
     assert ham[-1] < ham[0]  # the alternation improves the support estimate on this instance
+
+
+# ------------------------------------------------------------------ f3: the paper's MRI model
+ORACLE_KEYS_MRI = ORACLE_KEYS | {"cg_iters", "cg_tol", "init_R", "lasso_lambda", "lasso_iters"}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mri_full_model_matches_oracle(precision):
+    """The paper's MRI problem on a synthetic 16 x 16 image: complex-DFT observation
+    (real-ified), the gamma-weighted second-difference terms, the LASSO solution
+    (FISTA on the GPU) as the initial R, conjugate-gradient CDP, the MRI pump
+    (d = 0.6) and fixed eta, against the oracle: supports of every trial after
+    every outer iteration identical, x_hat to 1e-7 relative."""
+    w = cs_inputs.workload("mri_full_n16384", mri_side=16, N=256, M_obs=77, M=2 * 77 + 2 * 256, nnz=26,
+                           n_outer=4, trials=3, precision=precision, mri_gamma=1e-3, lasso_iters=200)
+    inst = cs_inputs.workload_instance(w)
+    assert inst.A.shape == (w["M"], w["N"])
+    T = w["trials"]
+    prm = cs.params_from_workload(w, record_outer=1)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        cs.cs_solve(h, prm, T)
+        x, s, E, st, status = cs.cs_result(h)
+        sig_h, R_h = cs.cs_outer_history(h, w["n_outer"], inst.N, T)
+    finally:
+        cs.cs_problem_destroy(h)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle.Params(**{k: v for k, v in w.items() if k in ORACLE_KEYS_MRI}),
+                     trials=T)
+    np.testing.assert_array_equal(sig_h, r["sigma_outer"])
+    np.testing.assert_allclose(x, r["x_hat"], rtol=0, atol=1e-7 * max(1.0, np.abs(r["x_hat"]).max()))
+    # the LASSO start matters: the first support differs from the plain start's
+    plain = oracle.solve(inst.A, inst.y, inst.lam,
+                         oracle.Params(**{k: v for k, v in dict(w, init_R="zeeman").items() if k in ORACLE_KEYS_MRI}),
+                         trials=T)
+    assert not np.array_equal(plain["sigma_outer"][0], r["sigma_outer"][0])
