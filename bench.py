@@ -254,12 +254,12 @@ def job_value(world, units_per_rank, total_s):
     return world * units_per_rank / total_s
 
 
-def config_of(w, world, name=WORKLOAD):
+def config_of(w, world, name=WORKLOAD, autotune=1):
     return {"workload": name, "N": w["N"], "M": w["M"], "nnz": w["nnz"], "noise": w["nu"], "lambda": w["lam"],
             "trials": w["trials"], "n_outer": w["n_outer"], "n_steps": w["n_steps"], "dt": w["dt"],
             "field": w["field"], "precision": w["precision"], "refit": w["refit"],
             "parallelism": f"replicas{world}" if world > 1 else "single",
-            "work_split": "cost model" if name == "mri_n16384_fp16" else "autotuned",
+            "work_split": "cost model" if (name == "mri_n16384_fp16" or not autotune) else "autotuned",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
 
 
@@ -569,6 +569,9 @@ def main():
     ap.add_argument("--tensor-form", type=int, choices=[0, 1, 2, 3, 4], default=0,
                     help="cs_params.tensor_form: 0 planner, 1 FMA forms only, 2 tensor cores only, 3 mma.sync forms only, 4 tcgen05 form only")
     ap.add_argument("--reference-step-s", type=float, default=8.0)
+    ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
+                    help="cs_params.autotune of the main workloads (0 for profiling: under ncu the tuning runs' "
+                         "timings are distorted, so the cost model's split is the one to capture)")
     ap.add_argument("--n-outer", type=int, default=None,
                     help="override the workload's outer iterations (short runs for profiling only)")
     ap.add_argument("--n-steps", type=int, default=None,
@@ -617,7 +620,8 @@ def main():
     inst = cs_inputs.workload_instance(w)
     # work split timed on this GPU during the warm-up (the MRI-shaped problem keeps
     # the cost model's streamed split: its tuning runs would take seconds)
-    prm = cs.params_from_workload(w, autotune=0 if name == "mri_n16384_fp16" else 1, tensor_form=args.tensor_form)
+    tune = 0 if name == "mri_n16384_fp16" else args.autotune
+    prm = cs.params_from_workload(w, autotune=tune, tensor_form=args.tensor_form)
     T = w["trials"]
     stream = torch.cuda.Stream()
     A_dev = torch.from_numpy(inst.A).cuda()
@@ -759,6 +763,7 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["launch_ms"] = per_launch_s * 1e3
     roof["form"] = form
+    roof["plan"] = {"cluster": int(stats[8]), "ctas": int(stats[9])}
     roof["us_per_euler_step"] = per_launch_s * 1e6 / w["n_steps"]
     ms_sorted = sorted(step_ms)
     line = {
@@ -766,7 +771,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"single_n200_fp64": "f64", "mri_n16384_fp16": "f16 storage, f32 compute"}.get(name, "f32"),
-        "data": "synthetic", "config": config_of(w, world, name),
+        "data": "synthetic", "config": config_of(w, world, name, args.autotune),
         "spin_steps_per_s": world * w["N"] * T * w["n_outer"] * w["n_steps"] / (total_s / args.steps),
         "latency_ms": {"p50": ms_sorted[len(ms_sorted) // 2],
                        "p99": ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]},
