@@ -264,7 +264,7 @@ def config_of(w, world, name=WORKLOAD, autotune=1):
 
 
 # ------------------------------------------------------------------ batched and served workloads
-BATCH = dict(n_inst=512, n_min=256, n_max=1024, alphas=[0.3, 0.5, 0.7], sparsities=[0.05, 0.1, 0.2],
+BATCH = dict(n_inst=512, n_min=256, n_max=4096, alphas=[0.3, 0.5, 0.7], sparsities=[0.05, 0.1, 0.2],
              nu=0.01, lam=0.03, trials=16, n_plain=16, seed=17)
 
 
@@ -293,28 +293,33 @@ def run_batch(args):
     dev = [(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda()) for i in insts]
     torch.cuda.synchronize()
     over = {k: v for k, v in (("n_outer", args.n_outer), ("n_steps", args.n_steps)) if v}
-    prm_b = _run_params(cs, "bf16", **over)
+    prm_b = _run_params(cs, "bf16", autotune=args.autotune, **over)
+    prm_w = _run_params(cs, "bf16", autotune=args.autotune, **dict(over, n_outer=1))
     prm_p = _run_params(cs, "fp32", **over)
+    # the problems (G formed once, kept resident) serve every batch
+    hs = [cs.cs_problem_create(A, y, i.lam, stream=stream) for (A, y), i in zip(dev, insts)]
 
-    def batched():
-        hs = [cs.cs_problem_create(A, y, i.lam, stream=stream) for (A, y), i in zip(dev, insts)]
+    def batched(prm):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        cs.cs_solve_batch(hs, prm_b, T)
+        cs.cs_solve_batch(hs, prm, T)
         ev1.record(stream)
         res = [cs.cs_result(h) for h in hs]
-        for h in hs:
-            cs.cs_problem_destroy(h)
         return ev0.elapsed_time(ev1) / 1e3, res
 
+    # warm-up batches of one outer iteration each: the same launches (and the
+    # batch autotuner's timing runs) at a thirtieth of a full batch's time
     for _ in range(max(1, args.warmup)):
-        batched()
+        batched(prm_w)
     times, res = [], None
     with ClockSampler(_env_int("LOCAL_RANK", 0)) as clocks:
         for _ in range(max(1, args.steps)):
-            t, res = batched()
+            t, res = batched(prm_b)
             times.append(t)
+        shapes = sorted({(int(r[3][8]), int(r[3][10])) for r in res})
+        for h in hs:
+            cs.cs_problem_destroy(h)
         # plain FP32 solves, one instance at a time, on the first n_plain instances
         plain_s, plain_rmse = 0.0, []
         for k in range(b["n_plain"]):
@@ -371,8 +376,9 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
         "config": {"workload": "batch_uneven_bf16", "instances": len(insts), "N_range": [min(Ns), max(Ns)],
                    "alphas": b["alphas"], "sparsities": b["sparsities"], "trials": T, "n_outer": prm_b.n_outer,
-                   "n_steps": prm_b.n_steps, "precision": "bf16", "note": "N range scaled down from [256, 4096]: "
-                   "the batched kernel runs each problem on one CTA"},
+                   "n_steps": prm_b.n_steps, "precision": "bf16", "autotune": args.autotune,
+                   "warmup_batches": "one outer iteration each",
+                   "cluster_sizes_and_forms": shapes, "l2": "inputs larger than L2 (G_off of all instances)"},
         "spin_steps_per_s": sum(Ns) * T * prm_b.n_outer * prm_b.n_steps / t_b,
         "quality": {"rmse_mean": float(np.mean(rmse_b)),
                     "rmse_mean_first_plain": float(np.mean(rmse_b[:b["n_plain"]])),

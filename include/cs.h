@@ -86,7 +86,8 @@ typedef struct {
   int32_t test_phantom_ctas; /* test hook: the grid barrier also waits for this many CTAs that
                                 do not exist, so it runs into timeout_ms; 0 in normal use */
   int32_t cluster_size; /* CTAs per thread-block cluster of the Euler kernel: 0 = chosen by the
-                           library's planner, or 1, 2, 4, 8 */
+                           library's planner, or 1, 2, 4, 8; in a batch, the first problem of a
+                           group fixes the batched kernel's cluster size this way */
   int32_t max_ctas;     /* at most this many CTAs (SMs) per Euler launch, 0 = all; lets solves
                            on different streams share the GPU */
   int32_t stream_g;     /* 0: keep G_off on chip when it fits, else stream its tiles from memory
@@ -94,7 +95,10 @@ typedef struct {
   int32_t autotune;     /* 0: the planner's cost model picks the Euler work split (deterministic);
                            1: the first solve of a shape in this process times the cost model's
                            four cheapest splits on this GPU (48 steps each, synchronising the
-                           problem's stream) and keeps the fastest for later solves */
+                           problem's stream) and keeps the fastest for later solves; in a batch,
+                           the first batch of a shape times the batched kernel's cluster sizes
+                           and ring shapes (48 steps of every problem each).  Choices persist
+                           across processes in the tuning cache file (cs_tune_info) */
   int32_t tensor_form;  /* the product G_off X on the tensor cores.  FP32 problems with trial
                            blocks of 16, 32 or 64: G_off and X each split into two FP16 parts
                            (FP32-level accuracy), either on the tcgen05 tensor cores (one
@@ -171,8 +175,14 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
  * problem i with its own parameters *prm[i] and trials[i] (<= 64) trials.
  * Problems that share a storage precision, a trial count and the tensor-core
  * decision form a group; each outer iteration of a group is one persistent
- * launch in which every CTA takes whole problems from a device work queue
- * (largest N first) and streams that problem's G_off tiles from memory, then
+ * launch of thread-block clusters that take problems from a device work queue
+ * (largest N first) and stream each problem's G_off tiles from memory: a
+ * large problem (at least two 128-row tiles per CTA) is run by a whole
+ * cluster, the CTAs splitting its row tiles and meeting at the cluster barrier
+ * after every Euler step, a small one by one CTA alone.  The cluster size
+ * (1, 2, 4, 8) is the group's first problem's cluster_size when that is not
+ * 0; otherwise, and for the ring shape, the batch autotuner chooses when a
+ * problem of the group sets autotune = 1, else clusters of one CTA.  Then
  * one refit launch covers every (problem, trial) of the group.  A problem
  * leaves the batch after its own n_outer iterations.  All outer iterations and
  * the objective are captured into one CUDA graph, submitted to the problems'
@@ -186,6 +196,13 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials);
  * tensor-core form), CS_ENOMEM, CS_ECUDA. */
 cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prm, const int32_t* trials, int32_t n);
 
+/* The autotuners' record: *tunings = timed tuning runs in this process,
+ * *disk_hits = choices taken from the tuning cache file instead, and path
+ * (path_len bytes, NUL-terminated, may be NULL) = that file: $CS_TUNE_CACHE if
+ * set (empty: no file), else $XDG_CACHE_HOME/paper_2405_00366_gb300/tune.txt,
+ * else $HOME/.cache/paper_2405_00366_gb300/tune.txt.  Host only; never fails. */
+cs_status cs_tune_info(int64_t* tunings, int64_t* disk_hits, char* path, int64_t path_len);
+
 /* Wait for the last solve and copy out the kept trial (lowest energy, ties to
  * the lower trial index): x_hat = sigma o R (N doubles), sigma_hat (N bytes,
  * 0/1) and its energy (Eq. doublel0 with the problem's lambda, recomputed from
@@ -193,7 +210,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prm, con
  * receives CS_STATS_LEN doubles:
  *   [0] kept trial index  [1] |sigma_hat|  [2] 1 if a refit used the ridge
  *   [3] device error word (0 = none)       [4] trials  [5] N  [6] M
- *   [7] energy of the kept trial  [8] cluster size and [9] CTAs of the Euler kernel
+ *   [7] energy of the kept trial  [8] cluster size (batched: CTAs that ran the problem) and [9] CTAs of the Euler kernel
  *   [10] form of the Euler kernel: 0 FP32/FP64 FMAs (narrow split), 1 packed FP32
  *        FMAs (wide split), 2 tensor cores (mma.sync), 3 batched (one problem per CTA),
  *        4 batched on tensor cores (mma.sync), 5 tensor cores (tcgen05, TMEM)

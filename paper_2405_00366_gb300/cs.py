@@ -102,6 +102,8 @@ def lib():
         L.cs_server_destroy.argtypes = [P]
         L.cs_server_destroy.restype = None
         L.cs_problem_shape.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.cs_tune_info.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P,
+                                   ctypes.c_int64]
         L.cs_problem_destroy.argtypes = [P]
         L.cs_problem_destroy.restype = None
         L.cs_last_error.argtypes = []
@@ -110,7 +112,7 @@ def lib():
                      "cs_outer_history",
                      "cs_problem_gram", "cs_problem_shape", "cs_problem_timing", "cs_objective_static",
                      "cs_server_create", "cs_server_submit", "cs_server_submit_host", "cs_server_poll",
-                     "cs_server_wait", "cs_server_result"]:
+                     "cs_server_wait", "cs_server_result", "cs_tune_info"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -321,6 +323,15 @@ def cs_outer_history(problem, n_outer: int, N: int, trials: int):
     R = np.empty((n_outer, N, trials))
     _check(lib().cs_outer_history(problem, s.ctypes.data, R.ctypes.data), allow=(CS_OK, CS_ESINGULAR))
     return s, R
+
+
+def cs_tune_info():
+    """(timed tunings, choices read from the tuning cache file, that file's path)."""
+    t = ctypes.c_int64()
+    h = ctypes.c_int64()
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib().cs_tune_info(ctypes.byref(t), ctypes.byref(h), buf, len(buf)))
+    return t.value, h.value, buf.value.decode()
 
 
 def cs_problem_shape(problem):

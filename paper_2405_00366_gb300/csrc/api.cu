@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -468,6 +469,110 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   return CS_OK;
 }
 
+// Cluster size, span threshold and ring shape of a batched launch; the
+// problems (row tiles in processing order, largest first) with at least
+// span_rt row tiles are each run by a whole cluster.
+static void apply_batch_shape(const BatchShape& sh, const std::vector<int>& rts, BatchLaunch* L) {
+  L->cc = sh.cc;
+  L->tps = sh.tps;
+  L->slots = sh.slots;
+  L->n_large = 0;
+  if (sh.cc > 1)
+    while (L->n_large < (int)rts.size() && rts[L->n_large] >= sh.span_rt) ++L->n_large;
+}
+
+// Batch autotuner: the shape of the group's launches (BatchShape), chosen
+// by timing kBatchTuneSteps Euler steps of every problem of the group's first
+// outer iteration for each candidate (clusters of 1, 2, 4, 8 CTAs, where a
+// problem has at least two row tiles per CTA of a cluster, or only the
+// cluster size the group's first problem fixes with cluster_size; 4, 2 or 1 column
+// tiles per ring slot with as many slots as fit), twice each on the problems'
+// stream (the second run counts), unless the tuning cache holds a choice for
+// the group's precision, trials, form and row-tile histogram on this device.
+// The runs write only the solves' scratch (state, X, sigma), which the real
+// launches rewrite.
+constexpr int kBatchTuneSteps = 48;
+
+static cs_status tune_batch_shape(BatchLaunch L, const std::vector<int>& rts, bool btc, int fixed_cc, int device,
+                                  cudaStream_t stream, BatchShape* out) {
+  std::map<int, int> hist;
+  for (int r : rts) ++hist[r];
+  std::string key = "batch|" + tune_device_tag(device) + "|p" + std::to_string(L.prm->precision) + "|T" +
+                    std::to_string(L.T) + "|tc" + std::to_string((int)btc) + "|c" + std::to_string(L.ctas) + "|k" +
+                    std::to_string(fixed_cc) + "|";
+  for (const auto& kv : hist) key += std::to_string(kv.first) + ":" + std::to_string(kv.second) + ",";
+  const int max_rt = rts.empty() ? 0 : *std::max_element(rts.begin(), rts.end());
+  std::vector<BatchShape> cands;
+  for (int cc : {1, 2, 4, 8}) {
+    if ((cc > 1 && max_rt < 2 * cc && cc != fixed_cc) || (fixed_cc > 0 && cc != fixed_cc)) continue;
+    for (int tps : {4, 2, 1}) {
+      BatchShape b;
+      b.cc = cc;
+      b.tps = tps;
+      b.slots = 0;
+      b.span_rt = cc > 1 ? 2 * cc : 0;
+      cands.push_back(b);
+    }
+  }
+  auto tag = [](const BatchShape& b) {
+    return std::to_string(b.cc) + " " + std::to_string(b.tps) + " " + std::to_string(b.slots) + " " +
+           std::to_string(b.span_rt);
+  };
+  std::string stored;
+  if (tune_lookup(key, &stored))
+    for (const BatchShape& b : cands)
+      if (tag(b) == stored) {
+        *out = b;
+        tune_note(false);
+        return CS_OK;
+      }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CS_CUDA(cudaEventCreate(&e0), "tuning event");
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    CS_CUDA(e, "tuning event");
+  }
+  float best = 0.f;
+  bool have = false;
+  L.step_cap = kBatchTuneSteps;
+  for (const BatchShape& b : cands) {
+    apply_batch_shape(b, rts, &L);
+    float ms = 0.f;
+    bool fits = true;
+    for (int rep = 0; rep < 2 && e == cudaSuccess && fits; ++rep) {
+      e = cudaEventRecord(e0, stream);
+      if (e == cudaSuccess) {
+        e = launch_euler_batch(L, stream);
+        if (e == cudaErrorInvalidConfiguration) {  // the ring shape does not fit shared memory
+          cudaGetLastError();
+          e = cudaSuccess;
+          fits = false;
+        }
+      }
+      if (e == cudaSuccess && fits) e = cudaEventRecord(e1, stream);
+      if (e == cudaSuccess && fits) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && fits) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e != cudaSuccess) break;
+    if (fits && (!have || ms < best)) {
+      best = ms;
+      *out = b;
+      have = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CS_CUDA(e, "batch autotuning run");
+  if (!have) return fail(CS_EINVAL, "batched Euler kernel does not fit shared memory");
+  int err = 0;
+  CS_CUDA(cudaMemcpy(&err, L.err, sizeof(int), cudaMemcpyDeviceToHost), "read tuning error word");
+  if (err == DEV_TIMEOUT) return fail(CS_ETIMEOUT, "a device-side wait timed out while tuning the batch");
+  tune_note(true);
+  tune_store(key, tag(*out));
+  return CS_OK;
+}
+
 cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, const int32_t* trials, int32_t n) {
   if (!ps || !prms || !trials || n < 1) return fail(CS_EINVAL, "need at least one problem, with its params and trials");
   for (int i = 0; i < n; ++i) {
@@ -539,6 +644,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   std::vector<unsigned char> hinst;
   std::vector<std::vector<size_t>> inst_off(n_outer_max, std::vector<size_t>(groups.size(), 0));
   std::vector<std::vector<int>> inst_cnt(n_outer_max, std::vector<int>(groups.size(), 0));
+  std::vector<std::vector<std::vector<int>>> inst_rt(n_outer_max, std::vector<std::vector<int>>(groups.size()));
   for (int it = 0; it < n_outer_max; ++it)
     for (size_t g = 0; g < groups.size(); ++g) {
       std::vector<int> act;
@@ -547,6 +653,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
       std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return ps[a]->P.N > ps[b]->P.N; });
       inst_off[it][g] = hinst.size();
       inst_cnt[it][g] = (int)act.size();
+      for (int i : act) inst_rt[it][g].push_back(batch_row_tiles(ps[i]->P.N));
       hinst.resize(hinst.size() + ib * act.size());
       for (size_t k = 0; k < act.size(); ++k) {
         const int i = act[k];
@@ -595,6 +702,33 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   const long long timeout_cycles = timeout_ms * (long long)(khz > 0 ? khz : 2000000);
   for (size_t g = 0; g < groups.size(); ++g)
     CS_CUDA(launch_init_R(d_jobs + job_off[g], (int)groups[g].idx.size(), groups[g].T, P0.num_sms, stream), "init R");
+  // ring and cluster shape of each group: tuned (or taken from the tuning
+  // cache) when a problem of the group asks for autotuning, else the default
+  std::vector<BatchShape> shapes(groups.size());
+  for (size_t g = 0; g < groups.size(); ++g) {
+    bool tune = false;
+    for (int i : groups[g].idx) tune = tune || prms[i]->autotune != 0;
+    const int fixed_cc = prms[groups[g].idx[0]]->cluster_size;
+    if (fixed_cc > 1) {
+      shapes[g].cc = fixed_cc;
+      shapes[g].span_rt = 2 * fixed_cc;
+    }
+    if (!tune || inst_cnt[0][g] == 0) continue;
+    BatchLaunch L;
+    L.insts = static_cast<unsigned char*>(d_insts) + inst_off[0][g];
+    L.order = d_order;
+    L.n = inst_cnt[0][g];
+    L.T = groups[g].T;
+    L.prm = prms[groups[g].idx[0]];
+    L.queue = d_queue;
+    L.outer = 0;
+    L.err = d_err;
+    L.timeout_cycles = timeout_cycles;
+    L.ctas = L.prm->max_ctas > 0 ? std::min(L.prm->max_ctas, P0.num_sms) : P0.num_sms;
+    if ((st = tune_batch_shape(L, inst_rt[0][g], groups[g].btc, fixed_cc, P0.device, stream, &shapes[g])) != CS_OK)
+      return st;
+  }
+  CS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream), "memset err");
   // Every outer iteration of every group (batched Euler launch + refit) and the
   // objective are captured into one CUDA graph and submitted as a single launch.
   // (captured on a private stream: the problems' stream may be the legacy
@@ -628,6 +762,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
       L.err = d_err;
       L.timeout_cycles = timeout_cycles;
       L.ctas = gp.max_ctas > 0 ? std::min(gp.max_ctas, P0.num_sms) : P0.num_sms;
+      apply_batch_shape(shapes[g], inst_rt[it][g], &L);
       e = launch_euler_batch(L, cap);
       where = "batched euler launch";
       if (e == cudaSuccess) {
@@ -669,7 +804,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     for (int i : groups[g].idx) {
       ps[i]->S.done = true;
       ps[i]->S.has_outer = false;
-      ps[i]->S.plan_cluster = 0;
+      ps[i]->S.plan_cluster =
+          (shapes[g].cc > 1 && batch_row_tiles(ps[i]->P.N) >= shapes[g].span_rt) ? shapes[g].cc : 1;
       ps[i]->S.plan_ctas = std::min((int)groups[g].idx.size(), P0.num_sms);
       ps[i]->S.plan_form = groups[g].btc ? 4 : 3;
     }

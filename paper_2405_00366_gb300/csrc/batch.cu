@@ -1,12 +1,16 @@
 // Batched solves of many independent problems of uneven size (Algorithm 1 for
 // each): one outer iteration of every problem in one persistent launch.
 //
-// Each CTA takes whole problems from a device work queue (largest first, so the
-// tail is short) and runs a complete CIM run of the problem it took: the
-// prologue (b or q, initial c and e), every Euler step of Eq. mfeq1 /
-// Eq. GMFZEC5 with the field of Eq. localfieldMFZ or Eq. localfieldMFZBN, and
-// the readout sigma = H(c).  A problem never spans CTAs, so no inter-CTA
-// synchronisation is needed and the whole GPU streams independent problems.
+// The launch is a grid of thread-block clusters of cc CTAs that take problems
+// from a device work queue, largest first, so the tail is short.  The queue's
+// first n_large problems (the large ones) are each run by a whole cluster: CTA
+// rank j of the cluster takes row tiles j, j + cc, ... of every product and
+// update, and the cluster barrier ends each Euler step (X of the next step is
+// complete once every CTA has written its rows).  Every other problem is run
+// by one CTA alone, with no inter-CTA synchronisation.  A run is one complete
+// CIM run of Algorithm 1's inner loop: the prologue (b or q, initial c and e),
+// every Euler step of Eq. mfeq1 / Eq. GMFZEC5 with the field of
+// Eq. localfieldMFZ or Eq. localfieldMFZBN, and the readout sigma = H(c).
 //
 // G_off of a problem is stored for streaming: tiles of kRT rows x kKC columns,
 // tile (rt, kc) contiguous, rows zero-padded to a multiple of kRT and columns
@@ -20,6 +24,8 @@
 // next X.  With BF16 / FP16 storage and 8 or 16 trials the product runs on the
 // tensor cores instead (tile_product_tc): the tiles then hold G_off in the
 // MMA's A-operand order and X is stored in two 16-bit parts.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -30,6 +36,8 @@
 #include "tma.cuh"
 
 namespace cs {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -100,6 +108,9 @@ struct BArgs {
   int outer;
   int* err;
   long long timeout_cycles;
+  int cc;           // CTAs per cluster
+  int n_large;      // queue items [0, n_large) are run by a whole cluster
+  int step_cap;     // > 0: at most this many Euler steps per run (tuning runs)
 };
 
 // One ring slot: tps consecutive column tiles of G_off, then their tps x kKC
@@ -326,12 +337,13 @@ __device__ __forceinline__ bool tile_product_pair(const BArgs<float>& a, const B
 // 16 x 8 x 16 tile (hi and lo of X).  The MMAs of one ring slot chain in
 // accumulators that start from zero and are then added to the FP32 sums
 // (round to nearest).  P (kRT x twp) receives U, scaled back by xsi.  The
-// producer issues the next row tile's first chunks before the CTA-wide sync
-// that ends this product (pre counts them; every row tile of a pass reads the
-// same X, so only the pass's last row tile issues none).
+// producer issues the CTA's next row tile's (rt + rstep) first chunks before
+// the CTA-wide sync that ends this product (pre counts them; every row tile of
+// a pass reads the same X, so only the CTA's last row tile of a pass issues
+// none).
 template <typename GT, int NT>
 __device__ __forceinline__ bool tile_product_tc(const BArgs<float>& a, const BInst<float>& I,
-                                                const float* __restrict__ X, int rt, unsigned char* ring,
+                                                const float* __restrict__ X, int rt, int rstep, unsigned char* ring,
                                                 size_t slot, float* P, uint64_t* full, uint64_t* empty,
                                                 unsigned& gctr, unsigned* issued, float xsi, int& pre) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -345,9 +357,9 @@ __device__ __forceinline__ bool tile_product_tc(const BArgs<float>& a, const BIn
       // tile of this pass (same X), whose copies then land during the update
       produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued, pre, nch);
       pre = 0;
-      if (rt + 1 < I.nrt) {
+      if (rt + rstep < I.nrt) {
         pre = min(a.slots, nch);
-        produce_row_tile<GT, float>(a, I, X, rt + 1, ring, slot, full, empty, gctr + nch, issued, 0, pre);
+        produce_row_tile<GT, float>(a, I, X, rt + rstep, ring, slot, full, empty, gctr + nch, issued, 0, pre);
       }
     }
     gctr += nch;
@@ -447,11 +459,11 @@ __device__ __forceinline__ CT tile_sum(const CT* P, int rl, int t, int twp) {
 // Product of one row tile in the form the launch was built for.
 template <typename GT, typename CT, int MR, bool PAIR, bool TC>
 __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
-                                                 int rt, unsigned char* ring, size_t slot, CT* P, uint64_t* full,
-                                                 uint64_t* empty, unsigned& gctr, unsigned* issued, float xsi,
-                                                 int& pre) {
+                                                 int rt, int rstep, unsigned char* ring, size_t slot, CT* P,
+                                                 uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued,
+                                                 float xsi, int& pre) {
   if constexpr (TC) {
-    return tile_product_tc<GT, MR>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued, xsi, pre);
+    return tile_product_tc<GT, MR>(a, I, X, rt, rstep, ring, slot, P, full, empty, gctr, issued, xsi, pre);
   } else if constexpr (PAIR) {
     return tile_product_pair<GT>(a, I, X, rt, ring, slot, P, full, empty, gctr, issued);
   } else {
@@ -459,12 +471,41 @@ __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst
   }
 }
 
-// One CIM run of problem I.  Returns false (in every thread) if a wait timed out.
+__device__ __forceinline__ size_t zmin(size_t x, size_t y) { return x < y ? x : y; }
+
+// End of a phase of a run: X (and the state) written by every CTA of the run
+// become visible to the next phase's bulk copies.  A run of `span` CTAs (a
+// whole cluster) meets at the cluster barrier, where each CTA also posts its
+// `ok` (CTA-uniform) in vote[vpar] and then reads every CTA's: every CTA of the
+// cluster returns the same decision, so all of them take the same number of
+// cluster barriers.  (vote has two entries, used in turn: an entry is rewritten
+// only two barriers later, after every CTA has read it.)
+__device__ __forceinline__ bool run_sync(int span, bool ok, int* vote, unsigned& vpar) {
+  fence_proxy_async_global();
+  if (span == 1) {
+    __syncthreads();
+    return ok;
+  }
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x == 0) vote[vpar] = ok ? 1 : 0;
+  cl.sync();
+  int all = 1;
+  for (int r = 0; r < span; ++r) all &= *cl.map_shared_rank(vote + vpar, r);
+  vpar ^= 1u;
+  return all != 0;
+}
+
+// One CIM run of problem I by `span` CTAs (rank `rank` of them takes row tiles
+// rank, rank + span, ...).  Returns false (in every thread of every CTA of the
+// run) if a wait timed out.
 template <typename GT, typename CT, int MR, bool PAIR, bool TC>
-__device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned char* ring, size_t slot, CT* P,
-                             uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued) {
+__device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, int span, unsigned char* ring,
+                             size_t slot, CT* P, uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued,
+                             int* vote, unsigned& vpar) {
   const int T = a.T, twp = a.twp, N = I.N;
   const size_t NT = (size_t)N * T;
+  const size_t tileT = (size_t)kRT * T;  // elements of one row tile
+  const int steps = a.step_cap > 0 ? min(I.n_steps, a.step_cap) : I.n_steps;
   int pre = 0;  // producer: chunks of the next row tile already issued
   // tensor-core form: X scaled by 2^-e with max |R| < 2^e (exact; U scaled back)
   CT xsc = CT(1);
@@ -492,16 +533,17 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
   const CT wcoef = (I.field == CS_FIELD_CN) ? CT(-0.25) : CT(-0.5 * st);
   bool ok = true;
   // ---- prologue
+  // (the elements of this CTA's rows: row tiles rank, rank + span, ...)
   if (I.field == CS_FIELD_CN) {
-    for (size_t idx = threadIdx.x; idx < NT; idx += kBThreads) {
-      const int r = (int)(idx / T), t = (int)(idx % T);
-      bxput<GT, CT, PAIR, TC>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
-    }
-    fence_proxy_async_global();
-    __syncthreads();
-    for (int rt = 0; rt < I.nrt && ok; ++rt) {
-      ok = __syncthreads_and(
-          row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, ring, slot, P, full, empty, gctr, issued, xsi, pre));
+    for (int rt = rank; rt < I.nrt; rt += span)
+      for (size_t idx = rt * tileT + threadIdx.x; idx < zmin(NT, (rt + 1) * tileT); idx += kBThreads) {
+        const int r = (int)(idx / T), t = (int)(idx % T);
+        bxput<GT, CT, PAIR, TC>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
+      }
+    ok = run_sync(span, ok, vote, vpar);
+    for (int rt = rank; rt < I.nrt && ok; rt += span) {
+      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, span, ring, slot, P, full, empty,
+                                                                    gctr, issued, xsi, pre));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
         const int r = rt * kRT + idx / T, t = idx % T;
         if (r >= N) continue;
@@ -513,31 +555,33 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
       __syncthreads();
     }
   } else {
-    for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
-      const int r = (int)(o / T);
-      const double corr = I.self_term ? (st / 4.0) * I.g[r] * I.R[o] * I.R[o] : 0.0;
-      b[o] = CT((st / 2.0) * I.R[o] * I.hz[r] - I.theta - corr);
+    for (int rt = rank; rt < I.nrt; rt += span)
+      for (size_t o = rt * tileT + threadIdx.x; o < zmin(NT, (rt + 1) * tileT); o += kBThreads) {
+        const int r = (int)(o / T);
+        const double corr = I.self_term ? (st / 4.0) * I.g[r] * I.R[o] * I.R[o] : 0.0;
+        b[o] = CT((st / 2.0) * I.R[o] * I.hz[r] - I.theta - corr);
+      }
+  }
+  for (int rt = rank; rt < I.nrt; rt += span)
+    for (size_t o = rt * tileT + threadIdx.x; o < zmin(NT, (rt + 1) * tileT); o += kBThreads) {
+      const int r = (int)(o / T), t = (int)(o % T);
+      const uint64_t key = run_key(I.seed, (uint64_t)I.inst, (uint64_t)t, (uint64_t)a.outer);
+      const CT c0 = CT(initial_amplitude(key, (uint64_t)r, I.init_kind, I.init_scale));
+      c[o] = c0;
+      e[o] = CT(1);
+      const CT Rr = CT(I.R[o]);
+      bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp,
+                              ((I.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
     }
-  }
-  for (size_t o = threadIdx.x; o < NT; o += kBThreads) {
-    const int r = (int)(o / T), t = (int)(o % T);
-    const uint64_t key = run_key(I.seed, (uint64_t)I.inst, (uint64_t)t, (uint64_t)a.outer);
-    const CT c0 = CT(initial_amplitude(key, (uint64_t)r, I.init_kind, I.init_scale));
-    c[o] = c0;
-    e[o] = CT(1);
-    const CT Rr = CT(I.R[o]);
-    bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp, ((I.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
-  }
-  fence_proxy_async_global();
-  __syncthreads();
+  ok = run_sync(span, ok, vote, vpar);
   // ---- Euler steps
   const CT dt = CT(I.dt), beta = CT(I.beta), tau = CT(I.tau), Kj = CT(I.Kj);
   CT* Xc = I.X1;
   CT* Xn = I.X0;
-  for (int n = 0; n < I.n_steps && ok; ++n) {
+  for (int n = 0; n < steps && ok; ++n) {
     const CT p = pump_at<CT>(n, I.n_steps, I.pump_kind, I.p0, I.p1, I.p_thr, I.d, I.dt, I.t0, I.width);
-    const bool last = (n + 1 == I.n_steps);
-    for (int rt = 0; rt < I.nrt && ok; ++rt) {
+    const bool last = (n + 1 == steps);
+    for (int rt = rank; rt < I.nrt && ok; rt += span) {
       constexpr int kU = 8;
       const int ne = kRT * T;
       if constexpr (TC) {
@@ -567,8 +611,8 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
             }
           }
         }
-        ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty,
-                                                                      gctr, issued, xsi, pre));
+        ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, span, ring, slot, P, full,
+                                                                      empty, gctr, issued, xsi, pre));
         if (tid < kUT) {
 #pragma unroll
           for (int u = 0; u < kU; ++u) {
@@ -592,8 +636,8 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
         __syncthreads();
         continue;
       }
-      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, ring, slot, P, full, empty, gctr,
-                                                                    issued, xsi, pre));
+      ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, Xc, rt, span, ring, slot, P, full, empty,
+                                                                    gctr, issued, xsi, pre));
       // the row tile's update, kU elements per thread at a time: every load of
       // the state (global memory, L2-resident) is issued before the first
       // update, so the L2 latency is paid once per kU elements (measured on
@@ -635,8 +679,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, unsigned ch
       }
       __syncthreads();
     }
-    fence_proxy_async_global();
-    __syncthreads();
+    ok = run_sync(span, ok, vote, vpar);
     CT* tmp = Xc; Xc = Xn; Xn = tmp;
   }
   return ok;
@@ -651,7 +694,9 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
   uint64_t* full =
       reinterpret_cast<uint64_t*>(smem_raw + (size_t)a.slots * slot + b_part_bytes(a.twp, sizeof(CT), PAIR));
   uint64_t* empty = full + a.slots;
-  __shared__ int s_next;
+  __shared__ int s_next;   // this CTA's own pops
+  __shared__ int s_bcast;  // rank 0: the cluster's pops (read by every CTA of the cluster)
+  __shared__ int s_vote[2];
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.slots; ++i) {
       mbar_init(full + i, 1);
@@ -660,23 +705,78 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
     fence_mbar_init();
   }
   __syncthreads();
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
   unsigned gctr = 0;
+  unsigned vpar = 0;
   unsigned issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // producer: 1 + last ring use issued per slot
   bool ok = true;
+  // The large problems come first in the queue: while the cluster's pops return
+  // large problems it runs them together; the first small one goes to rank 0,
+  // and from then on every CTA pops and runs small problems alone.
+  bool together = a.n_large > 0;
   while (ok) {
-    if (threadIdx.x == 0) s_next = ld_volatile(a.err) != 0 ? a.n : atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int qi = s_next;
-    __syncthreads();
-    if (qi >= a.n) break;
+    int qi;
+    if (together) {
+      cl.sync();  // every CTA has read the previous pop
+      if (rank == 0 && threadIdx.x == 0) s_bcast = ld_volatile(a.err) != 0 ? a.n : atomicAdd(a.queue, 1);
+      cl.sync();
+      qi = *cl.map_shared_rank(&s_bcast, 0);
+      if (qi >= a.n) break;
+      if (qi < a.n_large) {
+        const BInst<CT> I = a.insts[a.order[qi]];
+        ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, rank, a.cc, ring, slot, P, full, empty, gctr, issued, s_vote,
+                                                vpar);
+        continue;
+      }
+      together = false;
+      if (rank != 0) continue;  // pops its own next
+    } else {
+      if (threadIdx.x == 0) s_next = ld_volatile(a.err) != 0 ? a.n : atomicAdd(a.queue, 1);
+      __syncthreads();
+      qi = s_next;
+      __syncthreads();
+      if (qi >= a.n) break;
+    }
     const BInst<CT> I = a.insts[a.order[qi]];
-    ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, ring, slot, P, full, empty, gctr, issued);
+    ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, 0, 1, ring, slot, P, full, empty, gctr, issued, s_vote, vpar);
   }
   // After a timeout, let any copy still in flight land before the CTA exits.
   if (!ok && threadIdx.x == kBWarps * 32) {
     for (int s = 0; s < a.slots; ++s)
       if (issued[s] > 0) mbar_wait(full + s, (issued[s] - 1) / a.slots & 1u, a.timeout_cycles);
   }
+  // no CTA leaves while another of its cluster may still read its shared memory
+  cl.sync();
+}
+
+// Ring shape of a launch: column tiles per slot (tps) and slots.  Unless the
+// launch fixes them (L.tps, L.slots), the most column tiles (4, 2, 1) that
+// still leave 3 slots (measured: one 32-column tile per slot leaves too little
+// work between ring handoffs), and as many slots as fit (at most 8).
+inline bool batch_ring(const BatchLaunch& L, int twp, size_t gbytes, size_t cbytes, size_t fixed, size_t cap,
+                       int* tps_out, int* slots_out, size_t* smem_out) {
+  auto need = [&](int tps, int slots) {
+    return (size_t)slots * b_slot_bytes(twp, gbytes, cbytes, tps) + fixed + 2 * (size_t)slots * sizeof(uint64_t);
+  };
+  int tps = L.tps, slots = L.slots;
+  if (tps == 0) {
+    for (tps = 4; tps >= 1; tps >>= 1) {
+      slots = 8;
+      while (slots > 2 && need(tps, slots) > cap) --slots;
+      if (slots >= 3 || tps == 1) break;
+    }
+    if (L.slots > 0) slots = L.slots;
+  } else if (slots == 0) {
+    slots = 8;
+    while (slots > 2 && need(tps, slots) > cap) --slots;
+  }
+  if (tps != 1 && tps != 2 && tps != 4) return false;
+  if (slots < 2 || slots > 8 || need(tps, slots) > cap) return false;
+  *tps_out = tps;
+  *slots_out = slots;
+  *smem_out = need(tps, slots);
+  return true;
 }
 
 template <typename GT, typename CT, int MR, bool PAIR, bool TC = false>
@@ -693,18 +793,12 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const size_t fixed = b_part_bytes(twp, sizeof(CT), PAIR);
   const size_t cap = (size_t)optin - fa.sharedSizeBytes;
-  // column tiles per slot: the most (4, 2, 1) that still leave 3 slots (measured:
-  // one 32-column tile per slot leaves too little work between ring handoffs)
-  int tps = 4, slots = 0;
-  size_t slot = 0;
-  for (; tps >= 1; tps >>= 1) {
-    slot = b_slot_bytes(twp, sizeof(GT), sizeof(CT), tps);
-    slots = 8;
-    while (slots > 2 && (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t) > cap) --slots;
-    if (slots >= 3 || tps == 1) break;
-  }
-  const size_t smem = (size_t)slots * slot + fixed + 2 * slots * sizeof(uint64_t);
-  if (smem > cap) return cudaErrorInvalidConfiguration;
+  int tps = 0, slots = 0;
+  size_t smem = 0;
+  if (!batch_ring(L, twp, sizeof(GT), sizeof(CT), fixed, cap, &tps, &slots, &smem))
+    return cudaErrorInvalidConfiguration;
+  const int cc = L.cc > 0 ? L.cc : 1;
+  if (cc != 1 && cc != 2 && cc != 4 && cc != 8) return cudaErrorInvalidValue;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   BArgs<CT> a;
@@ -719,10 +813,35 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.outer = L.outer;
   a.err = L.err;
   a.timeout_cycles = L.timeout_cycles;
+  a.cc = cc;
+  a.n_large = cc > 1 ? std::min(L.n_large, L.n) : 0;
+  a.step_cap = L.step_cap;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kBThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // clusters: no more than are resident at once (the rest would only wait for
+  // the queue to drain), nor than the queue has items for
+  int resident = L.ctas;  // one CTA per SM
+  if (cc > 1) {
+    cfg.gridDim = dim3(cc);
+    e = cudaOccupancyMaxActiveClusters(&resident, fn, &cfg);
+    if (e != cudaSuccess) return e;
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int items = a.n_large + (L.n - a.n_large + cc - 1) / cc;
+  const int nclu = std::max(1, std::min({resident, std::max(1, L.ctas / cc), items}));
+  cfg.gridDim = dim3(nclu * cc);
   e = cudaMemsetAsync(L.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  euler_batch_kernel<GT, CT, MR, PAIR, TC><<<std::min(L.n, L.ctas), kBThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 template <typename GT, typename CT>
@@ -751,6 +870,8 @@ cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace
+
+int batch_row_tiles(int64_t N) { return (int)((N + kRT - 1) / kRT); }
 
 size_t batch_inst_bytes() {
   return sizeof(BInst<double>) > sizeof(BInst<float>) ? sizeof(BInst<double>) : sizeof(BInst<float>);

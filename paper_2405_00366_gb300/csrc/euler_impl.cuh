@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -434,6 +435,15 @@ cudaError_t launch_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int ou
   return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
+// The fields that identify a plan among the planner's candidates.
+inline std::string plan_tag(const Plan& p) {
+  const int v[] = {p.C, p.NC, p.RPC, p.RPC_pad, p.ORW, p.kq, p.kch, p.slots, p.RW, p.RG, p.MR, p.WK, p.ldg,
+                   (int)p.stream, (int)p.wide, (int)p.tc, (int)p.tc5};
+  std::string s;
+  for (int x : v) s += (s.empty() ? "" : " ") + std::to_string(x);
+  return s;
+}
+
 // Autotuner: time the kTuneCands cheapest candidate splits of the cost model,
 // plus the cheapest of each kernel form (FMA, mma.sync, tcgen05) not among them, on
 // this GPU (kTuneSteps Euler steps each, twice, CUDA events on the problem's
@@ -512,8 +522,30 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
                                       prm.readout == CS_READOUT_BEST ? 5 : 4);
     if (e != cudaSuccess) return e;
     if (prm.autotune && cands.size() > 1) {
-      e = autotune_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands, &pl);
-      if (e != cudaSuccess) return e;
+      // a choice persisted by an earlier process counts if it is still one of
+      // the candidates; otherwise time them
+      const std::string dkey = "euler|" + tune_device_tag(P.device) + "|p" + std::to_string(prm.precision) + "|N" +
+                               std::to_string(P.N) + "|T" + std::to_string(S.trials) + "|h" +
+                               std::to_string(prm.cluster_size) + "|c" + std::to_string(prm.max_ctas) + "|s" +
+                               std::to_string(prm.stream_g) + "|f" + std::to_string(prm.tensor_form) + "|r" +
+                               std::to_string(prm.readout);
+      std::string stored;
+      bool found = false;
+      if (tune_lookup(dkey, &stored))
+        for (const auto& c : cands)
+          if (plan_tag(c.second) == stored) {
+            pl = c.second;
+            found = true;
+            break;
+          }
+      if (found) {
+        tune_note(false);
+      } else {
+        e = autotune_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, cands, &pl);
+        if (e != cudaSuccess) return e;
+        tune_note(true);
+        tune_store(dkey, plan_tag(pl));
+      }
     }
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = pl;

@@ -135,8 +135,26 @@ struct BatchLaunch {
   int outer;
   int* err;
   long long timeout_cycles;
-  int ctas;            // CTAs to launch (one per SM)
+  int ctas;            // CTAs to launch at most (one per SM)
+  int cc = 1;          // CTAs per cluster (1, 2, 4 or 8)
+  int n_large = 0;     // the first n_large problems (in processing order) are each run by a whole cluster
+  int tps = 0;         // column tiles per ring slot (1, 2, 4; 0 = the launch's default)
+  int slots = 0;       // ring slots (2..8; 0 = as many as fit)
+  int step_cap = 0;    // > 0: at most this many Euler steps per run (tuning runs)
 };
+// Ring shape and cluster size of a batched launch (the batch autotuner's choice).
+struct BatchShape {
+  int cc = 1, tps = 0, slots = 0, span_rt = 0;  // span_rt: problems with at least this many row tiles span a cluster
+};
+// Persisted autotuner choices (tune_cache.cu): the device part of every key,
+// lookup, store (memory and the cache file), and a count of timed tunings
+// (timed = true) or choices taken from the file (timed = false).
+std::string tune_device_tag(int device);
+bool tune_lookup(const std::string& key, std::string* value);
+void tune_store(const std::string& key, const std::string& value);
+void tune_note(bool timed);
+// Row tiles of a problem of N rows in the batched kernel's tiling.
+int batch_row_tiles(int64_t N);
 size_t batch_inst_bytes();
 void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
                      int inst);

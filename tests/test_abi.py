@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -91,3 +92,15 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.cs_solve(None, ctypes.byref(p), 1) == cs.CS_EINVAL
     assert lib.cs_result(None, None, None, None, None) == cs.CS_EINVAL
     lib.cs_problem_destroy(None)
+
+
+def test_tune_info_reports_cache_path(lib, tmp_path):
+    """cs_tune_info answers on the host: no tunings yet and the cache file named by
+    CS_TUNE_CACHE (read in a fresh process, which loads the file on first use)."""
+    cache = tmp_path / "sub" / "tune.txt"
+    code = ("import sys; sys.path.insert(0, sys.argv[1]); from paper_2405_00366_gb300 import cs; "
+            "print(cs.cs_tune_info())")
+    env = dict(os.environ, CS_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == repr((0, 0, str(cache)))

@@ -7,6 +7,11 @@ oracle's supports exactly; BF16/FP16 storage of G_off changes the trajectories,
 so those are gated on the final support and the RMSE (within 1e-3 of the
 oracle's) only.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 import torch
@@ -272,3 +277,105 @@ def test_batch_argument_checks():
             cs.cs_solve_batch([h], [prm, prm], 2)
     finally:
         cs.cs_problem_destroy(h)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_cluster_span_matches_oracle(precision):
+    """Large problems of a batch run by whole clusters (cluster_size 2 and 4: the
+    problems with at least two 128-row tiles per CTA span the cluster, the others
+    run on one CTA): every result is bitwise the one of clusters of one CTA (each
+    row tile's product and update are the same arithmetic wherever it runs), the
+    stats name the CTAs that ran each problem, and the supports match the oracle's
+    exactly."""
+    insts = uneven([1000, 520, 130, 40], seed=41)  # 8, 5, 2 and 1 row tiles
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300, precision=precision, seed=3)
+    T = 4
+    base = run_batch(insts, w, T, cluster_size=1)
+    for cc in (2, 4):
+        g = run_batch(insts, w, T, cluster_size=cc)
+        for i, inst in enumerate(insts):
+            np.testing.assert_array_equal(g[i]["sigmas"], base[i]["sigmas"])
+            np.testing.assert_array_equal(g[i]["R"], base[i]["R"])
+            nrt = (inst.N + 127) // 128
+            assert g[i]["stats"][8] == (cc if nrt >= 2 * cc else 1)
+    for i, inst in enumerate(insts):
+        r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)
+        np.testing.assert_array_equal(base[i]["sigmas"], r["sigmas"])
+        tol = 1e-9 if precision == "fp64" else 1e-5
+        np.testing.assert_allclose(base[i]["x_hat"], r["x_hat"], rtol=0, atol=tol)
+
+
+def test_batch_large_instance_bf16_spans_cluster_matches_oracle():
+    """A batch in the shape of the uneven workload with an instance above N = 2048
+    (N = 2304, alpha = 0.7, a = 0.05, 16 trials, BF16 G_off on the tensor cores)
+    beside a small one: with clusters of 8 the large instance is run by all 8 CTAs
+    (18 row tiles) and the result is bitwise that of clusters of one; run to
+    settled amplitudes (3 x 1000 steps) the large instance meets the
+    reduced-precision gate (kept support identical, RMSE within 1e-3) against the
+    oracle on the same BF16-rounded G_off."""
+    big = cs_inputs.random_instance(2304, int(0.7 * 2304), int(0.05 * 2304), 0.01, 0.03, seed=61)
+    small = cs_inputs.random_instance(300, 210, 15, 0.01, 0.03, seed=62)
+    insts = [big, small]
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=1000, precision="bf16", seed=5)
+    g8 = run_batch(insts, w, 16, cluster_size=8)
+    g1 = run_batch(insts, w, 16, cluster_size=1)
+    assert g8[0]["stats"][8] == 8 and g8[1]["stats"][8] == 1
+    for a, b in zip(g8, g1):
+        assert a["stats"][10] == 4
+        np.testing.assert_array_equal(a["sigmas"], b["sigmas"])
+        np.testing.assert_array_equal(a["R"], b["R"])
+    r = oracle_solve_rounded(big, w, 16, 0, "bf16")
+    np.testing.assert_array_equal(g8[0]["sigma"], r["sigma"])
+    assert abs(oracle.rmse(g8[0]["x_hat"], big.x0) - oracle.rmse(r["x_hat"], big.x0)) <= 1e-3
+
+
+_TUNE_SCRIPT = r"""
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+import cs_inputs
+from paper_2405_00366_gb300 import cs
+insts = [cs_inputs.random_instance(N, int(0.6 * N), N // 10, 0.01, 0.03, seed=70 + k)
+         for k, N in enumerate([1100, 600, 250])]
+w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=1, n_steps=100, precision="bf16", seed=1, autotune=1)
+hs = [cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam) for i in insts]
+cs.cs_solve_batch(hs, cs.params_from_workload(w), 16)
+out = {"batch": [cs.cs_result(h)[0].tolist() for h in hs]}
+wf = dict(w, precision="fp32")
+cs.cs_solve(hs[0], cs.params_from_workload(wf), 16)
+x, s, E, st, _ = cs.cs_result(hs[0])
+out["single"] = x.tolist()
+out["plan"] = [float(st[8]), float(st[9]), float(st[10])]
+for h in hs:
+    cs.cs_problem_destroy(h)
+t, d, path = cs.cs_tune_info()
+out.update(tunings=t, disk_hits=d, path=path)
+print(json.dumps(out))
+"""
+
+
+def test_tune_cache_persists_across_processes(tmp_path):
+    """With autotune = 1 the first process times the batch shapes and the single
+    solve's splits and appends its choices to the tuning cache file
+    (CS_TUNE_CACHE); a second process reads them back instead of timing, and both
+    give the same plans and results."""
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, CS_TUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def run():
+        r = subprocess.run([sys.executable, "-c", _TUNE_SCRIPT, root], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    first = run()
+    assert first["path"] == str(cache)
+    assert first["tunings"] >= 1 and first["disk_hits"] == 0
+    lines = cache.read_text().splitlines()
+    assert len(lines) == first["tunings"] and any(l.startswith("batch|") for l in lines)
+    second = run()
+    assert second["tunings"] == 0 and second["disk_hits"] == first["tunings"]
+    assert second["plan"] == first["plan"]
+    assert second["batch"] == first["batch"] and second["single"] == first["single"]
