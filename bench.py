@@ -788,6 +788,7 @@ def main():
                 "h2d_bytes_per_step": (inst.A.size + inst.y.size) * 8,
                 "d2h_bytes_per_step": inst.N * 8 + inst.N + 8 + cs.CS_STATS_LEN * 8},
         "gpu_launches": launches,
+        "host_submissions_per_step": int(tm[0][4]),
         "breakdown_ms_per_step": {k: v / args.steps for k, v in zip(["gram", "euler", "refit", "other"], phase_ms)},
         "clocks": ck,
     }

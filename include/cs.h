@@ -250,12 +250,16 @@ cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g);
 
 /* Device time of the work queued by the last cs_problem_create and the last
  * cs_solve on this problem, from CUDA events recorded on the problem's stream
- * around each group of launches, summed per group into ms[CS_TIMING_LEN]:
+ * around each group of launches (event-record nodes inside the solve's graph),
+ * summed per group into ms[0..3]:
  *   [0] Gram formation  [1] Euler kernels (all outer iterations)
  *   [2] refits          [3] the rest (coupling copy, initial R, objective, selection)
- * and, in *launches, how many kernels the library launched for them.  Waits for
- * the stream.  Host pointers, either may be NULL. */
-#define CS_TIMING_LEN 4
+ *   [4] (a count, not a time) host submissions of the last cs_solve's device
+ *       work: the kernels it queued directly (coupling copy, initial R) plus
+ *       one CUDA graph launch that holds every outer iteration and the objective
+ * and, in *launches, how many kernels the library launched for them, inside
+ * the graph or not.  Waits for the stream.  Host pointers, either may be NULL. */
+#define CS_TIMING_LEN 5
 cs_status cs_problem_timing(cs_problem* p, double* ms, int64_t* launches);
 
 /* Per-trial objective E_t = 1/2 ||y - A (sigma_t o R_t)||^2 + lambda |sigma_t| in

@@ -241,11 +241,12 @@ def cs_problem_gram(problem):
     return G, hz, g
 
 
-CS_TIMING_LEN = 4
+CS_TIMING_LEN = 5
 
 
 def cs_problem_timing(problem):
-    """(ms per group [gram, euler, refit, other], kernel launches) of the last create + solve."""
+    """(ms per group [gram, euler, refit, other] followed by the count of host
+    submissions of the last solve, kernel launches) of the last create + solve."""
     ms = np.zeros(CS_TIMING_LEN)
     n = ctypes.c_int64()
     _check(lib().cs_problem_timing(problem, ms.ctypes.data, ctypes.byref(n)))

@@ -20,6 +20,8 @@ struct cs_problem {
   std::vector<cudaEvent_t> events;
   std::vector<int> cats;
   int n_marks = 0, n_create_marks = 0;
+  bool capturing = false;     // the solve's outer loop is being captured into a graph
+  int64_t submissions = 0;    // host submissions of the last solve's device work (launches outside the graph + 1)
 };
 
 namespace cs {
@@ -235,7 +237,10 @@ cudaError_t mark(cs_problem* p, int cat, bool begin) {
     p->cats[k] = cat;
     ++p->n_marks;
   }
-  return cudaEventRecord(p->events[2 * k + (begin ? 0 : 1)], p->P.stream);
+  // (inside a stream capture the record becomes an event-record node of the graph)
+  return p->capturing ? cudaEventRecordWithFlags(p->events[2 * k + (begin ? 0 : 1)], p->P.stream,
+                                                 cudaEventRecordExternal)
+                      : cudaEventRecord(p->events[2 * k + (begin ? 0 : 1)], p->P.stream);
 }
 
 }  // namespace
@@ -281,18 +286,21 @@ RefitJob make_job(const ProblemDev& P, const SolveDev& S, const cs_params& prm) 
 
 using namespace cs;
 
-// Executable batch graphs stay alive until their stream has run them; finished
-// ones are destroyed at the next batched solve (and at unload).
+// Executable graphs (one per cs_solve and per cs_solve_batch) stay alive until
+// they have run: each is kept with an event recorded after its launch, and the
+// finished ones are destroyed at the next solve.  (The event, not the stream,
+// tells: a caller may destroy its stream before the next solve.)
 namespace {
 std::mutex g_graph_mu;
-std::vector<std::pair<cudaStream_t, cudaGraphExec_t>> g_graphs;
+std::vector<std::pair<cudaEvent_t, cudaGraphExec_t>> g_graphs;
 
-void reap_batch_graphs() {
+void reap_graphs() {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   for (size_t i = 0; i < g_graphs.size();) {
-    if (cudaStreamQuery(g_graphs[i].first) != cudaErrorNotReady) {
+    if (cudaEventQuery(g_graphs[i].first) != cudaErrorNotReady) {
       cudaGetLastError();
       cudaGraphExecDestroy(g_graphs[i].second);
+      cudaEventDestroy(g_graphs[i].first);
       g_graphs[i] = g_graphs.back();
       g_graphs.pop_back();
     } else {
@@ -301,9 +309,24 @@ void reap_batch_graphs() {
   }
 }
 
-void keep_batch_graph(cudaStream_t st, cudaGraphExec_t exec) {
+// Launch `exec` on `st` and keep it until it has run; on failure the graph is
+// destroyed here.
+cudaError_t launch_and_keep(cudaGraphExec_t exec, cudaStream_t st) {
+  cudaError_t e = cudaGraphLaunch(exec, st);
+  cudaEvent_t done = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(done, st);
+  if (e != cudaSuccess) {
+    // not launched, or launched without a completion event: wait for the
+    // stream before destroying the graph
+    cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    if (done) cudaEventDestroy(done);
+    return e;
+  }
   std::lock_guard<std::mutex> lk(g_graph_mu);
-  g_graphs.emplace_back(st, exec);
+  g_graphs.emplace_back(done, exec);
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -398,6 +421,47 @@ cs_status cs_problem_create(const double* A, const double* y, int64_t M, int64_t
   return CS_OK;
 }
 
+// The outer loop of Algorithm 1 for one problem (every CIM run, readout,
+// refit and recording) and the final objective and selection, queued on
+// P.stream (the capture stream while cs_solve captures them into its graph).
+static cs_status queue_outer_loop(cs_problem* p, const cs_params* prm, long long timeout_cycles) {
+  ProblemDev& P = p->P;
+  SolveDev& S = p->S;
+  for (int i = 0; i < prm->n_outer; ++i) {
+    const double eta = eta_at(i, *prm, P.lambda);
+    CS_CUDA(mark(p, TM_EULER, true), "event");
+    cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
+    if (e != cudaSuccess)
+      return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
+    if (prm->readout == CS_READOUT_BEST) {
+      CS_CUDA(launch_readout(S.e_hist, S.s_hist, S.sigma, (int)P.N, S.trials, prm->n_steps, S.plan_ctas, P.stream),
+              "readout launch");
+      P.launches += 1;
+    }
+    CS_CUDA(mark(p, TM_EULER, false), "event");
+    CS_CUDA(mark(p, TM_REFIT, true), "event");
+    const RefitPlan rplan{prm->refit, prm->jacobi_iters, (int)P.N, P.num_sms, S.R};
+    CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream, &rplan),
+            "refit launch");
+    if (refit_grid_wide(&rplan, 1, S.trials, S.work_blocks, S.work_stride)) P.launches += prm->jacobi_iters - 1;
+    if (prm->record_outer) {
+      const size_t nt = (size_t)P.N * S.trials;
+      CS_CUDA(cudaMemcpyAsync(S.sig_outer + (size_t)i * nt, S.sigma, nt, cudaMemcpyDeviceToDevice, P.stream),
+              "record outer support");
+      CS_CUDA(cudaMemcpyAsync(S.R_outer + (size_t)i * nt, S.R, nt * sizeof(double), cudaMemcpyDeviceToDevice,
+                              P.stream),
+              "record outer signal");
+    }
+    CS_CUDA(mark(p, TM_REFIT, false), "event");
+    P.launches += 2;
+  }
+  CS_CUDA(mark(p, TM_OTHER, true), "event");
+  CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream, S.err4), "finish launch");
+  CS_CUDA(mark(p, TM_OTHER, false), "event");
+  P.launches += 4;  // energy, selection, error against FP64 and its ratio
+  return CS_OK;
+}
+
 cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   if (!p) return fail(CS_EINVAL, "problem is NULL");
   cs_status st = check_params(prm, trials);
@@ -427,43 +491,52 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
     CS_CUDA(launch_init_R(S.job, 1, S.trials, P.num_sms, P.stream), "init R");
     P.launches += 1;
   }
-  CS_CUDA(mark(p, TM_OTHER, false), "event");
-  for (int i = 0; i < prm->n_outer; ++i) {
-    const double eta = eta_at(i, *prm, P.lambda);
-    CS_CUDA(mark(p, TM_EULER, true), "event");
-    cudaError_t e = launch_euler(P, S, *prm, i, eta, timeout_cycles);
+  // the Euler plan of this shape (autotuning, if asked, times its candidates
+  // here) and its streamed tiles, so that the loop below is stream work only
+  {
+    const cudaError_t e = launch_euler(P, S, *prm, 0, eta_at(0, *prm, P.lambda), timeout_cycles, true);
     if (e == cudaErrorInvalidConfiguration)
       return fail(CS_EINVAL, prm->tensor_form >= 2
                                  ? "tensor_form >= 2: no tensor-core work split of that kind for this shape and trials"
                                  : "N too large for the on-chip Euler kernel at this precision");
     if (e != cudaSuccess)
-      return fail(CS_ECUDA, std::string("euler launch: ") + cudaGetErrorString(e) + " at " + euler_last_call());
-    if (prm->readout == CS_READOUT_BEST) {
-      CS_CUDA(launch_readout(S.e_hist, S.s_hist, S.sigma, (int)P.N, S.trials, prm->n_steps, S.plan_ctas, P.stream),
-              "readout launch");
-      P.launches += 1;
-    }
-    CS_CUDA(mark(p, TM_EULER, false), "event");
-    CS_CUDA(mark(p, TM_REFIT, true), "event");
-    const RefitPlan rplan{prm->refit, prm->jacobi_iters, (int)P.N, P.num_sms, S.R};
-    CS_CUDA(launch_refit(S.job, 1, S.trials, S.work, S.work_stride, S.work_blocks, i, P.stream, &rplan),
-            "refit launch");
-    if (refit_grid_wide(&rplan, 1, S.trials, S.work_blocks, S.work_stride)) P.launches += prm->jacobi_iters - 1;
-    if (prm->record_outer) {
-      const size_t nt = (size_t)P.N * S.trials;
-      CS_CUDA(cudaMemcpyAsync(S.sig_outer + (size_t)i * nt, S.sigma, nt, cudaMemcpyDeviceToDevice, P.stream),
-              "record outer support");
-      CS_CUDA(cudaMemcpyAsync(S.R_outer + (size_t)i * nt, S.R, nt * sizeof(double), cudaMemcpyDeviceToDevice,
-                              P.stream),
-              "record outer signal");
-    }
-    CS_CUDA(mark(p, TM_REFIT, false), "event");
-    P.launches += 2;
+      return fail(CS_ECUDA, std::string("euler plan: ") + cudaGetErrorString(e) + " at " + euler_last_call());
   }
-  CS_CUDA(mark(p, TM_OTHER, true), "event");
-  CS_CUDA(launch_finish(S.job, 1, S.trials, P.num_sms, P.stream, S.err4), "finish launch");
   CS_CUDA(mark(p, TM_OTHER, false), "event");
-  P.launches += 4;  // energy, selection, error against FP64 and its ratio
+  const int64_t eager = P.launches - 2;  // kernels queued directly (coupling copy, initial R)
+  // Every outer iteration and the objective are captured into one CUDA graph
+  // and submitted to the problem's stream as a single launch (captured on a
+  // private stream: the problem's stream may be the legacy default stream).
+  reap_graphs();
+  cudaStream_t user = P.stream, cap = nullptr;
+  CS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create the capture stream");
+  {
+    const cudaError_t eb = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (eb != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      CS_CUDA(eb, "begin graph capture");
+    }
+  }
+  P.stream = cap;
+  p->capturing = true;
+  st = queue_outer_loop(p, prm, timeout_cycles);
+  p->capturing = false;
+  P.stream = user;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (st != CS_OK || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != CS_OK) return st;
+    CS_CUDA(ec, "end graph capture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CS_CUDA(e, "instantiate the solve graph");
+  CS_CUDA(launch_and_keep(exec, user), "launch the solve graph");
+  p->submissions = eager + 1;
   S.has_outer = prm->record_outer != 0;
   S.done = true;
   return CS_OK;
@@ -733,7 +806,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   // objective are captured into one CUDA graph and submitted as a single launch.
   // (captured on a private stream: the problems' stream may be the legacy
   // default stream, which cannot be captured; the graph then runs on theirs)
-  reap_batch_graphs();
+  reap_graphs();
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
   CS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create the capture stream");
@@ -789,10 +862,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   CS_CUDA(e, "instantiate the batch graph");
-  e = cudaGraphLaunch(exec, stream);
-  if (e != cudaSuccess) cudaGraphExecDestroy(exec);
-  CS_CUDA(e, "launch the batch graph");
-  keep_batch_graph(stream, exec);
+  CS_CUDA(launch_and_keep(exec, stream), "launch the batch graph");
   dev_free(d_insts, stream);
   dev_free(d_order, stream);
   dev_free(d_queue, stream);
@@ -887,12 +957,13 @@ cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g) {
 cs_status cs_problem_timing(cs_problem* p, double* ms, int64_t* launches) {
   if (!p) return fail(CS_EINVAL, "problem is NULL");
   CS_CUDA(cudaStreamSynchronize(p->P.stream), "synchronize");
-  double acc[CS_TIMING_LEN] = {0, 0, 0, 0};
+  double acc[CS_TIMING_LEN] = {0, 0, 0, 0, 0};
   for (int k = 0; k < p->n_marks; ++k) {
     float t = 0.f;
     CS_CUDA(cudaEventElapsedTime(&t, p->events[2 * k], p->events[2 * k + 1]), "event time");
     acc[p->cats[k]] += t;
   }
+  acc[4] = (double)p->submissions;
   if (ms) std::memcpy(ms, acc, sizeof(acc));
   if (launches) *launches = p->P.launches;
   return CS_OK;

@@ -8,26 +8,26 @@ namespace cs {
 thread_local const char* g_where = "";
 
 cudaError_t launch_euler_fp64(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                          long long timeout_cycles);
+                          long long timeout_cycles, bool plan_only);
 cudaError_t launch_euler_fp32(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                          long long timeout_cycles);
+                          long long timeout_cycles, bool plan_only);
 cudaError_t launch_euler_bf16(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                          long long timeout_cycles);
+                          long long timeout_cycles, bool plan_only);
 cudaError_t launch_euler_fp16(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                          long long timeout_cycles);
+                          long long timeout_cycles, bool plan_only);
 cudaError_t launch_euler_fp8(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                          long long timeout_cycles);
+                          long long timeout_cycles, bool plan_only);
 
 const char* euler_last_call() { return g_where; }
 
 cudaError_t launch_euler(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                         long long timeout_cycles) {
+                         long long timeout_cycles, bool plan_only) {
   switch (prm.precision) {
-    case CS_P_FP64: return launch_euler_fp64(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_FP32: return launch_euler_fp32(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_BF16: return launch_euler_bf16(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_FP16: return launch_euler_fp16(P, S, prm, outer, eta, timeout_cycles);
-    case CS_P_FP8: return launch_euler_fp8(P, S, prm, outer, eta, timeout_cycles);
+    case CS_P_FP64: return launch_euler_fp64(P, S, prm, outer, eta, timeout_cycles, plan_only);
+    case CS_P_FP32: return launch_euler_fp32(P, S, prm, outer, eta, timeout_cycles, plan_only);
+    case CS_P_BF16: return launch_euler_bf16(P, S, prm, outer, eta, timeout_cycles, plan_only);
+    case CS_P_FP16: return launch_euler_fp16(P, S, prm, outer, eta, timeout_cycles, plan_only);
+    case CS_P_FP8: return launch_euler_fp8(P, S, prm, outer, eta, timeout_cycles, plan_only);
     default: return cudaErrorInvalidValue;
   }
 }

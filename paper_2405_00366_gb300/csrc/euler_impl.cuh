@@ -493,7 +493,7 @@ cudaError_t autotune_plan(ProblemDev& P, SolveDev& S, const cs_params& prm, int 
 
 template <typename GT, typename CT>
 cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer, double eta,
-                         long long timeout_cycles) {
+                         long long timeout_cycles, bool plan_only) {
   // plans depend only on the shape, the caller's limits and the device; one
   // cache per process (so every thread and every solve of a shape agrees)
   struct Key {
@@ -549,6 +549,14 @@ cudaError_t launch_typed(ProblemDev& P, SolveDev& S, const cs_params& prm, int o
     }
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = pl;
+  }
+  if (plan_only) {
+    if (pl.stream) {
+      const cudaError_t e = ensure_cluster_tiles<GT>(P, prm.precision, pl);
+      if (e != cudaSuccess) g_where = "streamed G_off tiles";
+      return e;
+    }
+    return cudaSuccess;
   }
   return launch_plan<GT, CT>(P, S, prm, outer, eta, timeout_cycles, pl, prm.n_steps, true);
 }

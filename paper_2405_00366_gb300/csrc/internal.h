@@ -169,8 +169,11 @@ cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);
 // Launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gram(const ProblemDev& P);
 cudaError_t launch_store_coupling(ProblemDev& P, int precision);
+// plan_only: choose (and cache) the plan, autotuning if asked, and build its
+// streamed tiles, without launching; a later launch of the shape is then a pure
+// stream operation (capturable into a CUDA graph).
 cudaError_t launch_euler(ProblemDev& P, SolveDev& S, const cs_params& prm, int outer,
-                         double eta, long long timeout_cycles);
+                         double eta, long long timeout_cycles, bool plan_only = false);
 const char* euler_last_call();  // the CUDA call the last failing Euler launch stopped at
 cudaError_t launch_init_R(const RefitJob* jobs, int njobs, int T, int num_sms, cudaStream_t st);
 // What the host knows of a single problem's refit, for launch_refit to pick

@@ -316,6 +316,35 @@ def test_barrier_timeout_is_reported_and_context_survives():
 
 
 # ------------------------------------------------------------------ s2: error against FP64 per result
+def test_solve_is_one_graph_launch():
+    """cs_solve queues the coupling copy and the initial R directly and every outer
+    iteration (Euler launch, refit) plus the objective as one CUDA graph: a second
+    solve of the same problem reports two host submissions, the per-phase device
+    times come from event nodes inside the graph, the two solves agree bitwise and
+    their supports are the oracle's."""
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=3, n_steps=300)
+    inst = cs_inputs.workload_instance(w)
+    prm = cs.params_from_workload(w)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        cs.cs_solve(h, prm, 2)
+        x1, s1, E1, st1, _ = cs.cs_result(h)
+        (ms1, n1) = cs.cs_problem_timing(h)
+        cs.cs_solve(h, prm, 2)
+        x2, s2, E2, st2, _ = cs.cs_result(h)
+        (ms2, n2) = cs.cs_problem_timing(h)
+    finally:
+        cs.cs_problem_destroy(h)
+    assert ms1[4] in (2, 3) and ms2[4] == 2
+    assert ms2[1] > 0 and ms2[2] > 0 and ms2[3] > 0
+    assert n2 >= 2 + 1 + 3 * 2 + 4  # Gram, initial R, per iteration Euler + refit, objective
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(s1, s2)
+    r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=2)
+    np.testing.assert_array_equal(s2, r["sigma"])
+    np.testing.assert_allclose(x2, r["x_hat"], rtol=0, atol=1e-8)
+
+
 @pytest.mark.parametrize("precision,refit", [("fp64", "exact"), ("fp32", "exact"), ("bf16", "exact"),
                                              ("fp16", "exact"), ("fp32", "jacobi")])
 def test_error_against_fp64_is_reported_per_result(precision, refit):
