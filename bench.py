@@ -14,13 +14,15 @@ sample of the same workload instead.
 
 Two further workloads print their own line (not the default):
   --workload batch_uneven_bf16   one step = one batched solve (cs_solve_batch) of
-      512 uneven instances (N in [256, 1024], alpha in {0.3, 0.5, 0.7}, a in
+      512 uneven instances (N in [256, 4096], alpha in {0.3, 0.5, 0.7}, a in
       {0.05, 0.1, 0.2}, 16 trials, 30 x 2000 steps, BF16 storage of G_off),
       against plain FP32 solves of the same instances one at a time (cs_solve);
-  --workload serve_mix           a Poisson stream (200 requests/s) of 40 requests
-      mixing the single FP64 N=200 shape, the 64-trial N=2000 shape and the
-      uneven BF16 shape 60/30/10, through the continuous-batching server, against
-      the same requests as plain FP32 solves one at a time; p50/p99 latency;
+  --workload serve_mix           60 s Poisson request streams (200 requests/s,
+      beyond one GPU's capacity, and 2 requests/s) mixing the single FP64 N=200
+      shape, the 64-trial N=2000 shape and the uneven BF16 shape 60/30/10 over
+      cached problems, through the continuous-batching server, against the same
+      requests as plain FP32 solves one at a time; achieved against offered
+      rate, p50/p99 latency;
   --workload sweep_random        the paper's random-data experiment: final RMSE
       against sparsity for alpha in {0.6, 0.8} and two noise levels, and the
       RMSE and Hamming loss after every outer iteration, both local fields.
@@ -394,29 +396,54 @@ def run_batch(args):
     return 0
 
 
-def _serve_requests(seed=23, n_req=40, rate=200.0):
-    """(arrival_s, instance, workload dict, trials) of a seeded Poisson request mix."""
+SERVE = dict(window_s=60.0, rates=[200.0, 2.0], mix=[0.6, 0.3, 0.1], pools=[64, 8, 32], slots=16, budget_gb=150,
+             seed=23)
+
+
+def _serve_pools(pools):
+    """The problems requests are drawn from, per shape (config 1, 2, 3 of the
+    benchmark set): (instances, workload dict, trials).  Shape 3 is the uneven
+    batch's distribution (N uniform on [256, 4096], BF16, 16 trials)."""
+    w1 = dict(cs_inputs.WORKLOADS["single_n200_fp64"])
+    w2 = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"])
+    w3 = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], precision="bf16", trials=16)
+    return [([cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=1000 + k) for k in range(pools[0])], w1, 1),
+            ([cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=2000 + k) for k in range(pools[1])],
+             w2, 64),
+            (cs_inputs.uneven_batch(pools[2], 256, 4096, [0.3, 0.5, 0.7], [0.05, 0.1, 0.2], 0.01, 0.03, seed=3000),
+             w3, 16)]
+
+
+def _serve_arrivals(rate, window, mix, pools, seed):
+    """A seeded Poisson stream over `window` seconds: (arrival_s, shape, pool index)."""
     rng = __import__("numpy").random.default_rng(seed)
     t, out = 0.0, []
-    for i in range(n_req):
+    cum = [sum(mix[:i + 1]) for i in range(len(mix))]
+    while True:
         t += float(rng.exponential(1.0 / rate))
+        if t >= window:
+            return out
         u = float(rng.random())
-        if u < 0.6:
-            w = dict(cs_inputs.WORKLOADS["single_n200_fp64"])
-            inst = cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=1000 + i)
-        elif u < 0.9:
-            w = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"])
-            inst = cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=1000 + i)
-        else:
-            w = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], precision="bf16", trials=16)
-            inst = cs_inputs.uneven_batch(1, 256, 1024, [0.3, 0.5, 0.7], [0.05, 0.1, 0.2], 0.01, 0.03,
-                                          seed=1000 + i)[0]
-        out.append((t, inst, w, w["trials"]))
-    return out
+        shape = next((i for i, c in enumerate(cum) if u < c), len(mix) - 1)
+        out.append((t, shape, int(rng.integers(pools[shape]))))
+
+
+def _pct(v, q):
+    if not v:
+        return None
+    v = sorted(v)
+    return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
 
 
 def run_serve(args):
-    """Poisson request mix through the server vs plain FP32 solves one at a time."""
+    """Config 5: a Poisson request stream mixing the config 1-3 shapes 60/30/10,
+    through the server (HBM-budget admission, G formed once per problem and cached,
+    device-resident state) and as plain FP32 solves one at a time in arrival order,
+    over the same 60 s window, at the offered rate of 200 requests/s (far above
+    what one GPU completes: the achieved rate is the server's capacity) and at a
+    sub-saturation rate.  Achieved rate = requests completed within the window /
+    window; latencies over the completed requests (at the sub-saturation rate every
+    request, the stream drained)."""
     import numpy as np
     import torch
 
@@ -425,70 +452,114 @@ def run_serve(args):
 
     if not os.path.exists(cs.LIB_PATH):
         build.build()
-    reqs = _serve_requests()
-    torch.cuda.init()
-    # warm-up: one request of each shape through the server
-    sv = cs.cs_server_create(150 << 30, 16)
+    cfg = SERVE
+    window = args.serve_window or cfg["window_s"]
+    pools = _serve_pools(cfg["pools"])
+    stream = torch.cuda.Stream()
+    handles = [[cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam, stream=stream)
+                for i in insts] for insts, _, _ in pools]
+    prms = [cs.params_from_workload(w) for _, w, _ in pools]
+    prms_plain = [cs.params_from_workload(dict(w, precision="fp32")) for _, w, _ in pools]
+    trials = [T for _, _, T in pools]
+    budget = int(cfg["budget_gb"]) << 30
+
+    # (time.monotonic is the clock of the server's request times)
+    def wait_until(t0, t):
+        while True:
+            d = t - (time.monotonic() - t0)
+            if d <= 0:
+                return
+            time.sleep(min(d, 0.002))
+
+    # warm-up: every problem once through the server (plans, coupling copies in
+    # every precision) and two of each shape as plain solves
+    sv = cs.cs_server_create(budget, cfg["slots"])
     try:
-        seen = {}
-        for _, inst, w, T in reqs:
-            seen.setdefault((inst.N, w["precision"]), (inst, w, T))
-        for inst, w, T in seen.values():
-            tk = cs.cs_server_submit_host(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)
-            cs.cs_server_wait(sv, tk)
-            cs.cs_server_result(sv, tk, inst.N)
+        tks = [cs.cs_server_submit(sv, h, prms[s], trials[s]) for s in range(3) for h in handles[s]]
+        for tk in tks:
+            cs.cs_server_wait(sv, tk, 600000)
+            cs.cs_server_result(sv, tk, 1 << 16)
     finally:
         cs.cs_server_destroy(sv)
+    for s in range(3):
+        for h in handles[s][:2]:
+            cs.cs_solve(h, prms_plain[s], trials[s])
+            cs.cs_result(h)
 
-    with ClockSampler(_env_int("LOCAL_RANK", 0)) as clocks:
-        sv = cs.cs_server_create(150 << 30, 16)
+    def summary(n_offered, lat, in_window, rmse):
+        return dict(offered=n_offered, completed=len(lat), completed_in_window=in_window,
+                    achieved_rate=in_window / window,
+                    latency_ms={"p50": None if not lat else _pct(lat, 0.5) * 1e3,
+                                "p99": None if not lat else _pct(lat, 0.99) * 1e3},
+                    rmse_mean=float(np.mean(rmse)) if rmse else None)
+
+    def serve_arm(arr, drain):
+        sv = cs.cs_server_create(budget, cfg["slots"])
+        tickets = []
+        lat, in_window, rmse = [], 0, []
         try:
-            t0 = time.perf_counter()
-            tickets = []
-            for arr, inst, w, T in reqs:
-                while time.perf_counter() - t0 < arr:
-                    time.sleep(min(0.001, arr - (time.perf_counter() - t0)))
-                tickets.append((time.perf_counter(),
-                                cs.cs_server_submit_host(sv, inst.A, inst.y, inst.lam, cs.params_from_workload(w), T)))
-            lat, rmse = [], []
-            for (ts, tk), (arr, inst, w, T) in zip(tickets, reqs):
-                cs.cs_server_wait(sv, tk)
-                x, s, E, st, tm, _ = cs.cs_server_result(sv, tk, inst.N)
+            t0 = time.monotonic()
+            for t, shape, k in arr:
+                wait_until(t0, t)
+                tickets.append((shape, k, cs.cs_server_submit(sv, handles[shape][k], prms[shape], trials[shape])))
+            wait_until(t0, window)
+            for shape, k, tk in tickets:
+                if drain:
+                    cs.cs_server_wait(sv, tk, 3600000)
+                elif not cs.cs_server_poll(sv, tk):
+                    continue
+                x, sg, E, st, tm, _ = cs.cs_server_result(sv, tk, pools[shape][0][k].N)
                 lat.append(tm[2] - tm[0])
-                rmse.append(oracle.rmse(x, inst.x0))
-            makespan = time.perf_counter() - t0  # first arrival clock to the last result
+                in_window += (tm[2] - t0) <= window
+                rmse.append(oracle.rmse(x, pools[shape][0][k].x0))
         finally:
-            cs.cs_server_destroy(sv)
-        # plain FP32 solves of the same requests one at a time, arrival order, same arrival clock
-        t0 = time.perf_counter()
-        free_at, plat, prmse = 0.0, [], []
-        for arr, inst, w, T in reqs:
-            while time.perf_counter() - t0 < arr:
-                time.sleep(min(0.001, arr - (time.perf_counter() - t0)))
-            h = cs.cs_problem_create(inst.A, inst.y, inst.lam)
-            cs.cs_solve(h, cs.params_from_workload(dict(w, precision="fp32")), T)
-            x, s, E, st, _ = cs.cs_result(h)
+            cs.cs_server_destroy(sv)  # queued requests past the window are dropped
+        return summary(len(arr), lat, in_window, rmse)
+
+    def plain_arm(arr, drain):
+        t0 = time.monotonic()
+        lat, in_window, rmse = [], 0, []
+        for t, shape, k in arr:
+            if not drain and time.monotonic() - t0 >= window:
+                break
+            wait_until(t0, t)
+            h = handles[shape][k]
+            cs.cs_solve(h, prms_plain[shape], trials[shape])
+            x, sg, E, st, _ = cs.cs_result(h)
+            done = time.monotonic() - t0
+            lat.append(done - t)
+            in_window += done <= window
+            rmse.append(oracle.rmse(x, pools[shape][0][k].x0))
+        return summary(len(arr), lat, in_window, rmse)
+
+    rates = [args.serve_rate] if args.serve_rate else cfg["rates"]
+    results = []
+    with ClockSampler(_env_int("LOCAL_RANK", 0)) as clocks:
+        for ri, rate in enumerate(rates):
+            arr = _serve_arrivals(rate, window, cfg["mix"], cfg["pools"], cfg["seed"] + ri)
+            drain = rate < 20.0
+            sv_r = serve_arm(arr, drain)
+            pl_r = plain_arm(arr, drain)
+            results.append(dict(offered_rate=rate, serve=sv_r, plain_fp32=pl_r,
+                                ratio_vs_plain_fp32=(sv_r["achieved_rate"] / pl_r["achieved_rate"]
+                                                     if pl_r["achieved_rate"] else None)))
+    for hs in handles:
+        for h in hs:
             cs.cs_problem_destroy(h)
-            plat.append(time.perf_counter() - t0 - arr)
-            prmse.append(oracle.rmse(x, inst.x0))
-        pmakespan = time.perf_counter() - t0
-
-    def pct(v, q):
-        v = sorted(v)
-        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
-
+    head = results[0]
     line = {
-        "metric": METRIC, "value": len(reqs) / makespan, "unit": "reconstructions/s", "n_gpus": 1, "steps": 1,
-        "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["serve"]["achieved_rate"], "unit": "reconstructions/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": window * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "per request (f64 / f32 / bf16 storage)", "data": "synthetic",
-        "config": {"workload": "serve_mix", "requests": len(reqs), "rate_per_s": 200.0, "mix": "60/30/10",
-                   "slots": 16, "hbm_budget_gb": 150},
-        "latency_ms": {"p50": pct(lat, 0.5) * 1e3, "p99": pct(lat, 0.99) * 1e3},
-        "quality": {"rmse_mean": float(np.mean(rmse)), "plain_fp32_rmse_mean": float(np.mean(prmse))},
-        "plain_fp32": {"value": len(reqs) / pmakespan, "unit": "reconstructions/s",
-                       "latency_ms": {"p50": pct(plat, 0.5) * 1e3, "p99": pct(plat, 0.99) * 1e3},
-                       "sample": "the same requests as plain FP32 solves one at a time, arrival order"},
-        "ratio_vs_plain_fp32": (len(reqs) / makespan) / (len(reqs) / pmakespan),
+        "config": {"workload": "serve_mix", "window_s": window, "rates_per_s": rates, "mix": "60/30/10 of the "
+                   "config 1 (N=200 FP64, 1 trial), config 2 (N=2000 FP32, 64 trials) and config 3 (N in "
+                   "[256, 4096] BF16, 16 trials) shapes", "problem_pools": cfg["pools"],
+                   "slots": cfg["slots"], "hbm_budget_gb": cfg["budget_gb"],
+                   "achieved": "requests completed within the window / window",
+                   "latency": "over completed requests; the sub-saturation stream is drained"},
+        "latency_ms": head["serve"]["latency_ms"],
+        "rates": results,
+        "ratio_vs_plain_fp32": head["ratio_vs_plain_fp32"],
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -585,6 +656,8 @@ def main():
     ap.add_argument("--workload", choices=SINGLE_WORKLOADS + ["batch_uneven_bf16", "serve_mix", "sweep_random"],
                     default=WORKLOAD)
     ap.add_argument("--sweep-datasets", type=int, default=2, help="random datasets per point of the sweep workload")
+    ap.add_argument("--serve-window", type=float, default=None, help="seconds of request arrivals (serve_mix)")
+    ap.add_argument("--serve-rate", type=float, default=None, help="one offered rate instead of 200 and 2 per s")
     ap.add_argument("--batch-instances", type=int, default=None,
                     help="instances of the batched workload (smaller batches for profiling only)")
     args = ap.parse_args()

@@ -1,18 +1,23 @@
 // Continuous-batching request loop (host code; the GPU work is the solver's own
-// kernels).  Each request gets a grid sized to its work (Euler CTAs, each a
+// kernels).  A small request gets a grid sized to its work (Euler CTAs, each a
 // whole SM: about one per 26 million coupling FMAs per step and per 150 KB of
-// G_off, at least 2; a request that would take more than half the GPU takes all
-// SMs but a small reserve, so that small requests keep running beside it).
-// Requests are admitted whenever a slot (a CUDA stream of the server) is free,
-// the request's device-memory estimate fits the remaining HBM budget and its
-// grid fits the SMs not held by running requests; the queue is scanned in
-// arrival order and a request that does not fit yet does not hold back smaller
-// ones behind it.  Each admitted request forms its problem (G stays on the
-// device for its solve) and queues its solve on its slot's stream as a
-// cooperative launch, so the work of several requests overlaps on the GPU.  A
-// worker thread harvests finished requests by event query, copies their results
-// to host memory and frees their device memory, SMs and slot at once, which is
-// what lets the next requests in.
+// G_off, at least 2) and runs as a cooperative launch with clusters of one CTA,
+// so several small requests share the GPU with every grid resident.  A request
+// whose grid would be more than half the GPU is large: it runs alone, with the
+// planner's own work split (clusters, all SMs, or the caller's cluster_size and
+// max_ctas), because a cluster launch does not keep its grid resident beside
+// other grids.  Requests are admitted whenever a slot (a CUDA stream of the
+// server) is free, the request's device-memory estimate fits the remaining HBM
+// budget and its grid fits the SMs not held by running requests; the queue is
+// scanned in arrival order, a small request that does not fit yet does not hold
+// back smaller ones behind it, and a large one at the head of the queue stops
+// further admissions until the running requests have drained and it can start.
+// Each admitted request forms its problem (or takes the caller's, whose G is
+// already on the device) and queues its solve on its slot's stream, so the work
+// of several requests overlaps on the GPU.  A worker thread harvests finished
+// requests by event query, copies their results to host memory and frees their
+// device memory, SMs and slot at once, which is what lets the next requests
+// in.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -43,6 +48,7 @@ struct Request {
   cs_params prm;
   int trials = 0;
   size_t bytes = 0;
+  bool alone = false;  // large: runs with the whole GPU to itself
   int state = RQ_QUEUED;
   int slot = -1;
   cs_problem* p = nullptr;
@@ -73,16 +79,12 @@ size_t request_bytes(int64_t M, int64_t N, int trials, int precision, bool own_p
 }
 
 // Euler CTAs for a request: one per 26e6 coupling FMAs per step (N^2 T), and
-// enough that each holds at most about 150 KB of G_off on chip, at least 2;
-// more than half the GPU becomes all SMs but a reserve of num_sms / 16 for
-// small requests.
+// enough that each holds at most about 150 KB of G_off on chip, at least 2.
 int server_grid(int num_sms, int64_t N, int trials, int precision) {
   const double work = (double)N * (double)N * (double)trials;
   const double gbytes = (double)N * (double)N * (double)cs::storage_bytes(precision);
-  int d = (int)std::max(std::ceil(work / 26.0e6), std::ceil(gbytes / 150.0e3));
-  d = std::max(2, std::min(d, num_sms));
-  if (d > num_sms / 2) d = num_sms - std::max(2, num_sms / 16);
-  return d;
+  const int d = (int)std::max(std::ceil(work / 26.0e6), std::ceil(gbytes / 150.0e3));
+  return std::max(2, std::min(d, num_sms));
 }
 
 }  // namespace
@@ -102,6 +104,8 @@ struct cs_server {
   std::thread worker;
   bool stop = false;
 
+  int sms_of(const Request* r) const { return r->alone ? num_sms : r->prm.max_ctas; }
+
   void finish(Request* r) {
     r->status = cs_result(r->p, r->x_hat.data(), r->sigma_hat.data(), &r->energy, r->stats);
     if (r->status != CS_OK && r->status != CS_ESINGULAR) r->error = cs_last_error();
@@ -112,7 +116,7 @@ struct cs_server {
     r->t_done = now_s();
     slot_busy[r->slot] = 0;
     in_use -= r->bytes;
-    sms_in_use -= r->prm.max_ctas;
+    sms_in_use -= sms_of(r);
     r->A.clear();
     r->A.shrink_to_fit();
     r->y.clear();
@@ -139,7 +143,7 @@ struct cs_server {
     r->slot = s;
     slot_busy[s] = 1;
     in_use += r->bytes;
-    sms_in_use += r->prm.max_ctas;
+    sms_in_use += sms_of(r);
     r->t_start = now_s();
     r->x_hat.resize((size_t)r->N);
     r->sigma_hat.resize((size_t)r->N);
@@ -174,7 +178,7 @@ struct cs_server {
       r->t_done = now_s();
       slot_busy[s] = 0;
       in_use -= r->bytes;
-      sms_in_use -= r->prm.max_ctas;
+      sms_in_use -= sms_of(r);
       return;
     }
     r->state = RQ_RUNNING;
@@ -202,7 +206,9 @@ struct cs_server {
         for (int i = 0; i < max_slots; ++i)
           if (!slot_busy[i]) { s = i; break; }
         if (s < 0) break;
-        if (in_use + r->bytes > budget || sms_in_use + r->prm.max_ctas > num_sms || (r->user && busy.count(r->user))) {
+        const bool held = r->user && busy.count(r->user);
+        if (r->alone && !held && (!running.empty() || in_use + r->bytes > budget)) break;  // drain, then run alone
+        if (in_use + r->bytes > budget || sms_in_use + sms_of(r) > num_sms || held) {
           ++it;
           continue;
         }
@@ -258,14 +264,18 @@ cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server
   return CS_OK;
 }
 
-// The server's share of the GPU for a request: a grid sized to the work, cluster
-// size 1 and cooperative launches (which keep every CTA of a grid resident while
-// grids share SMs).
-static void server_params(const cs_server* sv, const cs_params* prm, int64_t N, int trials, cs_params* out) {
+// The server's share of the GPU for a request.  Small (a grid of at most half
+// the SMs, sized to the work): cluster size 1 and cooperative launches, which
+// keep every CTA of a grid resident while grids share SMs.  Large: the whole
+// GPU, alone, with the caller's cluster_size and max_ctas (0: the planner's).
+static bool server_params(const cs_server* sv, const cs_params* prm, int64_t N, int trials, cs_params* out) {
   *out = *prm;
-  if (out->max_ctas <= 0) out->max_ctas = server_grid(sv->num_sms, N, trials, prm->precision);
-  out->max_ctas = std::min(out->max_ctas, sv->num_sms);
+  const int d = prm->max_ctas > 0 ? std::min(prm->max_ctas, sv->num_sms)
+                                  : server_grid(sv->num_sms, N, trials, prm->precision);
+  if (d > sv->num_sms / 2) return true;
+  out->max_ctas = d;
   out->cluster_size = 1;
+  return false;
 }
 
 static cs_status enqueue(cs_server* sv, std::unique_ptr<Request> r, uint64_t* ticket) {
@@ -296,7 +306,7 @@ cs_status cs_server_submit(cs_server* sv, cs_problem* p, const cs_params* prm, i
   r->user = p;
   r->M = cs::problem_M(p);
   r->N = cs::problem_N(p);
-  server_params(sv, prm, r->N, trials, &r->prm);
+  r->alone = server_params(sv, prm, r->N, trials, &r->prm);
   r->trials = trials;
   r->bytes = request_bytes(r->M, r->N, trials, prm->precision, false);
   return enqueue(sv, std::move(r), ticket);
@@ -316,7 +326,7 @@ cs_status cs_server_submit_host(cs_server* sv, const double* A, const double* y,
   r->M = M;
   r->N = N;
   r->lambda = lambda;
-  server_params(sv, prm, N, trials, &r->prm);
+  r->alone = server_params(sv, prm, N, trials, &r->prm);
   r->trials = trials;
   r->bytes = request_bytes(M, N, trials, prm->precision);
   if (r->bytes <= sv->budget) {

@@ -155,3 +155,33 @@ def test_requests_on_a_cached_problem():
         np.testing.assert_allclose(x, results[0][0], rtol=0, atol=1e-9)
     finally:
         cs.cs_problem_destroy(h)
+
+
+@pytest.mark.gpu
+def test_large_request_runs_alone_with_the_planner_split():
+    """A request whose grid would take more than half the GPU (N = 2000, 64 trials)
+    runs alone with the planner's own work split: no other request of the stream
+    runs while it does, and its result and plan are those of a plain cs_solve of
+    the same problem with the same parameters."""
+    import torch
+
+    base = cs_inputs.WORKLOADS["single_n200_fp64"]
+    small = [(cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=40 + k), dict(base, n_outer=2, n_steps=400), 1)
+             for k in range(3)]
+    big = cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=7)
+    wbig = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], n_outer=2, n_steps=300)
+    reqs = small[:2] + [(big, wbig, 64)] + small[2:]
+    res = _serve(reqs, slots=4, budget=64 << 30)
+    tb = res[2][4]
+    for k in (0, 1, 3):
+        t = res[k][4]
+        assert t[2] <= tb[1] or t[1] >= tb[2]
+    h = cs.cs_problem_create(torch.from_numpy(big.A).cuda(), torch.from_numpy(big.y).cuda(), big.lam)
+    try:
+        cs.cs_solve(h, cs.params_from_workload(wbig), 64)
+        x, s, E, st, _ = cs.cs_result(h)
+    finally:
+        cs.cs_problem_destroy(h)
+    assert res[2][3][8] == st[8] and res[2][3][9] == st[9] and res[2][3][10] == st[10]
+    np.testing.assert_array_equal(res[2][0], x)
+    np.testing.assert_array_equal(res[2][1], s)
