@@ -487,10 +487,11 @@ def run_serve(args):
             cs.cs_result(h)
 
     def summary(n_offered, lat, in_window, rmse):
+        in_window = int(in_window)
         return dict(offered=n_offered, completed=len(lat), completed_in_window=in_window,
                     achieved_rate=in_window / window,
-                    latency_ms={"p50": None if not lat else _pct(lat, 0.5) * 1e3,
-                                "p99": None if not lat else _pct(lat, 0.99) * 1e3},
+                    latency_ms={"p50": None if not lat else float(_pct(lat, 0.5)) * 1e3,
+                                "p99": None if not lat else float(_pct(lat, 0.99)) * 1e3},
                     rmse_mean=float(np.mean(rmse)) if rmse else None)
 
     def serve_arm(arr, drain):

@@ -3,15 +3,17 @@
 // whole SM: about one per 26 million coupling FMAs per step and per 150 KB of
 // G_off, at least 2) and runs as a cooperative launch with clusters of one CTA,
 // so several small requests share the GPU with every grid resident.  A request
-// whose grid would be more than half the GPU is large: it runs alone, with the
-// planner's own work split (clusters, all SMs, or the caller's cluster_size and
-// max_ctas), because a cluster launch does not keep its grid resident beside
-// other grids.  Requests are admitted whenever a slot (a CUDA stream of the
-// server) is free, the request's device-memory estimate fits the remaining HBM
-// budget and its grid fits the SMs not held by running requests; the queue is
-// scanned in arrival order, a small request that does not fit yet does not hold
-// back smaller ones behind it, and a large one at the head of the queue stops
-// further admissions until the running requests have drained and it can start.
+// whose grid would be more than half the GPU is large: it starts only on an idle
+// GPU and runs with the planner's own work split (clusters) over all SMs but a
+// reserve of kBackfillSms (or the caller's cluster_size and max_ctas), because a
+// cluster launch does not keep its grid resident beside grids that were there
+// first; small requests admitted after it run in the SMs it leaves.  Requests
+// are admitted whenever a slot (a CUDA stream of the server) is free, the
+// request's device-memory estimate fits the remaining HBM budget and its grid
+// fits the SMs not held by running requests; the queue is scanned in arrival
+// order, a small request that does not fit yet does not hold back smaller ones
+// behind it, and a large one at the head of the queue stops further admissions
+// until the running requests have drained and it can start.
 // Each admitted request forms its problem (or takes the caller's, whose G is
 // already on the device) and queues its solve on its slot's stream, so the work
 // of several requests overlaps on the GPU.  A worker thread harvests finished
@@ -48,7 +50,7 @@ struct Request {
   cs_params prm;
   int trials = 0;
   size_t bytes = 0;
-  bool alone = false;  // large: runs with the whole GPU to itself
+  bool alone = false;  // large: starts on an idle GPU, small requests backfill the SMs it leaves
   int state = RQ_QUEUED;
   int slot = -1;
   cs_problem* p = nullptr;
@@ -104,7 +106,7 @@ struct cs_server {
   std::thread worker;
   bool stop = false;
 
-  int sms_of(const Request* r) const { return r->alone ? num_sms : r->prm.max_ctas; }
+  int sms_of(const Request* r) const { return r->prm.max_ctas > 0 ? r->prm.max_ctas : num_sms; }
 
   void finish(Request* r) {
     r->status = cs_result(r->p, r->x_hat.data(), r->sigma_hat.data(), &r->energy, r->stats);
@@ -264,15 +266,22 @@ cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server
   return CS_OK;
 }
 
+// SMs a large request leaves to the small requests that backfill beside it.
+constexpr int kBackfillSms = 8;
+
 // The server's share of the GPU for a request.  Small (a grid of at most half
 // the SMs, sized to the work): cluster size 1 and cooperative launches, which
-// keep every CTA of a grid resident while grids share SMs.  Large: the whole
-// GPU, alone, with the caller's cluster_size and max_ctas (0: the planner's).
+// keep every CTA of a grid resident while grids share SMs.  Large: started on an
+// idle GPU, the caller's cluster_size and max_ctas (0: the planner's split over
+// all SMs but kBackfillSms).
 static bool server_params(const cs_server* sv, const cs_params* prm, int64_t N, int trials, cs_params* out) {
   *out = *prm;
   const int d = prm->max_ctas > 0 ? std::min(prm->max_ctas, sv->num_sms)
                                   : server_grid(sv->num_sms, N, trials, prm->precision);
-  if (d > sv->num_sms / 2) return true;
+  if (d > sv->num_sms / 2) {
+    out->max_ctas = prm->max_ctas > 0 ? d : std::max(1, sv->num_sms - kBackfillSms);
+    return true;
+  }
   out->max_ctas = d;
   out->cluster_size = 1;
   return false;
