@@ -295,8 +295,8 @@ def run_batch(args):
     dev = [(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda()) for i in insts]
     torch.cuda.synchronize()
     over = {k: v for k, v in (("n_outer", args.n_outer), ("n_steps", args.n_steps)) if v}
-    prm_b = _run_params(cs, "bf16", autotune=args.autotune, **over)
-    prm_w = _run_params(cs, "bf16", autotune=args.autotune, **dict(over, n_outer=1))
+    prm_b = _run_params(cs, "bf16", autotune=args.autotune, tensor_form=args.tensor_form, **over)
+    prm_w = _run_params(cs, "bf16", autotune=args.autotune, tensor_form=args.tensor_form, **dict(over, n_outer=1))
     prm_p = _run_params(cs, "fp32", **over)
     # the problems (G formed once, kept resident) serve every batch
     hs = [cs.cs_problem_create(A, y, i.lam, stream=stream) for (A, y), i in zip(dev, insts)]
@@ -348,7 +348,21 @@ def run_batch(args):
     tflops = flops / t_b / 1e12
     gbs = gbytes / t_b / 1e9
     hpeak = float(peaks.get("hbm_gbs", 6800.0))
-    if int(res[0][3][10]) == 4:
+    form = int(res[0][3][10])
+    if form == 6:
+        # tcgen05 form: one M = 128, N = 2 x 16 MMA per 16 k and 128-row tile
+        # (the two parts of X), against the dense BF16 tensor peak; and the G_off bytes
+        tpk = float(peaks.get("bf16_tflops", 1900.0))
+        executed = sum(((i.N + 127) // 128 * 128) * ((i.N + 31) // 32 * 32) * 2.0 * 2 * T for i in insts) * steps_all
+        tfrac = executed / t_b / 1e12 / tpk
+        hbm = gbs / hpeak >= tfrac
+        roof = {"kernel": "euler_batch_kernel<__nv_bfloat16, float, 2, PAIR=false, TC=false, TC5=true>",
+                "bound": "hbm" if hbm else "tensor", "achieved": gbs if hbm else executed / t_b / 1e12,
+                "peak": hpeak if hbm else tpk, "unit": "GB/s" if hbm else "TFLOP/s",
+                "frac": max(gbs / hpeak, tfrac), "hbm_frac": gbs / hpeak, "tensor_frac": tfrac,
+                "algorithmic_tflops": tflops, "traffic": None,
+                "peak_source": f"HBM copy bandwidth and dense BF16 tensor rate ({peak_kind})"}
+    elif form == 4:
         # tensor-core form: two FP16/BF16 MMAs per product (the two parts of X) on
         # the mma.sync path, against its measured ceiling; and the G_off bytes
         mma = 2.0 * tflops

@@ -105,14 +105,18 @@ typedef struct {
                            M = 128 MMA per 16 k on the stacked parts, TMEM accumulators;
                            resident G_off, at most 64 rows per cluster) or on the mma.sync
                            path (three MMAs per tile); streamed FP16 / BF16 G_off with exactly
-                           8 trials, and batches of FP16 / BF16 problems with 8 or 16 trials
-                           (mma.sync: the stored G_off times X in two 16-bit parts).  X is
+                           8 trials (mma.sync), and batches of FP16 / BF16 problems with 8 or
+                           16 trials (tcgen05 or mma.sync: the stored G_off times X in two
+                           16-bit parts).  X is
                            scaled by a power of two from max |R|, so |X| <= |c| and FP16 X
                            overflows only on runs whose explicit Euler steps already diverge.
                            0: the planner chooses among every form; 1: FMA forms only;
                            2: tensor-core forms only; 3: mma.sync tensor-core forms only;
-                           4: the tcgen05 form only (resident FP32 G_off).  2, 3 and 4 make
-                           the solve fail with CS_EINVAL where no such form applies */
+                           4: the tcgen05 forms only (single solves: resident FP32 G_off;
+                           batches: BF16 / FP16 G_off with 8 or 16 trials, one M = 128 MMA
+                           per 128-row tile and 16 k, TMEM accumulators, the batched default
+                           where it applies).  2, 3 and 4 make the solve fail with CS_EINVAL
+                           where no such form applies */
   int32_t self_term;    /* 0: the injection of Eq. MFZlocalfieldmain as written (its Hamiltonian,
                            Eq. l0Hamiltonian, has no self-term, so a spin at its refit value turns
                            on when G_rr R_r^2 > lambda); 1: corrected mode, the injection also
@@ -213,7 +217,8 @@ cs_status cs_tune_info(int64_t* tunings, int64_t* disk_hits, char* path, int64_t
  *   [7] energy of the kept trial  [8] cluster size (batched: CTAs that ran the problem) and [9] CTAs of the Euler kernel
  *   [10] form of the Euler kernel: 0 FP32/FP64 FMAs (narrow split), 1 packed FP32
  *        FMAs (wide split), 2 tensor cores (mma.sync), 3 batched (one problem per CTA),
- *        4 batched on tensor cores (mma.sync), 5 tensor cores (tcgen05, TMEM)
+ *        4 batched on tensor cores (mma.sync), 5 tensor cores (tcgen05, TMEM),
+ *        6 batched on tensor cores (tcgen05, TMEM)
  *   [11] error of the coupling against FP64: max_r |(G_off^s x_hat)_r - (G_off x_hat)_r|
  *        / max_r |(G_off x_hat)_r|, G_off^s being G_off rounded to the storage precision
  *        the Euler kernels used (0 for FP64), both products formed in FP64

@@ -96,6 +96,15 @@ size_t compute_bytes(int precision) { return precision == CS_P_FP64 ? 8 : 4; }
 
 // (Re)size the per-solve buffers for `trials`, n_outer and record_steps.  A
 // batched solve (`pool` false) shares one refit workspace across its problems.
+// Zero both X buffers: every product form relies on X rows >= N being zero,
+// and the forms lay X out differently, so rows a previous solve of another
+// form wrote may sit where this one keeps padding.
+static cudaError_t clear_x(ProblemDev& P, SolveDev& S) {
+  cudaError_t e = cudaMemsetAsync(S.X0, 0, S.x_bytes, P.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.X1, 0, S.x_bytes, P.stream);
+  return e;
+}
+
 cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int trials, bool pool = true) {
   const int rec = prm.record_steps > 0 ? std::min(prm.record_steps, prm.n_steps) : 0;
   const bool fits = S.R && trials <= S.cap_trials && prm.n_outer <= S.cap_outer && rec <= S.cap_record &&
@@ -111,8 +120,7 @@ cs_status ensure_solve(ProblemDev& P, SolveDev& S, const cs_params& prm, int tri
     const size_t T4 = (T + 3) / 4 * 4;
     CS_CUDA(dev_alloc(&S.X0, Np * T4 * cb, P.stream), "cudaMalloc X0");
     CS_CUDA(dev_alloc(&S.X1, Np * T4 * cb, P.stream), "cudaMalloc X1");
-    CS_CUDA(cudaMemsetAsync(S.X0, 0, Np * T4 * cb, P.stream), "memset X0");
-    CS_CUDA(cudaMemsetAsync(S.X1, 0, Np * T4 * cb, P.stream), "memset X1");
+    S.x_bytes = Np * T4 * cb;
     CS_CUDA(alloc(&S.sigma, N * T), "cudaMalloc sigma");
     CS_CUDA(alloc(&S.energy, T), "cudaMalloc energy");
     CS_CUDA(alloc(&S.ssize, (size_t)prm.n_outer * T), "cudaMalloc ssize");
@@ -204,8 +212,8 @@ cs_status check_params(const cs_params* p, int trials) {
   if (p->tensor_form < 0 || p->tensor_form > 4) return fail(CS_EINVAL, "tensor_form must be 0, 1, 2, 3 or 4");
   if (p->tensor_form >= 2 && (p->precision == CS_P_FP64 || p->precision == CS_P_FP8))
     return fail(CS_EINVAL, "tensor_form >= 2: no tensor-core form for FP64 or FP8 storage");
-  if (p->tensor_form == 4 && (p->precision != CS_P_FP32 || p->stream_g == 1))
-    return fail(CS_EINVAL, "tensor_form = 4: the tcgen05 form is built for resident FP32 G_off only");
+  if (p->tensor_form == 4 && p->precision == CS_P_FP32 && p->stream_g == 1)
+    return fail(CS_EINVAL, "tensor_form = 4: the single-problem tcgen05 form keeps FP32 G_off resident");
   if (p->self_term != 0 && p->self_term != 1) return fail(CS_EINVAL, "self_term must be 0 or 1");
   if (p->readout != CS_READOUT_FINAL && p->readout != CS_READOUT_BEST) return fail(CS_EINVAL, "bad readout");
   if (p->readout == CS_READOUT_BEST && p->field != CS_FIELD_BN)
@@ -475,6 +483,7 @@ cs_status cs_solve(cs_problem* p, const cs_params* prm, int32_t trials) {
   if (P.gs_prec != prm->precision) ++P.launches;
   CS_CUDA(launch_store_coupling(P, prm->precision), "store coupling");
   if ((st = ensure_solve(P, S, *prm, trials)) != CS_OK) return st;
+  CS_CUDA(clear_x(P, S), "memset X");
   CS_CUDA(cudaMemsetAsync(S.err, 0, sizeof(int), P.stream), "memset err");
   CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), P.stream), "memset singular");
   int khz = 0;
@@ -566,12 +575,12 @@ static void apply_batch_shape(const BatchShape& sh, const std::vector<int>& rts,
 // launches rewrite.
 constexpr int kBatchTuneSteps = 48;
 
-static cs_status tune_batch_shape(BatchLaunch L, const std::vector<int>& rts, bool btc, int fixed_cc, int device,
+static cs_status tune_batch_shape(BatchLaunch L, const std::vector<int>& rts, int btc, int fixed_cc, int device,
                                   cudaStream_t stream, BatchShape* out) {
   std::map<int, int> hist;
   for (int r : rts) ++hist[r];
   std::string key = "batch|" + tune_device_tag(device) + "|p" + std::to_string(L.prm->precision) + "|T" +
-                    std::to_string(L.T) + "|tc" + std::to_string((int)btc) + "|c" + std::to_string(L.ctas) + "|k" +
+                    std::to_string(L.T) + "|tc" + std::to_string(btc) + "|c" + std::to_string(L.ctas) + "|k" +
                     std::to_string(fixed_cc) + "|";
   for (const auto& kv : hist) key += std::to_string(kv.first) + ":" + std::to_string(kv.second) + ",";
   const int max_rt = rts.empty() ? 0 : *std::max_element(rts.begin(), rts.end());
@@ -655,7 +664,6 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     if (trials[i] > 64) return fail(CS_EINVAL, "a batched solve takes at most 64 trials per problem");
     if (prms[i]->record_steps != 0 || prms[i]->record_outer != 0)
       return fail(CS_EINVAL, "a batched solve does not record trajectories or outer histories");
-    if (prms[i]->tensor_form == 4) return fail(CS_EINVAL, "tensor_form = 4: the batched kernel has no tcgen05 form");
     if (prms[i]->init_R != CS_INIT_R_ZEEMAN)
       return fail(CS_EINVAL, "a batched solve starts from R = h^z / diag G (init_R = CS_INIT_R_ZEEMAN)");
     if (prms[i]->readout != CS_READOUT_FINAL)
@@ -674,15 +682,15 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   // iteration `it` are a prefix of the group.
   struct Group {
     int precision, T;
-    bool btc;
+    int btc;  // batch_tc_kind
     std::vector<int> idx;
   };
   std::vector<Group> groups;
-  std::vector<char> btcs(n);
+  std::vector<int> btcs(n);
   for (int i = 0; i < n; ++i) {
     const cs_params& p = *prms[i];
-    const bool btc = batch_tensor_form(p.precision, trials[i], p.tensor_form);
-    if (p.tensor_form >= 2 && !btc)
+    const int btc = batch_tc_kind(p.precision, trials[i], p.tensor_form);
+    if (p.tensor_form >= 2 && btc == 0)
       return fail(CS_EINVAL, "tensor_form >= 2: the batched tensor-core form needs BF16 or FP16 storage and 8 or 16 "
                              "trials");
     btcs[i] = btc;
@@ -709,6 +717,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     n_outer_max = std::max(n_outer_max, prms[i]->n_outer);
     CS_CUDA(launch_store_tiled(P, prms[i]->precision, btcs[i]), "store tiled coupling");
     if ((st = ensure_solve(P, S, *prms[i], trials[i], false)) != CS_OK) return st;
+    CS_CUDA(clear_x(P, S), "memset X");
     CS_CUDA(cudaMemsetAsync(S.singular, 0, sizeof(int), stream), "memset singular");
   }
   // batch-owned buffers, released (stream-ordered) after the graph
@@ -877,7 +886,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
       ps[i]->S.plan_cluster =
           (shapes[g].cc > 1 && batch_row_tiles(ps[i]->P.N) >= shapes[g].span_rt) ? shapes[g].cc : 1;
       ps[i]->S.plan_ctas = std::min((int)groups[g].idx.size(), P0.num_sms);
-      ps[i]->S.plan_form = groups[g].btc ? 4 : 3;
+      ps[i]->S.plan_form = groups[g].btc == 2 ? 6 : (groups[g].btc == 1 ? 4 : 3);
     }
   return CS_OK;
 }

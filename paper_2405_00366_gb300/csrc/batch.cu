@@ -33,6 +33,7 @@
 #include "internal.h"
 #include "kernels_common.cuh"
 #include "mma.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace cs {
@@ -48,7 +49,8 @@ constexpr int kKC = 32;                        // columns (k) per tile
 
 // Tiled, swizzled copy of G_off (see the file comment), divided by its row
 // scales when the storage type is row-scaled.  frag = 1: inside each tile the
-// A-operand order of the tensor-core form, [row tile of 16][k half][lane][8].
+// A-operand order of the mma.sync form, [row tile of 16][k half][lane][8];
+// frag = 2: the canonical operand layout of the tcgen05 form.
 template <typename GT>
 __global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict__ Gt, int N, int nrt, int nkc,
                                    const float* __restrict__ gscale, int frag) {
@@ -59,7 +61,13 @@ __global__ void store_tiled_kernel(const double* __restrict__ G, GT* __restrict_
     const int within = (int)(idx % (kRT * kKC));
     const int rt = (int)(tile / nkc), kc = (int)(tile % nkc);
     int r, k;
-    if (frag) {
+    if (frag == 2) {
+      // tcgen05 operand order: two 16-k blocks of 128 rows, each in the
+      // canonical no-swizzle K-major layout (tcgen05.cuh), 4 KB apart
+      const int b = 2 * within, blk = b >> 12, rem = b & 4095;
+      r = (rem >> 8) * 8 + ((rem & 127) >> 4);
+      k = blk * 16 + ((rem >> 7) & 1) * 8 + ((rem & 15) >> 1);
+    } else if (frag) {
       const int sub = within >> 8, L = (within >> 3) & 31, e = within & 7;
       int rr, kk;
       tc_arow_col(L, e, rr, kk);
@@ -129,7 +137,7 @@ __host__ __device__ __forceinline__ size_t b_part_bytes(int twp, size_t cbytes, 
 // its column tiles of G_off, tps per ring slot, each slot followed by the
 // matching k rows of X; chunk ci is ring use gctr + ci.
 template <typename GT, typename CT>
-__device__ __forceinline__ void produce_row_tile(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
+__device__ __forceinline__ bool produce_row_tile(const BArgs<CT>& a, const BInst<CT>& I, const CT* __restrict__ X,
                                                  int rt, unsigned char* ring, size_t slot, uint64_t* full,
                                                  uint64_t* empty, unsigned gctr, unsigned* issued, int ci0,
                                                  int ci1) {
@@ -144,7 +152,7 @@ __device__ __forceinline__ void produce_row_tile(const BArgs<CT>& a, const BInst
     const unsigned u = g / a.slots;
     if (u >= 1 && !mbar_wait(empty + s, (u - 1) & 1u, a.timeout_cycles)) {
       set_error(a.err, DEV_TIMEOUT);
-      break;
+      return false;
     }
     const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
     unsigned char* dst = ring + (size_t)s * slot;
@@ -153,6 +161,7 @@ __device__ __forceinline__ void produce_row_tile(const BArgs<CT>& a, const BInst
     bulk_copy_g2s(dst, gsrc + (size_t)kc0 * kRT * kKC, (unsigned)(nt * gtile), full + s);
     bulk_copy_g2s(dst + a.tps * gtile, X + (size_t)kc0 * kKC * twp, (unsigned)(nt * xbytes), full + s);
   }
+  return true;
 }
 
 // Partial-free product of one row tile: U[r][tt] = sum_k G_off[rt*kRT + r][k] X[k][tt]
@@ -429,9 +438,22 @@ __device__ __forceinline__ bool tile_product_tc(const BArgs<float>& a, const BIn
 
 // Store X[k][t] = v in the layout of the launch's product form; the
 // tensor-core form stores two 16-bit parts (X scaled so that |X| <= |c|).
-template <typename GT, typename CT, bool PAIR, bool TC>
+// X of the tcgen05 form: 16-k blocks of NN = 2 twp operand rows (trial t's
+// high part is row t, its low part row twp + t), each block in the canonical
+// layout (tcgen05.cuh); element index of (k, row n).
+__host__ __device__ __forceinline__ size_t tc5_xidx(int k, int n, int NN) {
+  return (size_t)(k >> 4) * (size_t)(NN * 16) + tc5::canon_off(n, k & 15) / 2;
+}
+
+template <typename GT, typename CT, bool PAIR, bool TC, bool TC5 = false>
 __device__ __forceinline__ void bxput(CT* X, int k, int t, int twp, CT v) {
-  if constexpr (TC) {
+  if constexpr (TC5) {
+    GT* h = reinterpret_cast<GT*>(X);
+    const GT hi = GT(v);
+    const float hf = float(hi);
+    h[tc5_xidx(k, t, 2 * twp)] = hi;
+    h[tc5_xidx(k, twp + t, 2 * twp)] = GT((v - hf) * (float)(1 << tc_type<GT>::kLoShift));
+  } else if constexpr (TC) {
     GT* h = reinterpret_cast<GT*>(X);
     const GT hi = GT(v);
     const float hf = float(hi);
@@ -473,19 +495,157 @@ __device__ __forceinline__ bool row_tile_product(const BArgs<CT>& a, const BInst
 
 __device__ __forceinline__ size_t zmin(size_t x, size_t y) { return x < y ? x : y; }
 
+// 8 consecutive floats (32-byte aligned) into registers.
+__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// tcgen05 form of the batched product (BF16 / FP16 G_off, 8 or 16 trials): the
+// product of a row tile is one M = 128, N = NN = 2 twp MMA per 16-k block (A =
+// the row tile's G_off block, B = the two 16-bit parts of the block's X rows),
+// issued by one thread, lane 0 of the producer warp, which also issues the
+// ring's bulk copies.  The 16-k blocks of a row tile rotate over four FP32
+// accumulators (limiting how many truncating accumulations any one sum
+// takes), summed with round-to-nearest additions in the epilogue.  Two sets of
+// accumulators (buf = row-tile count & 1) let the consumer warps read and
+// apply one row tile's U while the MMAs of the next run.  Barriers: accfull[b]
+// (one arrival: the tcgen05 commit after a row tile's last MMA), accfree[b]
+// (the 8 consumer warps, after reading buffer b), fin (the final commit).
+struct Tc5 {
+  uint64_t* accfull;
+  uint64_t* accfree;
+  uint64_t* fin;
+  uint32_t tmem;    // TMEM base address
+  uint32_t idesc;   // instruction descriptor (M = 128, N = NN)
+  int NN;           // 2 twp
+  unsigned jt = 0;  // producer: row tiles issued
+  unsigned jc = 0;  // consumers: row tiles read
+};
+
+// Producer lane 0: the copies and MMAs of row tile rt (X = this pass's X), then
+// the first ring-full of copies of the CTA's next row tile of the pass.
+// Returns false after a timed-out wait.
+template <typename GT>
+__device__ __forceinline__ bool tc5_row_tile(const BArgs<float>& a, const BInst<float>& I, const float* __restrict__ X, int rt,
+                             int rstep, unsigned char* ring, size_t slot, uint64_t* full, uint64_t* empty,
+                             unsigned& gctr, unsigned* issued, int& pre, Tc5& t5) {
+  const int nkc = I.nkc, nch = (nkc + a.tps - 1) / a.tps;
+  const uint32_t gtile = (uint32_t)(kRT * kKC * sizeof(GT));
+  const uint32_t xblk = (uint32_t)t5.NN * 32;  // bytes of one 16-k block of X
+  const int b = (int)(t5.jt & 1u);
+  const unsigned u = t5.jt >> 1;
+  ++t5.jt;
+  if (u >= 1 && !mbar_wait(t5.accfree + b, (u - 1) & 1u, a.timeout_cycles)) {
+    set_error(a.err, DEV_TIMEOUT);
+    return false;
+  }
+  tc5::fence_after_sync();
+  const uint32_t acc0 = t5.tmem + (uint32_t)(b * 4 * t5.NN);
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  int next = pre;  // chunks of this row tile whose copies are issued
+  if (!produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued, next, min(nch, a.slots)))
+    return false;
+  next = max(next, min(nch, a.slots));
+  int kb = 0;
+  for (int ci = 0; ci < nch; ++ci) {
+    const unsigned g = gctr + ci;
+    const int s = (int)(g % a.slots);
+    if (!mbar_wait(full + s, (g / a.slots) & 1u, a.timeout_cycles)) {
+      set_error(a.err, DEV_TIMEOUT);
+      return false;
+    }
+    tc5::fence_after_sync();
+    const int nt = min(a.tps, nkc - ci * a.tps);
+    const uint32_t sb = ring_s + (uint32_t)(s * slot);
+    for (int j = 0; j < nt; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h, ++kb) {
+        const uint64_t ad = tc5::smem_desc(sb + j * gtile + h * 4096u, tc5::kLBO, tc5::kSBO);
+        const uint64_t bd = tc5::smem_desc(sb + a.tps * gtile + (2 * j + h) * xblk, tc5::kLBO, tc5::kSBO);
+        tc5::mma_f16(acc0 + (uint32_t)((kb & 3) * t5.NN), ad, bd, t5.idesc, kb >= 4 ? 1u : 0u);
+      }
+    tc5::commit(empty + s);  // the slot is free once these MMAs have read it
+    // copies ahead: up to chunk ci + slots - 1 (its slot was read by chunk ci - 1)
+    const int upto = min(nch, ci + a.slots);
+    if (next < upto) {
+      if (!produce_row_tile<GT, float>(a, I, X, rt, ring, slot, full, empty, gctr, issued, next, upto)) return false;
+      next = upto;
+    }
+  }
+  tc5::commit(t5.accfull + b);
+  gctr += nch;
+  pre = 0;
+  if (rt + rstep < I.nrt) {
+    const int nn = min(a.slots, nch);
+    if (!produce_row_tile<GT, float>(a, I, X, rt + rstep, ring, slot, full, empty, gctr, issued, 0, nn)) return false;
+    pre = nn;
+  }
+  return true;
+}
+
+// Consumer warps: U of this thread's row (32 (warp % 4) + lane of row tile rt)
+// and trials 8 (warp / 4) .. + 7 from the row tile's accumulators (the warps
+// with no trials there read nothing), then release the accumulators.  Returns
+// false after a timed-out wait.
+template <typename GT>
+__device__ __forceinline__ bool tc5_read(const BArgs<float>& a, const BInst<float>& I, Tc5& t5, float xsi, float (&U)[8]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = (int)(t5.jc & 1u);
+  const unsigned u = t5.jc >> 1;
+  ++t5.jc;
+  // (warp-uniform decision: the TMEM loads below are warp-collective)
+  if (!__all_sync(0xffffffffu, mbar_wait(t5.accfull + b, u & 1u, a.timeout_cycles))) {
+    if (lane == 0) set_error(a.err, DEV_TIMEOUT);
+    return false;
+  }
+  tc5::fence_after_sync();
+  const int hh = w >> 2;
+  if (hh * 8 < a.twp) {
+    const uint32_t base = tc5::taddr(t5.tmem, 32 * (w & 3), b * 4 * t5.NN + hh * 8);
+    float hi[8], lo[8];
+    const int nacc = min(4, 2 * I.nkc);
+    if (nacc == 4) {
+      tc5::ld8x4_sum(base, (uint32_t)t5.NN, hi);
+      tc5::ld8x4_sum(base + (uint32_t)a.twp, (uint32_t)t5.NN, lo);
+    } else {
+      tc5::ld8(base, hi);
+      tc5::ld8(base + (uint32_t)a.twp, lo);
+      for (int k = 1; k < nacc; ++k) {
+        float h2[8], l2[8];
+        tc5::ld8(base + (uint32_t)(k * t5.NN), h2);
+        tc5::ld8(base + (uint32_t)(k * t5.NN + a.twp), l2);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          hi[i] += h2[i];
+          lo[i] += l2[i];
+        }
+      }
+    }
+    const float wlo = 1.0f / (float)(1 << tc_type<GT>::kLoShift);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) U[i] = fmaf(wlo, lo[i], hi[i]) * xsi;
+  }
+  tc5::fence_before_sync();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(t5.accfree + b);
+  return true;
+}
+
 // End of a phase of a run: X (and the state) written by every CTA of the run
 // become visible to the next phase's bulk copies.  A run of `span` CTAs (a
 // whole cluster) meets at the cluster barrier, where each CTA also posts its
 // `ok` (CTA-uniform) in vote[vpar] and then reads every CTA's: every CTA of the
 // cluster returns the same decision, so all of them take the same number of
 // cluster barriers.  (vote has two entries, used in turn: an entry is rewritten
-// only two barriers later, after every CTA has read it.)
+// only two barriers later, after every CTA has read it.)  `ok` may differ
+// between the threads of a CTA; the CTA's is their AND.
 __device__ __forceinline__ bool run_sync(int span, bool ok, int* vote, unsigned& vpar) {
   fence_proxy_async_global();
-  if (span == 1) {
-    __syncthreads();
-    return ok;
-  }
+  ok = __syncthreads_and(ok);
+  if (span == 1) return ok;
   cg::cluster_group cl = cg::this_cluster();
   if (threadIdx.x == 0) vote[vpar] = ok ? 1 : 0;
   cl.sync();
@@ -498,10 +658,10 @@ __device__ __forceinline__ bool run_sync(int span, bool ok, int* vote, unsigned&
 // One CIM run of problem I by `span` CTAs (rank `rank` of them takes row tiles
 // rank, rank + span, ...).  Returns false (in every thread of every CTA of the
 // run) if a wait timed out.
-template <typename GT, typename CT, int MR, bool PAIR, bool TC>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC, bool TC5>
 __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, int span, unsigned char* ring,
                              size_t slot, CT* P, uint64_t* full, uint64_t* empty, unsigned& gctr, unsigned* issued,
-                             int* vote, unsigned& vpar) {
+                             int* vote, unsigned& vpar, Tc5& t5) {
   const int T = a.T, twp = a.twp, N = I.N;
   const size_t NT = (size_t)N * T;
   const size_t tileT = (size_t)kRT * T;  // elements of one row tile
@@ -510,7 +670,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
   // tensor-core form: X scaled by 2^-e with max |R| < 2^e (exact; U scaled back)
   CT xsc = CT(1);
   float xsi = 1.f;
-  if constexpr (TC) {
+  if constexpr (TC || TC5) {
     double m = 0.0;
     for (size_t o = threadIdx.x; o < NT; o += kBThreads) m = fmax(m, fabs(I.R[o]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -538,10 +698,36 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
     for (int rt = rank; rt < I.nrt; rt += span)
       for (size_t idx = rt * tileT + threadIdx.x; idx < zmin(NT, (rt + 1) * tileT); idx += kBThreads) {
         const int r = (int)(idx / T), t = (int)(idx % T);
-        bxput<GT, CT, PAIR, TC>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
+        bxput<GT, CT, PAIR, TC, TC5>(I.X0, r, t, twp, CT(I.R[idx]) * xsc);
       }
     ok = run_sync(span, ok, vote, vpar);
-    for (int rt = rank; rt < I.nrt && ok; rt += span) {
+    if constexpr (TC5) {
+      // b of this CTA's rows from U = G_off X0 (producer lane 0: copies and MMAs;
+      // consumer warps: U from TMEM, then b)
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      bool okt = ok;
+      if (w == kBWarps) {
+        if (lane == 0)
+          for (int rt = rank; rt < I.nrt && okt; rt += span)
+            okt = tc5_row_tile<GT>(a, I, I.X0, rt, span, ring, slot, full, empty, gctr, issued, pre, t5);
+      } else {
+        for (int rt = rank; rt < I.nrt && okt; rt += span) {
+          float U[8];
+          okt = tc5_read<GT>(a, I, t5, xsi, U);
+          const int hh = w >> 2, r = rt * kRT + 32 * (w & 3) + lane;
+          if (okt && hh * 8 < T && r < N)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const size_t o = (size_t)r * T + hh * 8 + i;
+              const double v = (double)U[i];
+              const double corr = I.self_term ? (st / 4.0) * I.g[r] * I.R[o] * I.R[o] : 0.0;
+              b[o] = CT(I.R[o] * (-(st / 4.0) * v + (st / 2.0) * I.hz[r]) - I.theta - corr);
+            }
+        }
+      }
+      ok = __syncthreads_and(okt);
+    }
+    for (int rt = rank; rt < I.nrt && ok && !TC5; rt += span) {
       ok = __syncthreads_and(row_tile_product<GT, CT, MR, PAIR, TC>(a, I, I.X0, rt, span, ring, slot, P, full, empty,
                                                                     gctr, issued, xsi, pre));
       for (int idx = threadIdx.x; idx < kRT * T; idx += kBThreads) {
@@ -570,7 +756,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
       c[o] = c0;
       e[o] = CT(1);
       const CT Rr = CT(I.R[o]);
-      bxput<GT, CT, PAIR, TC>(I.X1, r, t, twp,
+      bxput<GT, CT, PAIR, TC, TC5>(I.X1, r, t, twp,
                               ((I.field == CS_FIELD_CN) ? Rr * c0 : (c0 > CT(0) ? Rr : CT(0))) * xsc);
     }
   ok = run_sync(span, ok, vote, vpar);
@@ -581,6 +767,66 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
   for (int n = 0; n < steps && ok; ++n) {
     const CT p = pump_at<CT>(n, I.n_steps, I.pump_kind, I.p0, I.p1, I.p_thr, I.d, I.dt, I.t0, I.width);
     const bool last = (n + 1 == steps);
+    if constexpr (TC5) {
+      // producer lane 0 streams and multiplies every row tile of the CTA; the
+      // consumer warps apply each row tile's U as soon as its accumulators are
+      // complete (no CTA-wide barrier until the end of the step)
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      bool okt = true;
+      if (w == kBWarps) {
+        if (lane == 0)
+          for (int rt = rank; rt < I.nrt && okt; rt += span)
+            okt = tc5_row_tile<GT>(a, I, Xc, rt, span, ring, slot, full, empty, gctr, issued, pre, t5);
+      } else {
+        const int hh = w >> 2;
+        for (int rt = rank; rt < I.nrt && okt; rt += span) {
+          const int r = rt * kRT + 32 * (w & 3) + lane;
+          const bool act = hh * 8 < T && r < N;
+          const size_t o = (size_t)r * T + hh * 8;
+          // this thread's 8 elements of the state, loaded before the wait
+          float cf[8], ef[8], bf[8];
+          double Rf[8];
+          if (act) {
+            load8(c + o, cf);
+            load8(e + o, ef);
+            load8(b + o, bf);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const double2 v = *reinterpret_cast<const double2*>(I.R + o + 2 * j);
+              Rf[2 * j] = v.x;
+              Rf[2 * j + 1] = v.y;
+            }
+          }
+          float U[8];
+          okt = tc5_read<GT>(a, I, t5, xsi, U);
+          if (okt && act) {
+            float cn8[8], en8[8];
+            uint64_t sg = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const CT Rr = CT(Rf[i]), cc = cf[i], ee = ef[i];
+              const CT f = wcoef * Rr * U[i] + bf[i];
+              const CT c2 = cc * cc;
+              const CT cn = cc + dt * ((CT(-1) + p - c2) * cc + Kj * ee * f);
+              const CT en = ee + dt * (-beta * (c2 - tau) * ee);
+              cn8[i] = cn;
+              en8[i] = en;
+              bxput<GT, CT, PAIR, TC, TC5>(Xn, r, hh * 8 + i, twp,
+                                           ((I.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
+              sg |= (uint64_t)(cn > CT(0) ? 1 : 0) << (8 * i);
+            }
+            *reinterpret_cast<float4*>(c + o) = make_float4(cn8[0], cn8[1], cn8[2], cn8[3]);
+            *reinterpret_cast<float4*>(c + o + 4) = make_float4(cn8[4], cn8[5], cn8[6], cn8[7]);
+            *reinterpret_cast<float4*>(e + o) = make_float4(en8[0], en8[1], en8[2], en8[3]);
+            *reinterpret_cast<float4*>(e + o + 4) = make_float4(en8[4], en8[5], en8[6], en8[7]);
+            if (last) *reinterpret_cast<uint64_t*>(I.sigma + o) = sg;
+          }
+        }
+      }
+      ok = run_sync(span, okt, vote, vpar);
+      CT* tmp = Xc; Xc = Xn; Xn = tmp;
+      continue;
+    }
     for (int rt = rank; rt < I.nrt && ok; rt += span) {
       constexpr int kU = 8;
       const int ne = kRT * T;
@@ -627,7 +873,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
               const CT en = ee + dt * (-beta * (c2 - tau) * ee);
               c[o] = cn;
               e[o] = en;
-              bxput<GT, CT, PAIR, TC>(Xn, r, t, twp,
+              bxput<GT, CT, PAIR, TC, TC5>(Xn, r, t, twp,
                                       ((I.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
               if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
             }
@@ -671,7 +917,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
             const CT en = ee + dt * (-beta * (c2 - tau) * ee);
             c[o] = cn;
             e[o] = en;
-            bxput<GT, CT, PAIR, TC>(Xn, r, t, twp,
+            bxput<GT, CT, PAIR, TC, TC5>(Xn, r, t, twp,
                                     ((I.field == CS_FIELD_CN) ? Rr * cn : (cn > CT(0) ? Rr : CT(0))) * xsc);
             if (last) I.sigma[o] = cn > CT(0) ? 1 : 0;
           }
@@ -685,7 +931,7 @@ __device__ bool run_instance(const BArgs<CT>& a, const BInst<CT>& I, int rank, i
   return ok;
 }
 
-template <typename GT, typename CT, int MR, bool PAIR, bool TC>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC, bool TC5>
 __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const size_t slot = b_slot_bytes(a.twp, sizeof(GT), sizeof(CT), a.tps);
@@ -697,14 +943,41 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
   __shared__ int s_next;   // this CTA's own pops
   __shared__ int s_bcast;  // rank 0: the cluster's pops (read by every CTA of the cluster)
   __shared__ int s_vote[2];
+  // tcgen05 form: accumulator barriers and the TMEM address
+  __shared__ uint64_t s_acc[5];
+  __shared__ uint32_t s_tmem;
+  Tc5 t5;
+  t5.accfull = s_acc;
+  t5.accfree = s_acc + 2;
+  t5.fin = s_acc + 4;
+  t5.NN = 2 * a.twp;
+  t5.idesc = std::is_same<GT, __nv_bfloat16>::value ? tc5::idesc_bf16_f32(128, t5.NN) : tc5::idesc_f16_f32(128, t5.NN);
+  // four accumulators of NN columns in each of two sets (a power of two >= 32)
+  const uint32_t tcols = t5.NN * 8 <= 32 ? 32u : (uint32_t)(t5.NN * 8);
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.slots; ++i) {
       mbar_init(full + i, 1);
-      mbar_init(empty + i, kBWarps);
+      mbar_init(empty + i, TC5 ? 1 : kBWarps);  // tcgen05: the commit after the slot's MMAs
+    }
+    if (TC5) {
+      mbar_init(t5.accfull, 1);
+      mbar_init(t5.accfull + 1, 1);
+      mbar_init(t5.accfree, kBWarps);
+      mbar_init(t5.accfree + 1, kBWarps);
+      mbar_init(t5.fin, 1);
     }
     fence_mbar_init();
   }
+  if (TC5 && threadIdx.x < 32) {
+    tc5::tmem_alloc(&s_tmem, tcols);
+    tc5::tmem_relinquish();
+  }
+  if (TC5) tc5::fence_before_sync();
   __syncthreads();
+  if (TC5) {
+    tc5::fence_after_sync();
+    t5.tmem = s_tmem;
+  }
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   unsigned gctr = 0;
@@ -725,8 +998,8 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
       if (qi >= a.n) break;
       if (qi < a.n_large) {
         const BInst<CT> I = a.insts[a.order[qi]];
-        ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, rank, a.cc, ring, slot, P, full, empty, gctr, issued, s_vote,
-                                                vpar);
+        ok = run_instance<GT, CT, MR, PAIR, TC, TC5>(a, I, rank, a.cc, ring, slot, P, full, empty, gctr, issued,
+                                                     s_vote, vpar, t5);
         continue;
       }
       together = false;
@@ -739,12 +1012,25 @@ __global__ void __launch_bounds__(kBThreads, 1) euler_batch_kernel(BArgs<CT> a) 
       if (qi >= a.n) break;
     }
     const BInst<CT> I = a.insts[a.order[qi]];
-    ok = run_instance<GT, CT, MR, PAIR, TC>(a, I, 0, 1, ring, slot, P, full, empty, gctr, issued, s_vote, vpar);
+    ok = run_instance<GT, CT, MR, PAIR, TC, TC5>(a, I, 0, 1, ring, slot, P, full, empty, gctr, issued, s_vote, vpar,
+                                                 t5);
   }
-  // After a timeout, let any copy still in flight land before the CTA exits.
-  if (!ok && threadIdx.x == kBWarps * 32) {
-    for (int s = 0; s < a.slots; ++s)
-      if (issued[s] > 0) mbar_wait(full + s, (issued[s] - 1) / a.slots & 1u, a.timeout_cycles);
+  // After a timeout, let any copy still in flight land before the CTA exits;
+  // in the tcgen05 form, let every MMA issued complete, then free the TMEM.
+  if (threadIdx.x == kBWarps * 32) {
+    if (!ok)
+      for (int s = 0; s < a.slots; ++s)
+        if (issued[s] > 0) mbar_wait(full + s, (issued[s] - 1) / a.slots & 1u, a.timeout_cycles);
+    if (TC5) {
+      tc5::commit(t5.fin);
+      mbar_wait(t5.fin, 0u, a.timeout_cycles);
+    }
+  }
+  if (TC5) tc5::fence_before_sync();
+  __syncthreads();
+  if (TC5 && threadIdx.x < 32) {
+    tc5::fence_after_sync();
+    tc5::tmem_dealloc(t5.tmem, tcols);
   }
   // no CTA leaves while another of its cluster may still read its shared memory
   cl.sync();
@@ -779,10 +1065,10 @@ inline bool batch_ring(const BatchLaunch& L, int twp, size_t gbytes, size_t cbyt
   return true;
 }
 
-template <typename GT, typename CT, int MR, bool PAIR, bool TC = false>
+template <typename GT, typename CT, int MR, bool PAIR, bool TC = false, bool TC5 = false>
 cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
-  auto fn = euler_batch_kernel<GT, CT, MR, PAIR, TC>;
+  auto fn = euler_batch_kernel<GT, CT, MR, PAIR, TC, TC5>;
   int optin = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -848,8 +1134,14 @@ template <typename GT, typename CT>
 cudaError_t launch_batch_mr(const BatchLaunch& L, cudaStream_t st) {
   const int twp = round4(L.T);
   if constexpr (tc_type<GT>::value && std::is_same<CT, float>::value) {
-    // the tensor-core form (batch_tensor_form): MR carries the n-tiles of 8 trials
-    if (batch_tensor_form(L.prm->precision, L.T, L.prm->tensor_form)) {
+    // the tensor-core forms (batch_tc_kind): tcgen05, or mma.sync with MR
+    // carrying the n-tiles of 8 trials
+    const int kind = batch_tc_kind(L.prm->precision, L.T, L.prm->tensor_form);
+    if (kind == 2) {
+      if (twp == 8) return launch_batch_typed<GT, CT, 1, false, false, true>(L, st);
+      return launch_batch_typed<GT, CT, 2, false, false, true>(L, st);
+    }
+    if (kind == 1) {
       if (twp == 8) return launch_batch_typed<GT, CT, 1, false, true>(L, st);
       return launch_batch_typed<GT, CT, 2, false, true>(L, st);
     }
@@ -882,12 +1174,14 @@ int64_t tiled_elems(int64_t N, int64_t Npad) {
   return nrt * kRT * Npad;
 }
 
-bool batch_tensor_form(int precision, int trials, int tensor_form) {
-  return tensor_form != 1 && (precision == CS_P_BF16 || precision == CS_P_FP16) && (trials == 8 || trials == 16);
+int batch_tc_kind(int precision, int trials, int tensor_form) {
+  if (tensor_form == 1 || !(precision == CS_P_BF16 || precision == CS_P_FP16) || !(trials == 8 || trials == 16))
+    return 0;
+  return tensor_form == 3 ? 1 : 2;
 }
 
-cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag) {
-  if (P.gt_prec == precision && P.Gt && P.gt_frag == (int)frag) return cudaSuccess;
+cudaError_t launch_store_tiled(ProblemDev& P, int precision, int frag) {
+  if (P.gt_prec == precision && P.Gt && P.gt_frag == frag) return cudaSuccess;
   if (P.Gt) { dev_free(P.Gt, P.stream); P.Gt = nullptr; P.gt_prec = -1; }
   const size_t gb = storage_bytes(precision);
   const int64_t elems = tiled_elems(P.N, P.Npad);
@@ -900,10 +1194,10 @@ cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag) {
     case CS_P_FP64: store_tiled_kernel<double><<<blocks, 256, 0, P.stream>>>(P.G, (double*)P.Gt, N, nrt, nkc, sc, 0); break;
     case CS_P_FP32: store_tiled_kernel<float><<<blocks, 256, 0, P.stream>>>(P.G, (float*)P.Gt, N, nrt, nkc, sc, 0); break;
     case CS_P_BF16:
-      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc, sc, (int)frag);
+      store_tiled_kernel<__nv_bfloat16><<<blocks, 256, 0, P.stream>>>(P.G, (__nv_bfloat16*)P.Gt, N, nrt, nkc, sc, frag);
       break;
     case CS_P_FP16:
-      store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc, sc, (int)frag);
+      store_tiled_kernel<__half><<<blocks, 256, 0, P.stream>>>(P.G, (__half*)P.Gt, N, nrt, nkc, sc, frag);
       break;
     case CS_P_FP8:
       if ((e = ensure_row_scales(P)) != cudaSuccess) return e;
@@ -915,7 +1209,7 @@ cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag) {
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     P.gt_prec = precision;
-    P.gt_frag = (int)frag;
+    P.gt_frag = frag;
   }
   return e;
 }

@@ -82,6 +82,7 @@ struct RefitJob {
 
 // Per-solve device state, sized by (N, trials).
 struct SolveDev {
+  size_t x_bytes = 0;   // bytes of each of X0, X1
   int trials = 0, n_outer = 0, record_steps = 0, precision = -1, cap_trials = 0, cap_outer = 0,
       cap_record = 0, cap_prec = -1;
   double* R = nullptr;          // N x T (FP64), refit signal
@@ -158,10 +159,13 @@ int batch_row_tiles(int64_t N);
 size_t batch_inst_bytes();
 void fill_batch_inst(void* dst, const ProblemDev& P, const SolveDev& S, const cs_params& prm, double theta,
                      int inst);
-cudaError_t launch_store_tiled(ProblemDev& P, int precision, bool frag);
-// Whether a batch of this precision and trial count runs the batched kernel's
-// tensor-core form (BF16 / FP16 storage, 8 or 16 trials, tensor_form != 1).
-bool batch_tensor_form(int precision, int trials, int tensor_form);
+// Tiled G_off of the batched kernel; frag = the batch_tc_kind of its launches.
+cudaError_t launch_store_tiled(ProblemDev& P, int precision, int frag);
+// Product form of a batch of this precision, trial count and tensor_form:
+// 0 FMAs, 1 mma.sync tensor cores, 2 tcgen05 tensor cores (the last two for
+// BF16 / FP16 storage and 8 or 16 trials: tensor_form 3 picks mma.sync, 1 the
+// FMAs, 0, 2 and 4 tcgen05).
+int batch_tc_kind(int precision, int trials, int tensor_form);
 cudaError_t ensure_row_scales(ProblemDev& P);
 size_t storage_bytes(int precision);
 cudaError_t launch_euler_batch(const BatchLaunch& L, cudaStream_t st);

@@ -48,6 +48,11 @@ __host__ __device__ __forceinline__ uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same for BF16 A and B (format BF16 = 1 in bits 7-9 and 10-12).
+__host__ __device__ __forceinline__ uint32_t idesc_bf16_f32(int M, int N) {
+  return idesc_f16_f32(M, N) | (1u << 7) | (1u << 10);
+}
+
 // Byte offset of element (r, k) inside one 16-k block of the canonical layout.
 __host__ __device__ __forceinline__ uint32_t canon_off(int r, int k) {
   return (uint32_t)((r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
@@ -147,6 +152,39 @@ __device__ __forceinline__ void ld16x4_sum(uint32_t taddr, uint32_t stride, floa
   for (int i = 0; i < 16; ++i)
     v[i] = ((__uint_as_float(r[i]) + __uint_as_float(r[16 + i])) + __uint_as_float(r[32 + i])) +
            __uint_as_float(r[48 + i]);
+}
+
+// 8 consecutive FP32 columns, as ld32.
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 consecutive FP32 columns from each of four accumulators (columns
+// taddr + a * stride, a = 0..3), summed in the fixed order 0 + 1 + 2 + 3 with
+// round-to-nearest additions; four loads and one completion wait.
+__device__ __forceinline__ void ld8x4_sum(uint32_t taddr, uint32_t stride, float (&v)[8]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%33];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%34];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%35];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride), "r"(taddr + 3 * stride)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    v[i] = ((__uint_as_float(r[i]) + __uint_as_float(r[8 + i])) + __uint_as_float(r[16 + i])) +
+           __uint_as_float(r[24 + i]);
 }
 
 // TMEM address of lane `lane`, column `col` relative to an allocation at `base`.

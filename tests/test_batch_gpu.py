@@ -139,18 +139,20 @@ def test_reduced_precision_support_and_rmse(precision):
     assert abs(oracle.rmse(g[0]["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
 
 
-@pytest.mark.parametrize("precision,T", [("bf16", 16), ("fp16", 8)])
-def test_batch_tensor_cores_support_and_rmse(precision, T):
-    """The batched kernel's tensor-core form (16-bit G_off, 8 or 16 trials, stats[10]
-    = 4) against the FP64 oracle with the reduced-precision gate (final support
-    identical, RMSE within 1e-3), and against the same batch on FMAs
+@pytest.mark.parametrize("precision,T,form,stat", [("bf16", 16, 0, 6), ("fp16", 8, 0, 6), ("bf16", 16, 3, 4),
+                                                    ("fp16", 8, 3, 4), ("bf16", 8, 4, 6)])
+def test_batch_tensor_cores_support_and_rmse(precision, T, form, stat):
+    """The batched kernel's tensor-core forms (16-bit G_off, 8 or 16 trials): tcgen05
+    (the default, tensor_form 0 or 4, stats[10] = 6) and mma.sync (tensor_form 3,
+    stats[10] = 4), against the FP64 oracle with the reduced-precision gate (final
+    support identical, RMSE within 1e-3), and against the same batch on FMAs
     (tensor_form = 1): identical supports."""
     w = cs_inputs.workload("trials64_n2000_fp32", N=500, M=300, nnz=50, n_outer=4, n_steps=800, precision=precision)
     inst = cs_inputs.workload_instance(w)
     r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T)
-    g = run_batch([inst], w, T)[0]
+    g = run_batch([inst], w, T, tensor_form=form)[0]
     f = run_batch([inst], w, T, tensor_form=1)[0]
-    assert g["stats"][10] == 4 and f["stats"][10] == 3
+    assert g["stats"][10] == stat and f["stats"][10] == 3
     np.testing.assert_array_equal(g["sigma"], r["sigma"])
     assert abs(oracle.rmse(g["x_hat"], inst.x0) - oracle.rmse(r["x_hat"], inst.x0)) <= 1e-3
     np.testing.assert_array_equal(g["sigma"], f["sigma"])
@@ -178,11 +180,11 @@ def test_batch_uneven_bf16_shapes():
     gs = run_batch([insts[i] for i in picked], ws, 16)
     for k, i in enumerate(picked):
         r = oracle_solve_rounded(insts[i], ws, 16, k, "bf16")
-        assert gs[k]["stats"][10] == 4
+        assert gs[k]["stats"][10] == 6
         np.testing.assert_array_equal(gs[k]["sigma"], r["sigma"])
         assert abs(oracle.rmse(gs[k]["x_hat"], insts[i].x0) - oracle.rmse(r["x_hat"], insts[i].x0)) <= 1e-3
     for inst, res, fma in zip(insts, g, f):
-        assert res["stats"][10] == 4 and fma["stats"][10] == 3
+        assert res["stats"][10] == 6 and fma["stats"][10] == 3
         assert oracle.hamming_loss(res["sigma"], fma["sigma"]) <= 0.01
         S = np.flatnonzero(res["sigma"])
         resid = inst.y - inst.A[:, S] @ res["x_hat"][S]
@@ -321,7 +323,7 @@ def test_batch_large_instance_bf16_spans_cluster_matches_oracle():
     g1 = run_batch(insts, w, 16, cluster_size=1)
     assert g8[0]["stats"][8] == 8 and g8[1]["stats"][8] == 1
     for a, b in zip(g8, g1):
-        assert a["stats"][10] == 4
+        assert a["stats"][10] == 6
         np.testing.assert_array_equal(a["sigmas"], b["sigmas"])
         np.testing.assert_array_equal(a["R"], b["R"])
     r = oracle_solve_rounded(big, w, 16, 0, "bf16")
