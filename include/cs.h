@@ -254,7 +254,8 @@ cs_status cs_outer_history(cs_problem* p, uint8_t* sigma, double* R);
 cs_status cs_problem_gram(cs_problem* p, double* G, double* hz, double* g);
 
 /* Device time of the work queued by the last cs_problem_create and the last
- * cs_solve on this problem, from CUDA events recorded on the problem's stream
+ * cs_solve on this problem (for the first problem of a cs_solve_batch: the
+ * whole batch's Euler launches, refits and objective), from CUDA events recorded on the problem's stream
  * around each group of launches (event-record nodes inside the solve's graph),
  * summed per group into ms[0..3]:
  *   [0] Gram formation  [1] Euler kernels (all outer iterations)

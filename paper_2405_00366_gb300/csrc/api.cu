@@ -828,6 +828,16 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
   }
   cudaError_t e = cudaSuccess;
   const char* where = "";
+  // phase timings of the whole batch, kept on the first problem (event-record
+  // nodes of the graph; read with cs_problem_timing on ps[0])
+  cs_problem* tp = ps[0];
+  const cudaStream_t tp_stream = tp->P.stream;
+  tp->n_marks = tp->n_create_marks;
+  tp->P.stream = cap;
+  tp->capturing = true;
+  auto tmark = [&](int cat, bool begin) {
+    if (e == cudaSuccess) e = mark(tp, cat, begin);
+  };
   for (int it = 0; it < n_outer_max && e == cudaSuccess; ++it) {
     for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
       const int na = inst_cnt[it][g];
@@ -845,19 +855,27 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
       L.timeout_cycles = timeout_cycles;
       L.ctas = gp.max_ctas > 0 ? std::min(gp.max_ctas, P0.num_sms) : P0.num_sms;
       apply_batch_shape(shapes[g], inst_rt[it][g], &L);
-      e = launch_euler_batch(L, cap);
+      tmark(TM_EULER, true);
+      if (e == cudaSuccess) e = launch_euler_batch(L, cap);
       where = "batched euler launch";
+      tmark(TM_EULER, false);
+      tmark(TM_REFIT, true);
       if (e == cudaSuccess) {
         e = launch_refit(d_jobs + job_off[g], na, groups[g].T, pool, stride, pool_blocks, it, cap);
         where = "batched refit launch";
       }
+      tmark(TM_REFIT, false);
     }
   }
+  tmark(TM_OTHER, true);
   for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
     e = launch_finish(d_jobs + job_off[g], (int)groups[g].idx.size(), groups[g].T, P0.num_sms, cap,
                       d_err4 + 4 * job_off[g]);
     where = "batched finish launch";
   }
+  tmark(TM_OTHER, false);
+  tp->capturing = false;
+  tp->P.stream = tp_stream;
   const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess || ec != cudaSuccess) {
