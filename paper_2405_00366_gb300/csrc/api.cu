@@ -656,6 +656,15 @@ static cs_status tune_batch_shape(BatchLaunch L, const std::vector<int>& rts, in
 }
 
 cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, const int32_t* trials, int32_t n) {
+  return cs::solve_batch(ps, prms, trials, n, nullptr);
+}
+
+}  // extern "C"
+
+// cs_solve_batch with problem i drawing its initial amplitudes with instance
+// number instances[i] (NULL: i).
+cs_status cs::solve_batch(cs_problem* const* ps, const cs_params* const* prms, const int32_t* trials, int32_t n,
+                          const int32_t* instances) {
   if (!ps || !prms || !trials || n < 1) return fail(CS_EINVAL, "need at least one problem, with its params and trials");
   for (int i = 0; i < n; ++i) {
     if (!ps[i]) return fail(CS_EINVAL, "problem is NULL");
@@ -741,7 +750,7 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
         const int i = act[k];
         const double eta = eta_at(it, *prms[i], ps[i]->P.lambda);
         fill_batch_inst(hinst.data() + inst_off[it][g] + ib * k, ps[i]->P, ps[i]->S, *prms[i],
-                        std::sqrt(prms[i]->tau) * eta * eta / 4.0, i);
+                        std::sqrt(prms[i]->tau) * eta * eta / 4.0, instances ? instances[i] : i);
       }
     }
   // refit jobs: per group, in the group's order (n_outer descending)
@@ -908,6 +917,8 @@ cs_status cs_solve_batch(cs_problem* const* ps, const cs_params* const* prms, co
     }
   return CS_OK;
 }
+
+extern "C" {
 
 static cs_status wait_and_check(cs_problem* p, double* stats_out) {
   if (!p) return fail(CS_EINVAL, "problem is NULL");

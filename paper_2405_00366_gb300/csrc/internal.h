@@ -154,6 +154,11 @@ std::string tune_device_tag(int device);
 bool tune_lookup(const std::string& key, std::string* value);
 void tune_store(const std::string& key, const std::string& value);
 void tune_note(bool timed);
+// cs_solve_batch with problem i drawing its initial amplitudes with instance
+// number instances[i] (NULL: i), so that a problem's result does not depend on
+// its place in the batch (the server's batches).
+cs_status solve_batch(cs_problem* const* ps, const cs_params* const* prms, const int32_t* trials, int32_t n,
+                      const int32_t* instances);
 // Row tiles of a problem of N rows in the batched kernel's tiling.
 int batch_row_tiles(int64_t N);
 size_t batch_inst_bytes();
