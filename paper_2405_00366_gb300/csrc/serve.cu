@@ -3,17 +3,20 @@
 // whole SM: about one per 26 million coupling FMAs per step and per 150 KB of
 // G_off, at least 2) and runs as a cooperative launch with clusters of one CTA,
 // so several small requests share the GPU with every grid resident.  A request
-// whose grid would be more than half the GPU is large: it starts only on an idle
-// GPU and runs with the planner's own work split (clusters) over all SMs but a
-// reserve of kBackfillSms (or the caller's cluster_size and max_ctas), because a
-// cluster launch does not keep its grid resident beside grids that were there
-// first; small requests admitted after it run in the SMs it leaves.  Requests
-// are admitted whenever a slot (a CUDA stream of the server) is free, the
-// request's device-memory estimate fits the remaining HBM budget and its grid
-// fits the SMs not held by running requests; the queue is scanned in arrival
-// order, a small request that does not fit yet does not hold back smaller ones
-// behind it, and a large one at the head of the queue stops further admissions
-// until the running requests have drained and it can start.
+// whose grid would be more than half the GPU is large: it runs with the
+// planner's own work split (clusters) over all SMs but a reserve of kBackfillSms
+// (or the caller's cluster_size and max_ctas), one large request at a time, and
+// the small requests admitted beside it run in the SMs it leaves.  A large
+// request starts once no other large one runs and the small ones running fit in
+// its reserve: a cluster launch does not keep its grid resident beside other
+// grids, so a cluster that finds its SMs taken waits (bounded) until the small
+// grid there ends; small grids never wait on the large one, so that costs time,
+// not progress.  Requests are admitted whenever a slot (a CUDA stream of the
+// server) is free, the request's device-memory estimate fits the remaining HBM
+// budget and its grid fits the SMs not held by running requests; the queue is
+// scanned in arrival order, a small request that does not fit yet does not hold
+// back smaller ones behind it, and a large one at the head of the queue stops
+// further admissions until it can start.
 // Each admitted request forms its problem (or takes the caller's, whose G is
 // already on the device) and queues its solve on its slot's stream, so the work
 // of several requests overlaps on the GPU.  A worker thread harvests finished
@@ -50,7 +53,7 @@ struct Request {
   cs_params prm;
   int trials = 0;
   size_t bytes = 0;
-  bool alone = false;  // large: starts on an idle GPU, small requests backfill the SMs it leaves
+  bool alone = false;  // large: one at a time, small requests backfill the SMs it leaves
   int state = RQ_QUEUED;
   int slot = -1;
   cs_problem* p = nullptr;
@@ -209,7 +212,12 @@ struct cs_server {
           if (!slot_busy[i]) { s = i; break; }
         if (s < 0) break;
         const bool held = r->user && busy.count(r->user);
-        if (r->alone && !held && (!running.empty() || in_use + r->bytes > budget)) break;  // drain, then run alone
+        if (r->alone && !held) {
+          bool large_running = false;
+          for (const Request* q : running) large_running = large_running || q->alone;
+          // wait (admitting nothing behind it) until it can start
+          if (large_running || in_use + r->bytes > budget || sms_in_use + sms_of(r) > num_sms) break;
+        }
         if (in_use + r->bytes > budget || sms_in_use + sms_of(r) > num_sms || held) {
           ++it;
           continue;
@@ -271,9 +279,9 @@ constexpr int kBackfillSms = 8;
 
 // The server's share of the GPU for a request.  Small (a grid of at most half
 // the SMs, sized to the work): cluster size 1 and cooperative launches, which
-// keep every CTA of a grid resident while grids share SMs.  Large: started on an
-// idle GPU, the caller's cluster_size and max_ctas (0: the planner's split over
-// all SMs but kBackfillSms).
+// keep every CTA of a grid resident while grids share SMs.  Large: one at a
+// time, the caller's cluster_size and max_ctas (0: the planner's split over all
+// SMs but kBackfillSms).
 static bool server_params(const cs_server* sv, const cs_params* prm, int64_t N, int trials, cs_params* out) {
   *out = *prm;
   const int d = prm->max_ctas > 0 ? std::min(prm->max_ctas, sv->num_sms)

@@ -96,9 +96,9 @@ def test_server_argument_checks_need_no_gpu():
 
 @pytest.mark.gpu
 def test_small_requests_backfill_beside_a_large_one():
-    """A large request starts on an idle GPU and leaves a few SMs; small requests
-    submitted after it start while it runs, and a second large request waits
-    until the GPU has drained."""
+    """A large request leaves a few SMs; small requests submitted after it start
+    while it runs, and a second large request waits until the first has
+    finished (one large request at a time)."""
     base = cs_inputs.WORKLOADS["single_n200_fp64"]
     big = (cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=5),
            dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], n_outer=2, n_steps=1500), 64)
@@ -115,7 +115,7 @@ def test_small_requests_backfill_beside_a_large_one():
         cs.cs_server_destroy(sv)
     b1, s1, s2, b2 = times
     assert s1[1] < b1[2] and s2[1] < b1[2]  # the small ones started before the first large one finished
-    assert b2[1] >= max(b1[2], s1[2], s2[2])  # the second large one waited for the GPU to drain
+    assert b2[1] >= b1[2]                   # the second large one waited for the first
 
 
 @pytest.mark.gpu
@@ -161,9 +161,9 @@ def test_requests_on_a_cached_problem():
 @pytest.mark.gpu
 def test_large_request_runs_with_the_planner_split():
     """A request whose grid would take more than half the GPU (N = 2000, 64 trials)
-    starts only on an idle GPU (after the requests before it have finished) and
-    runs with the planner's own work split over all SMs but 8: its result and plan
-    are those of a plain cs_solve of the same problem with max_ctas = SMs - 8."""
+    runs with the planner's own work split over all SMs but 8, beside small
+    requests in the SMs it leaves: its result and plan are those of a plain
+    cs_solve of the same problem with max_ctas = SMs - 8."""
     import torch
 
     base = cs_inputs.WORKLOADS["single_n200_fp64"]
@@ -173,9 +173,6 @@ def test_large_request_runs_with_the_planner_split():
     wbig = dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], n_outer=2, n_steps=300)
     reqs = small[:2] + [(big, wbig, 64)] + small[2:]
     res = _serve(reqs, slots=4, budget=64 << 30)
-    tb = res[2][4]
-    for k in (0, 1):
-        assert res[k][4][2] <= tb[1]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     h = cs.cs_problem_create(torch.from_numpy(big.A).cuda(), torch.from_numpy(big.y).cuda(), big.lam)
     try:
