@@ -715,7 +715,11 @@ cs_status cs::solve_batch(cs_problem* const* ps, const cs_params* const* prms, c
   int refit_items_max = 0;
   cs_status st = CS_OK;
   for (Group& G : groups) {
-    std::stable_sort(G.idx.begin(), G.idx.end(), [&](int a, int b) { return prms[a]->n_outer > prms[b]->n_outer; });
+    // n_outer descending (the problems still running at iteration `it` are a
+    // prefix), then N descending (the refit's work queue takes the large first)
+    std::stable_sort(G.idx.begin(), G.idx.end(), [&](int a, int b) {
+      return prms[a]->n_outer != prms[b]->n_outer ? prms[a]->n_outer > prms[b]->n_outer : ps[a]->P.N > ps[b]->P.N;
+    });
     refit_items_max = std::max(refit_items_max, (int)G.idx.size() * G.T);
   }
   for (int i = 0; i < n; ++i) {
@@ -870,7 +874,7 @@ cs_status cs::solve_batch(cs_problem* const* ps, const cs_params* const* prms, c
       tmark(TM_EULER, false);
       tmark(TM_REFIT, true);
       if (e == cudaSuccess) {
-        e = launch_refit(d_jobs + job_off[g], na, groups[g].T, pool, stride, pool_blocks, it, cap);
+        e = launch_refit(d_jobs + job_off[g], na, groups[g].T, pool, stride, pool_blocks, it, cap, nullptr, d_queue);
         where = "batched refit launch";
       }
       tmark(TM_REFIT, false);

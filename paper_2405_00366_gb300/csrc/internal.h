@@ -193,7 +193,7 @@ struct RefitPlan {
   double* R;  // the problem's R (N x T)
 };
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
-                         int outer, cudaStream_t st, const RefitPlan* plan = nullptr);
+                         int outer, cudaStream_t st, const RefitPlan* plan = nullptr, int* queue = nullptr);
 // Whether launch_refit takes the grid-wide damped Jacobi (1 + jacobi_iters
 // launches instead of 2).
 bool refit_grid_wide(const RefitPlan* plan, int njobs, int T, int pool_blocks, size_t pool_stride);

@@ -502,14 +502,28 @@ __device__ void cg_one(const RefitJob& J, int t, const int* idx, int n, double* 
 }
 
 // Refit of every (job, trial) item whose support is not a copy of an earlier
-// trial's; items are spread over the grid, block b owns workspace b of the pool.
+// trial's; block b owns workspace b of the pool.  Items go to the blocks in
+// order, each block taking the next one when it is done with its last (a
+// device counter, `queue`, zero at launch), so the expensive items of the
+// large problems (listed first by the batched solve) do not pile up on a few
+// blocks; queue = NULL spreads them round-robin instead.
 __global__ void __launch_bounds__(kRefitThreads) refit_kernel(const RefitJob* __restrict__ jobs, int T, int items,
                                                               double* __restrict__ pool, size_t pool_stride,
-                                                              int outer, size_t smem_bytes) {
+                                                              int outer, size_t smem_bytes, int* queue) {
   extern __shared__ __align__(16) float refit_smem[];
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
-    const RefitJob& J = jobs[it / T];
-    const int t = it % T;
+  __shared__ int s_item;
+  for (int it = blockIdx.x;;) {
+    if (queue) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+      __syncthreads();
+      it = s_item;
+    }
+    if (it >= items) break;
+    const int it_cur = it;
+    if (!queue) it += gridDim.x;
+    const RefitJob& J = jobs[it_cur / T];
+    const int t = it_cur % T;
     if (ld_volatile(J.err) != 0) continue;
     int* idx = J.sidx + (size_t)t * J.N;
     const int n = support_list(J.sigma, J.N, T, t, idx);
@@ -824,7 +838,7 @@ bool refit_grid_wide(const RefitPlan* plan, int njobs, int T, int pool_blocks, s
 }
 
 cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, size_t pool_stride, int pool_blocks,
-                         int outer, cudaStream_t st, const RefitPlan* plan) {
+                         int outer, cudaStream_t st, const RefitPlan* plan, int* queue) {
   const int items = njobs * T;
   if (refit_grid_wide(plan, njobs, T, pool_blocks, pool_stride)) {
     // a few trials of one problem: the sweeps spread over the whole GPU, R
@@ -860,8 +874,12 @@ cudaError_t launch_refit(const RefitJob* jobs, int njobs, int T, double* pool, s
     e = cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  if (queue) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
   refit_kernel<<<std::min(items, pool_blocks), kRefitThreads, smem, st>>>(jobs, T, items, pool, pool_stride, outer,
-                                                                           smem);
+                                                                           smem, queue);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   follow_kernel<<<std::min(items, 4096), 256, 0, st>>>(jobs, T, items);
