@@ -84,11 +84,17 @@ size_t request_bytes(int64_t M, int64_t N, int trials, int precision, bool own_p
 }
 
 // Euler CTAs for a request: one per 26e6 coupling FMAs per step (N^2 T), and
-// enough that each holds at most about 150 KB of G_off on chip, at least 2.
+// enough that each holds at most about 150 KB of G_off on chip, at least 2; at
+// least kFp64MinCtas for FP64 problems, whose FMAs issue at a small fraction of
+// the FP32 rate on this GPU (measured, N = 200 FP64: 27 us per step on 3 CTAs,
+// 18 on 8).
+constexpr int kFp64MinCtas = 8;
+
 int server_grid(int num_sms, int64_t N, int trials, int precision) {
   const double work = (double)N * (double)N * (double)trials;
   const double gbytes = (double)N * (double)N * (double)cs::storage_bytes(precision);
-  const int d = (int)std::max(std::ceil(work / 26.0e6), std::ceil(gbytes / 150.0e3));
+  int d = (int)std::max(std::ceil(work / 26.0e6), std::ceil(gbytes / 150.0e3));
+  if (precision == CS_P_FP64) d = std::max(d, kFp64MinCtas);
   return std::max(2, std::min(d, num_sms));
 }
 
