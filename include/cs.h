@@ -297,18 +297,22 @@ void cs_problem_destroy(cs_problem* p);
 
 /* ---- Serving: a continuous-batching request loop over the solver.
  * A server owns `max_slots` CUDA streams on the current device and a worker
- * thread.  Each request gets an Euler grid sized to its work (unless
+ * thread.  A small request gets an Euler grid sized to its work (unless
  * params.max_ctas is set): one CTA per 26e6 coupling FMAs per step (N^2 x
- * trials) and per 150 KB of G_off in its storage precision, at least 2; a
- * request that would take more than half the SMs takes all but SMs / 16 of
- * them, which stay for small requests.  Submitted requests
- * are scanned in arrival order; each is admitted when a slot is free, its
- * device-memory estimate fits what is left of `hbm_budget_bytes` and its grid
- * fits the SMs not held by running requests (a request that does not fit yet
- * does not hold back smaller ones behind it).  An admitted request takes its
- * problem (the caller's, or one it forms from host data) and queues its solve
- * on its slot's stream with cooperative launches, so the solves of several
- * requests overlap on the GPU.
+ * trials) and per 150 KB of G_off in its storage precision, at least 2 (8 for
+ * FP64), run as cooperative launches with clusters of one.  A request whose
+ * grid would take more than half the SMs is large: it runs with the planner's
+ * own work split (clusters) over all SMs but 8 (or the caller's cluster_size
+ * and max_ctas), one large request at a time, and small requests run beside it
+ * in the SMs it leaves.  Submitted requests are scanned in arrival order; each
+ * is admitted when a slot is free, its device-memory estimate fits what is left
+ * of `hbm_budget_bytes` and its grid fits the SMs not held by running requests
+ * (a small request that does not fit yet does not hold back smaller ones behind
+ * it; a large one at the head waits, admitting nothing behind it, until no
+ * other large request runs and the small ones fit in its reserve).  An admitted
+ * request takes its problem (the caller's, or one it forms from host data) and
+ * queues its solve on its slot's stream, so the solves of several requests
+ * overlap on the GPU.
  * When a solve finishes, the worker copies its result to host memory and
  * releases its device memory, SMs and slot at once.  A result is the same
  * whether the request ran alone or among others (same work split, fixed
@@ -321,8 +325,9 @@ cs_status cs_server_create(size_t hbm_budget_bytes, int32_t max_slots, cs_server
 /* Queue one reconstruction of the caller's problem p (made by
  * cs_problem_create): its G, h^z and g, formed once at creation, serve every
  * request on it, so a problem solved again (another seed, lambda schedule or
- * trial count) costs no new Gram.  params and trials as for cs_solve (the server
- * sets cluster_size = 1 and, if 0, max_ctas as above).  While the request runs
+ * trial count) costs no new Gram.  params and trials as for cs_solve (for a
+ * small request the server sets cluster_size = 1 and, if 0, max_ctas as above;
+ * a large one keeps them, max_ctas 0 becoming all SMs but 8).  While the request runs
  * the problem is the server's: its work moves to one of the server's streams
  * (ordered after what was already queued on the problem's own stream) and
  * returns to the problem's stream when the request finishes; requests on the
