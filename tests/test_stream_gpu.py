@@ -176,3 +176,45 @@ def test_tensor_form_2_where_no_tensor_form_applies():
         cs.cs_result(h)
     finally:
         cs.cs_problem_destroy(h)
+
+
+def test_mri_full_size_sampled_steps():
+    """The MRI-shaped workload at its full size (128 x 128 image: N = 16384,
+    M = 4915, 8 trials, FP16 G_off streamed, the plan the benchmark runs): the
+    first three Euler steps of the first CIM run, as the library recorded them,
+    against the oracle's own step (local field of Eq. localfieldMFZ, injection,
+    explicit Euler step) applied to the recorded state of the step before, on 64
+    sampled rows, with those rows of G_off formed from A in FP64 and rounded to
+    FP16 as the library stores them (relative 1e-4, the FP32 trajectory bar)."""
+    w = cs_inputs.workload("mri_n16384_fp16", n_outer=1)
+    inst = cs_inputs.workload_instance(w)
+    N, T, K = inst.N, w["trials"], 3
+    prm = cs.params_from_workload(w, record_steps=K)
+    h = cs.cs_problem_create(torch.from_numpy(inst.A).cuda(), torch.from_numpy(inst.y).cuda(), inst.lam)
+    try:
+        cs.cs_solve(h, prm, T)
+        cs.cs_result(h)
+        c_rec, e_rec = cs.cs_trajectory(h, K, T)
+    finally:
+        cs.cs_problem_destroy(h)
+    op = oracle_params(w)
+    rows = np.sort(np.random.default_rng(5).choice(N, 64, replace=False))
+    A = inst.A
+    hz = A.T @ inst.y
+    g = np.einsum("ij,ij->j", A, A)
+    Goff = A[:, rows].T @ A
+    Goff[np.arange(rows.size), rows] = 0.0
+    Goff = round_to_storage(Goff, "fp16")
+    R = np.repeat((hz / g)[:, None], T, axis=1)
+    eta = oracle.eta_at(0, op, inst.lam)
+    c = np.stack([oracle.initial_amplitudes(op.seed, 0, t, 0, N, op.init_kind, op.init_scale) for t in range(T)],
+                 axis=1)
+    e = np.ones((N, T))
+    for n in range(K):
+        hr = oracle.local_field_cn(Goff, R, c, hz[rows], op.tau)
+        inj = oracle.injection(op.j, e[rows], R[rows], hr, eta, op.tau)
+        cn, en = oracle.euler_step(c[rows], e[rows], oracle.pump(n, op), inj, op)
+        for got, ref in ((c_rec[n][rows], cn), (e_rec[n][rows], en)):
+            err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-2)
+            assert err <= 1e-4, (n, err)
+        c, e = c_rec[n], e_rec[n]
