@@ -84,7 +84,9 @@ typedef struct {
   int32_t record_steps; /* record c, e after each of the first k steps of outer iteration 0 */
   int64_t timeout_ms;   /* bound on every device-side wait (grid barrier) */
   int32_t test_phantom_ctas; /* test hook: the grid barrier also waits for this many CTAs that
-                                do not exist, so it runs into timeout_ms; 0 in normal use */
+                                do not exist, so it runs into timeout_ms; in a batch, > 0 makes
+                                each CTA's first ring copy never issued, so the waits on it
+                                run into timeout_ms; 0 in normal use */
   int32_t cluster_size; /* CTAs per thread-block cluster of the Euler kernel: 0 = chosen by the
                            library's planner, or 1, 2, 4, 8; in a batch, the first problem of a
                            group fixes the batched kernel's cluster size this way */

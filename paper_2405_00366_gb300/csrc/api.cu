@@ -867,6 +867,7 @@ cs_status cs::solve_batch(cs_problem* const* ps, const cs_params* const* prms, c
       L.err = d_err;
       L.timeout_cycles = timeout_cycles;
       L.ctas = gp.max_ctas > 0 ? std::min(gp.max_ctas, P0.num_sms) : P0.num_sms;
+      L.test_skip = gp.test_phantom_ctas > 0 ? 1 : 0;
       apply_batch_shape(shapes[g], inst_rt[it][g], &L);
       tmark(TM_EULER, true);
       if (e == cudaSuccess) e = launch_euler_batch(L, cap);

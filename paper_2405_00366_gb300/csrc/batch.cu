@@ -119,6 +119,7 @@ struct BArgs {
   int cc;           // CTAs per cluster
   int n_large;      // queue items [0, n_large) are run by a whole cluster
   int step_cap;     // > 0: at most this many Euler steps per run (tuning runs)
+  int test_skip;    // test hook: the CTA's first ring copy is never issued
 };
 
 // One ring slot: tps consecutive column tiles of G_off, then their tps x kKC
@@ -154,6 +155,7 @@ __device__ __forceinline__ bool produce_row_tile(const BArgs<CT>& a, const BInst
       set_error(a.err, DEV_TIMEOUT);
       return false;
     }
+    if (a.test_skip && g == 0) continue;  // test hook: the waits on this slot run out
     const int kc0 = ci * a.tps, nt = min(a.tps, nkc - kc0);
     unsigned char* dst = ring + (size_t)s * slot;
     issued[s] = g + 1;
@@ -1102,6 +1104,7 @@ cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st) {
   a.cc = cc;
   a.n_large = cc > 1 ? std::min(L.n_large, L.n) : 0;
   a.step_cap = L.step_cap;
+  a.test_skip = L.test_skip;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

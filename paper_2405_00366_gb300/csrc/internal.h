@@ -142,6 +142,7 @@ struct BatchLaunch {
   int tps = 0;         // column tiles per ring slot (1, 2, 4; 0 = the launch's default)
   int slots = 0;       // ring slots (2..8; 0 = as many as fit)
   int step_cap = 0;    // > 0: at most this many Euler steps per run (tuning runs)
+  int test_skip = 0;   // test hook (test_phantom_ctas > 0): each CTA's first ring copy is never issued
 };
 // Ring shape and cluster size of a batched launch (the batch autotuner's choice).
 struct BatchShape {

@@ -381,3 +381,32 @@ def test_tune_cache_persists_across_processes(tmp_path):
     assert second["tunings"] == 0 and second["disk_hits"] == first["tunings"]
     assert second["plan"] == first["plan"]
     assert second["batch"] == first["batch"] and second["single"] == first["single"]
+
+
+@pytest.mark.parametrize("precision,T", [("fp32", 4), ("bf16", 16)])
+def test_batch_timeout_is_reported_and_context_survives(precision, T):
+    """With the test hook (test_phantom_ctas > 0) each CTA's first ring copy of a
+    batched launch is never issued (FMA form for FP32, tcgen05 form for BF16): the
+    waits on it run into timeout_ms, every problem of the batch reports
+    CS_ETIMEOUT, and the next batch on the same problems completes (FP32: the
+    oracle's supports)."""
+    insts = uneven([300, 150], seed=51)
+    w = dict(cs_inputs.WORKLOADS["single_n200_fp64"], n_outer=2, n_steps=300, precision=precision, seed=2)
+    hs = [cs.cs_problem_create(torch.from_numpy(i.A).cuda(), torch.from_numpy(i.y).cuda(), i.lam) for i in insts]
+    try:
+        cs.cs_solve_batch(hs, cs.params_from_workload(w, timeout_ms=200, test_phantom_ctas=1), T)
+        for h in hs:
+            with pytest.raises(cs.CSError) as ei:
+                cs.cs_result(h)
+            assert ei.value.status == cs.CS_ETIMEOUT
+        cs.cs_solve_batch(hs, cs.params_from_workload(w), T)
+        for i, (h, inst) in enumerate(zip(hs, insts)):
+            x, s, E, st, status = cs.cs_result(h)
+            assert status == cs.CS_OK and np.isfinite(E)
+            if precision == "fp32":
+                r = oracle.solve(inst.A, inst.y, inst.lam, oracle_params(w), trials=T, inst=i)
+                np.testing.assert_array_equal(s, r["sigma"])
+    finally:
+        for h in hs:
+            cs.cs_problem_destroy(h)
+    torch.cuda.synchronize()
