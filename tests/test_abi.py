@@ -104,3 +104,20 @@ def test_tune_info_reports_cache_path(lib, tmp_path):
     r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip().splitlines()[-1] == repr((0, 0, str(cache)))
+
+
+def test_tune_cache_file_with_bad_lines_loads(lib, tmp_path):
+    """A tuning-cache file with malformed lines (no tab, empty key or value,
+    binary junk, an over-long line) loads without error on the host: the process
+    reports no tunings and no hits, and the file is left as it was."""
+    cache = tmp_path / "tune.txt"
+    junk = (b"no tab on this line\n\tempty key\nkey only\t\n" + bytes(range(1, 9)) + b"\n" + b"x" * 10000 +
+            b"\tlong\nbatch|cs-tune-1|fake|sm103|152|p3|T16\t1 4 0 0\n")
+    cache.write_bytes(junk)
+    code = ("import sys; sys.path.insert(0, sys.argv[1]); from paper_2405_00366_gb300 import cs; "
+            "print(cs.cs_tune_info())")
+    env = dict(os.environ, CS_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == repr((0, 0, str(cache)))
+    assert cache.read_bytes() == junk
