@@ -102,7 +102,9 @@ def test_small_requests_backfill_beside_a_large_one():
     base = cs_inputs.WORKLOADS["single_n200_fp64"]
     big = (cs_inputs.random_instance(2000, 1200, 200, 0.01, 0.03, seed=5),
            dict(cs_inputs.WORKLOADS["trials64_n2000_fp32"], n_outer=2, n_steps=1500), 64)
-    small = (cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=6), dict(base, n_outer=2, n_steps=300), 1)
+    # FP32 small requests: 2-CTA grids, so both fit in the SMs the large one leaves
+    small = (cs_inputs.random_instance(200, 120, 20, 0.0, 0.05, seed=6),
+             dict(base, n_outer=2, n_steps=300, precision="fp32"), 1)
     sv = cs.cs_server_create(8 << 30, 8)
     try:
         order = [big, small, small, big]
